@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 PC-LSQR (Gaia AVU-GSR hot path).
+
+One step = one whole PC-LSQR solve through the C ABI (preconditioner, the
+LSQR iterations with aprod 1 / aprod 2 and the vector updates, the final
+x = p o z and standard errors) on a synthetic system of the paper's
+structure.  The metric is LSQR iterations per second over the whole job.
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own
+replica (different seed, same shape): the path needs no exchange between
+replicas, so there is no collective on the data path ("scaling": "weak").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload medium]
+  python bench.py --impl reference ...   # the CPU oracle, timed on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2212_11675_gb300 import gen  # noqa: E402
+
+ITMAX = {"tiny": 200, "medium": 500}
+METRIC = "PC-LSQR iter/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 FMA peak of GB300: 1.25 TFLOP/s nominal (152 SMs, 2070 MHz).
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([c.strip() for c in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_system(workload, rank):
+    shape = gen.SHAPES[workload]
+    seed = gen.SEEDS[workload] + 7919 * rank
+    return gen.generate(shape, seed), seed
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    sys_, seed = make_system(args.workload, 0)
+    xt = gen.x_true(sys_, seed)
+    b = oracle.aprod1(sys_, xt) + gen.noise(sys_, seed + 1)
+    iters = args.ref_iters
+    for _ in range(args.warmup):
+        oracle.pc_lsqr(sys_, b, 1, 0.0, 0.0)
+    t0 = time.perf_counter()
+    total = 0
+    for _ in range(args.steps):
+        r = oracle.pc_lsqr(sys_, b, iters, 0.0, 0.0)
+        total += r["itn"]
+    dt = time.perf_counter() - t0
+    val = total / dt
+    sample = ("%d steps x (preconditioner + %d LSQR iterations) of the %s system (m=%d, n=%d)"
+              % (args.steps, iters, args.workload, sys_.m, sys_.n))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "iter/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "m": sys_.m, "n": sys_.n},
+            "cpu_baseline": {"value": val, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_kernel(fn, stream, reps, torch):
+    """Average duration (s) of fn() launched reps times on `stream`."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps * 1e-3
+
+
+def cpu_baseline(sys_, seed, seconds):
+    """The oracle timed on a bounded sample: LSQR iterations of the same system."""
+    import oracle
+    xt = gen.x_true(sys_, seed)
+    b = oracle.aprod1(sys_, xt) + gen.noise(sys_, seed + 1)
+    t0 = time.perf_counter()
+    r = oracle.pc_lsqr(sys_, b, 1, 0.0, 0.0)
+    one = time.perf_counter() - t0
+    iters = max(1, min(500, int(seconds / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    r = oracle.pc_lsqr(sys_, b, iters, 0.0, 0.0)
+    dt = time.perf_counter() - t0
+    return {"value": r["itn"] / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": "preconditioner + %d LSQR iterations of the same system, single-threaded "
+                      "FP64 C oracle (%.1f s)" % (r["itn"], dt)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="medium", choices=["tiny", "medium"])
+    ap.add_argument("--itmax", type=int, default=0)
+    ap.add_argument("--ref-iters", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2212_11675_gb300 import _lib
+    from paper_2212_11675_gb300.solver import Solver
+
+    itmax = args.itmax or ITMAX[args.workload]
+    sys_, seed = make_system(args.workload, rank)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    solver = Solver(sys_, conlim=0.0)
+    # right-hand side b = A x_true + noise, built on the device
+    xt = torch.tensor(gen.x_true(sys_, seed), device=dev)
+    b = torch.tensor(gen.noise(sys_, seed + 1), device=dev)
+    with torch.cuda.stream(stream):
+        solver.aprod1(xt, b, stream=stream)
+    x = torch.empty(sys_.n, dtype=torch.float64, device=dev)
+    se = torch.empty(sys_.n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        return solver.lsqr_solve(b, itmax, 0.0, 0.0, x=x, se=se, stream=stream)[2]
+
+    for _ in range(args.warmup):
+        step()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    iters = 0
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            iters += step()["itn"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    # whole job: iterations of all ranks over the slowest rank's time
+    tot = torch.tensor([iters, t], dtype=torch.float64, device=dev)
+    if dist:
+        it_all = tot[:1].clone()
+        dist.all_reduce(it_all, op=dist.ReduceOp.SUM)
+        t_all = tot[1:].clone()
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+        iters_total, t_max = float(it_all), float(t_all)
+    else:
+        iters_total, t_max = float(iters), t
+    value = iters_total / t_max
+
+    # end to end through the C ABI with host buffers (H2D of b and D2H of x,
+    # se inside the timed region)
+    bh = b.cpu().numpy().copy()
+    xh = np.empty(sys_.n)
+    seh = np.empty(sys_.n)
+    solver.lsqr_solve(bh, itmax, 0.0, 0.0, x=xh, se=seh, stream=stream)
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(args.steps):
+        e2e_iters += solver.lsqr_solve(bh, itmax, 0.0, 0.0, x=xh, se=seh, stream=stream)[2]["itn"]
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": ws * e2e_iters / e2e_t, "unit": "iter/s",
+           "h2d_bytes_per_step": int(bh.nbytes), "d2h_bytes_per_step": int(xh.nbytes + seh.nbytes)}
+
+    # roofline of the two row kernels, each timed alone through its entry point
+    m, n = sys_.m, sys_.n
+    yv = torch.zeros(m, dtype=torch.float64, device=dev)
+    xv = torch.zeros(n, dtype=torch.float64, device=dev)
+    vin = torch.randn(n, dtype=torch.float64, device=dev)
+    uin = torch.randn(m, dtype=torch.float64, device=dev)
+    reps = 20
+    t_a1 = time_kernel(lambda: solver.aprod1(vin, yv, stream=stream), stream, reps, torch)
+    t_a2 = time_kernel(lambda: solver.aprod2(uin, xv, stream=stream), stream, reps, torch)
+    hbm, src = peaks()
+    # algorithmic bytes per launch: 24 values x 8 B + 16 B index record per row,
+    # y read+write (aprod 1) or read (aprod 2), 4 B star pointer per star,
+    # x gathered / written once per unknown
+    bytes_a1 = m * (24 * 8 + 16 + 16) + 4 * sys_.n_stars + 8 * n
+    bytes_a2 = m * (24 * 8 + 16 + 8) + 4 * sys_.n_stars + 16 * n
+    flops = 2 * 24 * m  # one FMA per nonzero
+    gbs_a1, gbs_a2 = bytes_a1 / t_a1 / 1e9, bytes_a2 / t_a2 / 1e9
+    tf_a1, tf_a2 = flops / t_a1 / 1e12, flops / t_a2 / 1e12
+    dom = "aprod2" if t_a2 >= t_a1 else "aprod1"
+    t_dom, gbs_dom, tf_dom, byt = ((t_a2, gbs_a2, tf_a2, bytes_a2) if dom == "aprod2"
+                                   else (t_a1, gbs_a1, tf_a1, bytes_a1))
+    f_hbm = gbs_dom / hbm
+    f_alu = tf_dom / FP64_NOMINAL_TFLOPS
+    if f_alu >= f_hbm:
+        roof = {"bound": "alu", "achieved": tf_dom, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": f_alu, "traffic": None}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs_dom, "peak": hbm, "unit": "GB/s", "frac": f_hbm,
+                "traffic": None}
+    roof.update({"kernel": dom, "peak_source": "FP64 nominal (recipe)" if roof["bound"] == "alu"
+                 else "%s HBM copy" % src,
+                 "kernels": {"aprod1": {"ms": t_a1 * 1e3, "GB/s": gbs_a1, "hbm_frac": gbs_a1 / hbm,
+                                        "fp64_TFLOP/s": tf_a1, "fp64_frac": tf_a1 / FP64_NOMINAL_TFLOPS},
+                             "aprod2": {"ms": t_a2 * 1e3, "GB/s": gbs_a2, "hbm_frac": gbs_a2 / hbm,
+                                        "fp64_TFLOP/s": tf_a2, "fp64_frac": tf_a2 / FP64_NOMINAL_TFLOPS}},
+                 "aprod_GB/s": (bytes_a1 + bytes_a2) / (t_a1 + t_a2) / 1e9})
+
+    launches_per_step = 9 + 4 * (iters // args.steps)
+    line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "stars": sys_.n_stars, "m": m, "n": n,
+                       "n_dfa": sys_.n_dfa, "n_instr": sys_.n_instr, "itmax": itmax,
+                       "iterations_per_step": iters / args.steps, "atol": 0.0, "btol": 0.0,
+                       "l2": "inputs larger than L2 (%.2f GB matrix)" % (m * 208 / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roof, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches_per_step * args.steps}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sys_, seed, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,153 @@
+/*
+ * gsr.h -- C ABI of the GB300 Gaia AVU-GSR PC-LSQR library (libgsr.so).
+ *
+ * The library solves, in the least-squares sense, the linearised Gaia
+ * observation system A x = b (paper §1, Eq. 1) with the preconditioned LSQR
+ * of the paper's flowchart (§3): column-norm preconditioning (§2), the two
+ * products aprod 1 and aprod 2 (Alg. 1, Alg. 2), the LSQR iteration of Paige
+ * and Saunders (1982) and, at the end, multiplication of the solution and of
+ * its standard errors by the preconditioning vector p (§3).
+ *
+ * Matrix structure (§3): row i is one observation of star s(i); it holds 24
+ * nonzeros in this order
+ *   5 astrometric  -> columns 5*s(i) + j,                 j = 0..4
+ *   12 attitude    -> columns 5*S + a*D + attoff[i] + j,  a = 0..2, j = 0..3
+ *   6 instrumental -> columns 5*S + 3*D + instr[6*i + j], j = 0..5
+ *   1 global       -> column  5*S + 3*D + I
+ * for S stars, D attitude knots per axis (N_DFA) and I instrumental unknowns,
+ * so there are n = 5*S + 3*D + I + 1 unknowns.  Rows are grouped by star:
+ * the rows of star s are star_ptr[s] .. star_ptr[s+1]-1.
+ *
+ * Conventions for every entry point:
+ *  - Return value: GSR_OK (0) or a negative GSR_ERR_* code; gsr_strerror()
+ *    names it.  On error no output has been written unless stated.
+ *  - Vectors are double precision.  Pointers may be device or host memory;
+ *    the library asks the CUDA runtime which, and stages host buffers
+ *    through device memory it owns (the copies are part of the call).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is ordered on that stream; entry points that return
+ *    scalar results (gsr_lsqr_solve) synchronise it before returning,
+ *    the others return without synchronising when all pointers are device
+ *    pointers.
+ *  - The caller owns every pointer it passes; the handle owns its copies of
+ *    the matrix and its workspace.  A handle is bound to the CUDA device that
+ *    was current at gsr_create and must be used from one host thread at a
+ *    time.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSR_OK 0
+#define GSR_ERR_ARG (-1)         /* bad argument (null pointer, size, tolerance) */
+#define GSR_ERR_INDEX (-2)       /* structure out of range (star_ptr, attoff, instr) */
+#define GSR_ERR_OOM (-3)         /* device or host allocation failed */
+#define GSR_ERR_CUDA (-4)        /* a CUDA runtime call failed */
+#define GSR_ERR_TIMEOUT (-5)     /* a bounded device wait expired */
+#define GSR_ERR_NONFINITE (-6)   /* NaN or Inf in the input or in the recurrences */
+#define GSR_ERR_UNSUPPORTED (-7) /* configuration not supported by this build */
+
+/* Storage and arithmetic of the matrix values. */
+#define GSR_PREC_FP64 0 /* IEEE double values, native FP64 arithmetic */
+
+typedef struct {
+    int64_t n_stars;  /* S >= 1 */
+    int64_t n_dfa;    /* D >= 4: attitude B-spline knots per axis (N_DFA) */
+    int64_t n_instr;  /* I >= 6, I <= 65536 */
+    int64_t n_rows;   /* m >= 1, must equal star_ptr[S]; m < 2^32 */
+} gsr_dims;
+
+typedef struct {
+    int precision;      /* GSR_PREC_*; default GSR_PREC_FP64 */
+    double conlim;      /* condition limit of stopping rule S3; 0 disables it.
+                           gsr_config_default sets 1e8 */
+    int lanes_per_star; /* threads cooperating on one star in the row kernels:
+                           4, 8, 16 or 32; 0 = library choice */
+    int validate;       /* nonzero: gsr_create checks every index and value */
+} gsr_config;
+
+typedef struct {
+    int istop;     /* LSQR stopping reason (Paige & Saunders 1982, §6):
+                      0 b = 0 or A^T b = 0, x = 0 is exact
+                      1 ||r|| <= btol*||b|| + atol*||A||*||x||   (rule S1)
+                      2 ||A^T r|| <= atol*||A||*||r||             (rule S2)
+                      3 cond(A) estimate >= conlim                (rule S3)
+                      4,5,6 as 1,2,3 with the tolerance at machine precision
+                      7 itmax iterations done */
+    int itn;       /* iterations done */
+    double rnorm;  /* ||b - A x|| estimate */
+    double arnorm; /* ||(A diag p)^T r|| estimate */
+    double anorm;  /* Frobenius-norm estimate of A diag(p) */
+    double acond;  /* condition estimate of A diag(p) */
+    double xnorm;  /* ||z|| of the preconditioned solution z (x = p o z), exact */
+    double bnorm;  /* ||b|| */
+} gsr_result;
+
+/* Fill cfg with the defaults (FP64, conlim 1e8, automatic lanes, validate). */
+void gsr_config_default(gsr_config *cfg);
+
+/*
+ * Create a handle holding A (paper §3, "A_d", "M_i", "I_c").
+ *   star_ptr [S+1]  uint32, star_ptr[0] = 0, non-decreasing, star_ptr[S] = m
+ *   attoff   [m]    uint32, first attitude knot of row i, attoff[i] <= D-4
+ *   instr    [6*m]  uint16, instrument indices of row i, each < I
+ *   values   [24*m] double, row-major in the 24-value order above
+ * The arrays are copied (host or device memory); they may be freed after the
+ * call.  cfg may be NULL for the defaults.  Errors: GSR_ERR_ARG for bad
+ * dims, GSR_ERR_INDEX for structure out of range, GSR_ERR_NONFINITE for a
+ * NaN/Inf value (when cfg->validate), GSR_ERR_OOM, GSR_ERR_CUDA.  *h is set
+ * only on success.
+ */
+int gsr_create(void **h, const gsr_dims *dims, const uint32_t *star_ptr,
+               const uint32_t *attoff, const uint16_t *instr,
+               const double *values, const gsr_config *cfg);
+
+/* Release every resource of the handle.  NULL is accepted. */
+int gsr_destroy(void *h);
+
+/* aprod mode 1 (Alg. 1): y[m] += A x[n], A the original (unpreconditioned)
+ * matrix.  x and y must not overlap. */
+int gsr_aprod1(void *h, const double *x, double *y, void *stream);
+
+/* aprod mode 2 (Alg. 2): x[n] += A^T y[m], shared columns summed exactly
+ * (no lost updates).  x and y must not overlap. */
+int gsr_aprod2(void *h, const double *y, double *x, void *stream);
+
+/* Column-norm preconditioner (§2): p[n] = 1/||A(:,j)||_2, or 1 for a column
+ * without nonzeros. */
+int gsr_precondition(void *h, double *p, void *stream);
+
+/*
+ * PC-LSQR (§3 flowchart): computes p, runs LSQR on A diag(p) from z = 0 for
+ * at most itmax iterations, then returns x = p o z and the standard errors
+ * se = p o sqrt(var) * rnorm / sqrt(max(m - n, 1)), var being LSQR's
+ * variance estimate.  b[m] is the right-hand side; x[n] and se[n] are
+ * outputs (se may be NULL).  atol, btol >= 0 are the tolerances of rules S1
+ * and S2 (0 disables them); the condition limit is the handle's conlim.
+ * The whole iteration runs on the device (one CUDA graph, no host
+ * synchronisation until the end).  `out` receives the stopping estimates.
+ * Errors: GSR_ERR_ARG, GSR_ERR_NONFINITE (a NaN/Inf in b or in the scalar
+ * recurrences; x and se are then undefined), GSR_ERR_CUDA.
+ */
+int gsr_lsqr_solve(void *h, const double *b, int itmax, double atol,
+                   double btol, double *x, double *se, gsr_result *out,
+                   void *stream);
+
+/* Text of the last CUDA failure seen by this host thread ("" if none). */
+const char *gsr_last_error(void);
+
+/* Sizes of a handle: m, n and the bytes of device memory it holds. */
+int gsr_info(void *h, int64_t *m, int64_t *n, int64_t *device_bytes);
+
+/* Text for a GSR_* code (static storage). */
+const char *gsr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSR_H */

@@ -1,0 +1,411 @@
+// C ABI of the GB300 PC-LSQR library: handle creation (copy, layout and
+// validation of the Gaia system), the two products, the preconditioner and
+// the whole PC-LSQR solve.  No torch types cross this boundary.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+cudaError_t enqueue_precondition(const gsr_handle_t *h, double *p, cudaStream_t st);
+int aprod2_grid(const gsr_handle_t *h);
+}  // namespace gsr
+
+using namespace gsr;
+
+static thread_local char g_last_error[256] = "";
+
+static int cuda_fail(cudaError_t e, const char *what)
+{
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
+    cudaGetLastError();
+    return GSR_ERR_CUDA;
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess)                                       \
+            return e_ == cudaErrorMemoryAllocation                   \
+                       ? (snprintf(g_last_error, sizeof g_last_error, \
+                                   "%s: out of memory", #call),      \
+                          cudaGetLastError(), GSR_ERR_OOM)           \
+                       : cuda_fail(e_, #call);                       \
+    } while (0)
+
+extern "C" const char *gsr_last_error(void) { return g_last_error; }
+
+extern "C" const char *gsr_strerror(int code)
+{
+    switch (code) {
+    case GSR_OK: return "success";
+    case GSR_ERR_ARG: return "invalid argument";
+    case GSR_ERR_INDEX: return "matrix structure out of range";
+    case GSR_ERR_OOM: return "out of memory";
+    case GSR_ERR_CUDA: return "CUDA runtime error";
+    case GSR_ERR_TIMEOUT: return "device wait timed out";
+    case GSR_ERR_NONFINITE: return "non-finite value";
+    case GSR_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+    }
+}
+
+extern "C" void gsr_config_default(gsr_config *c)
+{
+    if (!c)
+        return;
+    memset(c, 0, sizeof *c);
+    c->precision = GSR_PREC_FP64;
+    c->conlim = 1e8;
+    c->lanes_per_star = 0;
+    c->validate = 1;
+}
+
+static bool on_device(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static int dalloc(gsr_handle_t *h, T **p, int64_t count)
+{
+    const size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        snprintf(g_last_error, sizeof g_last_error, "cudaMalloc(%zu bytes): %s", bytes,
+                 cudaGetErrorString(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? GSR_ERR_OOM : GSR_ERR_CUDA;
+    }
+    h->device_bytes += (int64_t)bytes;
+    return GSR_OK;
+}
+
+#define TRY(x)                \
+    do {                      \
+        int rc_ = (x);        \
+        if (rc_ != GSR_OK)    \
+            return rc_;       \
+    } while (0)
+
+static void release(gsr_handle_t *h)
+{
+    if (!h)
+        return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    if (h->solve_exec)
+        cudaGraphExecDestroy(h->solve_exec);
+    if (h->cap_stream)
+        cudaStreamDestroy(h->cap_stream);
+    void *dev[] = {h->d_star_ptr, h->d_rec, h->d_val, h->d_p, h->d_u, h->d_v, h->d_w, h->d_z,
+                   h->d_var, h->d_q, h->d_vp, h->d_vt, h->d_bstage, h->d_xstage, h->d_sestage,
+                   h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err};
+    for (void *p : dev)
+        if (p)
+            cudaFree(p);
+    if (h->h_state)
+        cudaFreeHost(h->h_state);
+    if (h->h_args)
+        cudaFreeHost(h->h_args);
+    cudaGetLastError();
+    if (cur >= 0)
+        cudaSetDevice(cur);
+    delete h;
+}
+
+static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_ptr,
+                       const uint32_t *attoff, const uint16_t *instr, const double *values)
+{
+    const int64_t S = d->n_stars, D = d->n_dfa, I = d->n_instr, m = d->n_rows;
+    const int64_t n = kNAstro * S + 3 * D + I + 1;
+    const int64_t mp = (m + 31) / 32 * 32;
+    cudaDeviceProp prop;
+    CK(cudaGetDevice(&h->device));
+    CK(cudaGetDeviceProperties(&prop, h->device));
+    h->nsm = prop.multiProcessorCount;
+
+    SysView &A = h->sys;
+    A.S = S; A.D = D; A.I = I; A.m = m; A.n = n; A.mp = mp;
+    A.att0 = kNAstro * S;
+    A.ins0 = A.att0 + 3 * D;
+    A.glb0 = A.ins0 + I;
+
+    TRY(dalloc(h, &h->d_star_ptr, S + 1));
+    TRY(dalloc(h, &h->d_rec, m));
+    TRY(dalloc(h, &h->d_val, kNPar * mp));
+    TRY(dalloc(h, &h->d_p, n));
+    TRY(dalloc(h, &h->d_u, m));
+    TRY(dalloc(h, &h->d_v, n));
+    TRY(dalloc(h, &h->d_w, n));
+    TRY(dalloc(h, &h->d_z, n));
+    TRY(dalloc(h, &h->d_var, n));
+    TRY(dalloc(h, &h->d_q, n));
+    TRY(dalloc(h, &h->d_vp, n));
+    TRY(dalloc(h, &h->d_state, 1));
+    TRY(dalloc(h, &h->d_args, 1));
+    TRY(dalloc(h, &h->d_partial, (int64_t)kRedCount * kPartialsPerKind));
+    TRY(dalloc(h, &h->d_counter, kRedCount));
+    TRY(dalloc(h, &h->d_err, 1));
+    CK(cudaMemset(h->d_counter, 0, kRedCount * sizeof(unsigned)));
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    CK(cudaMemset(h->d_val, 0, (size_t)kNPar * mp * sizeof(double)));
+    CK(cudaMallocHost((void **)&h->h_state, sizeof(SolveState)));
+    CK(cudaMallocHost((void **)&h->h_args, sizeof(SolveArgs)));
+    A.star_ptr = h->d_star_ptr;
+    A.rec = h->d_rec;
+    A.val = h->d_val;
+
+    CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t st = h->cap_stream;
+
+    // star_ptr: host arrays are checked here; all of it again on the device
+    if (!on_device(star_ptr) && (star_ptr[0] != 0 || (int64_t)star_ptr[S] != m))
+        return GSR_ERR_INDEX;
+    CK(cudaMemcpyAsync(h->d_star_ptr, star_ptr, (S + 1) * sizeof(uint32_t), cudaMemcpyDefault, st));
+
+    // index records and value planes, staged in chunks of rows
+    const int64_t chunk = 1 << 20;
+    const bool rec_dev = on_device(attoff) && on_device(instr);
+    const bool val_dev = on_device(values);
+    uint32_t *s_att = nullptr;
+    uint16_t *s_ins = nullptr;
+    double *s_val = nullptr;
+    int rc = GSR_OK;
+    if (!rec_dev) {
+        if (cudaMalloc(&s_att, chunk * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&s_ins, chunk * kNInstr * sizeof(uint16_t)) != cudaSuccess)
+            rc = GSR_ERR_OOM;
+    }
+    if (rc == GSR_OK && !val_dev && cudaMalloc(&s_val, chunk * kNPar * sizeof(double)) != cudaSuccess)
+        rc = GSR_ERR_OOM;
+    for (int64_t r0 = 0; rc == GSR_OK && r0 < m; r0 += chunk) {
+        const int64_t nr = (m - r0 < chunk) ? m - r0 : chunk;
+        cudaError_t e = cudaSuccess;
+        if (rec_dev) {
+            e = launch_pack_rec(h, attoff + r0, instr + kNInstr * r0, r0, nr, st);
+        } else {
+            e = cudaMemcpyAsync(s_att, attoff + r0, nr * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s_ins, instr + kNInstr * r0, nr * kNInstr * sizeof(uint16_t),
+                                    cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = launch_pack_rec(h, s_att, s_ins, r0, nr, st);
+        }
+        if (e == cudaSuccess) {
+            if (val_dev) {
+                e = launch_planes(h, values + kNPar * r0, r0, nr, st);
+            } else {
+                e = cudaMemcpyAsync(s_val, values + kNPar * r0, nr * kNPar * sizeof(double),
+                                    cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess)
+                    e = launch_planes(h, s_val, r0, nr, st);
+            }
+        }
+        if (e == cudaSuccess && !(rec_dev && val_dev))
+            e = cudaStreamSynchronize(st);  // staging buffers are reused
+        if (e != cudaSuccess)
+            rc = cuda_fail(e, "layout");
+    }
+    if (s_att) cudaFree(s_att);
+    if (s_ins) cudaFree(s_ins);
+    if (s_val) cudaFree(s_val);
+    if (rc != GSR_OK)
+        return rc;
+
+    // validation of the structure (always) and of the values (cfg.validate)
+    CK(launch_validate(h, st));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err & 7)
+        return GSR_ERR_INDEX;
+    if (err & 8)
+        return GSR_ERR_NONFINITE;
+
+    // launch geometry
+    h->lanes = h->cfg.lanes_per_star ? h->cfg.lanes_per_star : 8;
+    int64_t gv = (n + kThreads - 1) / kThreads;
+    if (gv > (int64_t)h->nsm * 8) gv = (int64_t)h->nsm * 8;
+    if (gv > kMaxPartials) gv = kMaxPartials;
+    h->grid_vec = (int)(gv < 1 ? 1 : gv);
+    h->grid_rows2 = aprod2_grid(h);
+    if (h->grid_rows2 <= 0)
+        return cuda_fail(cudaGetLastError(), "aprod2 occupancy");
+
+    cudaError_t e = build_solve_graph(h);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "build_solve_graph");
+    return GSR_OK;
+}
+
+extern "C" int gsr_create(void **out, const gsr_dims *d, const uint32_t *star_ptr,
+                          const uint32_t *attoff, const uint16_t *instr, const double *values,
+                          const gsr_config *cfg)
+{
+    if (!out || !d || !star_ptr || !attoff || !instr || !values)
+        return GSR_ERR_ARG;
+    if (d->n_stars < 1 || d->n_dfa < 4 || d->n_instr < kNInstr || d->n_instr > 65536 ||
+        d->n_rows < 1 || d->n_rows >= ((int64_t)1 << 32) - 32)
+        return GSR_ERR_ARG;
+    gsr_config c;
+    if (cfg)
+        c = *cfg;
+    else
+        gsr_config_default(&c);
+    if (c.precision != GSR_PREC_FP64)
+        return GSR_ERR_UNSUPPORTED;
+    if (c.lanes_per_star != 0 && c.lanes_per_star != 4 && c.lanes_per_star != 8 &&
+        c.lanes_per_star != 16 && c.lanes_per_star != 32)
+        return GSR_ERR_ARG;
+    if (!(c.conlim >= 0.0))
+        return GSR_ERR_ARG;
+    gsr_handle_t *h = new (std::nothrow) gsr_handle_t();
+    if (!h)
+        return GSR_ERR_OOM;
+    h->cfg = c;
+    int rc = create_impl(h, d, star_ptr, attoff, instr, values);
+    if (rc != GSR_OK) {
+        release(h);
+        return rc;
+    }
+    *out = h;
+    return GSR_OK;
+}
+
+extern "C" int gsr_destroy(void *hv)
+{
+    release((gsr_handle_t *)hv);
+    return GSR_OK;
+}
+
+extern "C" int gsr_info(void *hv, int64_t *m, int64_t *n, int64_t *bytes)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h)
+        return GSR_ERR_ARG;
+    if (m) *m = h->sys.m;
+    if (n) *n = h->sys.n;
+    if (bytes) *bytes = h->device_bytes;
+    return GSR_OK;
+}
+
+// a device buffer for a caller's pointer: the pointer itself, or a staging
+// buffer owned by the handle
+static int stage(gsr_handle_t *h, double **slot, int64_t count, const double *user,
+                 double **dev, bool copy_in, cudaStream_t st)
+{
+    if (on_device(user)) {
+        *dev = (double *)user;
+        return GSR_OK;
+    }
+    if (!*slot)
+        TRY(dalloc(h, slot, count));
+    *dev = *slot;
+    if (copy_in)
+        CK(cudaMemcpyAsync(*slot, user, count * sizeof(double), cudaMemcpyHostToDevice, st));
+    return GSR_OK;
+}
+
+extern "C" int gsr_aprod1(void *hv, const double *x, double *y, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !x || !y)
+        return GSR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *dx, *dy;
+    TRY(stage(h, &h->d_xstage, h->sys.n, x, &dx, true, st));
+    TRY(stage(h, &h->d_ystage, h->sys.m, y, &dy, true, st));
+    CK(launch_aprod1(h, dx, dy, 0, st));
+    if (dy != y) {
+        CK(cudaMemcpyAsync(y, dy, h->sys.m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return GSR_OK;
+}
+
+extern "C" int gsr_aprod2(void *hv, const double *y, double *x, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !x || !y)
+        return GSR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *dx, *dy;
+    TRY(stage(h, &h->d_ystage, h->sys.m, y, &dy, true, st));
+    TRY(stage(h, &h->d_xstage, h->sys.n, x, &dx, true, st));
+    CK(launch_aprod2(h, dy, dx, kA2Accumulate, st));
+    if (dx != x) {
+        CK(cudaMemcpyAsync(x, dx, h->sys.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return GSR_OK;
+}
+
+extern "C" int gsr_precondition(void *hv, double *p, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !p)
+        return GSR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *dp;
+    TRY(stage(h, &h->d_xstage, h->sys.n, p, &dp, false, st));
+    CK(enqueue_precondition(h, dp, st));
+    if (dp != p) {
+        CK(cudaMemcpyAsync(p, dp, h->sys.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return GSR_OK;
+}
+
+extern "C" int gsr_lsqr_solve(void *hv, const double *b, int itmax, double atol, double btol,
+                              double *x, double *se, gsr_result *out, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !b || !x || itmax < 1 || !(atol >= 0.0) || !(btol >= 0.0))
+        return GSR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *db, *dx, *dse = nullptr;
+    TRY(stage(h, &h->d_bstage, h->sys.m, b, &db, true, st));
+    TRY(stage(h, &h->d_xstage, h->sys.n, x, &dx, false, st));
+    if (se)
+        TRY(stage(h, &h->d_sestage, h->sys.n, se, &dse, false, st));
+    SolveArgs *a = h->h_args;
+    a->b = db;
+    a->x = dx;
+    a->se = dse;
+    a->itmax = itmax;
+    a->atol = atol;
+    a->btol = btol;
+    a->ctol = (h->cfg.conlim > 0.0) ? 1.0 / h->cfg.conlim : 0.0;
+    CK(cudaMemcpyAsync(h->d_args, a, sizeof(SolveArgs), cudaMemcpyHostToDevice, st));
+    CK(cudaGraphLaunch(h->solve_exec, st));
+    CK(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    if (dx != x)
+        CK(cudaMemcpyAsync(x, dx, h->sys.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (se && dse != se)
+        CK(cudaMemcpyAsync(se, dse, h->sys.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const SolveState &s = *h->h_state;
+    if (out) {
+        out->istop = s.istop;
+        out->itn = s.itn;
+        out->rnorm = s.rnorm;
+        out->arnorm = s.arnorm;
+        out->anorm = s.anorm;
+        out->acond = s.acond;
+        out->xnorm = s.xnorm;
+        out->bnorm = s.bnorm;
+    }
+    return s.nonfinite ? GSR_ERR_NONFINITE : GSR_OK;
+}

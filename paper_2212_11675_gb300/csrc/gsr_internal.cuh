@@ -1,0 +1,114 @@
+// Internal declarations of the GB300 PC-LSQR library: device layout of the
+// Gaia observation system, LSQR device state and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gsr.h"
+
+namespace gsr {
+
+constexpr int kNAstro = 5;
+constexpr int kNAtt = 12;
+constexpr int kNInstr = 6;
+constexpr int kNPar = 24;
+constexpr int kThreads = 256;       // block size of every row kernel
+constexpr int kMaxPartials = 4096;  // per-block partial slots of one reduction
+
+// Row record, 16 bytes: attitude offset and the six instrument indices,
+// x = attoff, y = f0 | f1 << 16, z = f2 | f3 << 16, w = f4 | f5 << 16.
+// Device view of the system, passed to kernels by value.
+struct SysView {
+    const uint32_t *star_ptr;  // [S+1]
+    const uint4 *rec;          // [m]
+    const double *val;         // [24][mp] value planes (plane k = nonzero k)
+    int64_t mp;                // plane stride (m rounded up to 32)
+    int64_t S, D, I, m, n;
+    int64_t att0, ins0, glb0;  // first column of each section
+};
+
+// LSQR scalars kept on the device (Paige & Saunders 1982 notation).
+struct SolveState {
+    double alpha, beta;        // current alpha_i, beta_i
+    double beta_new;           // beta_{i+1} from the last aprod1 pass
+    double rhobar, phibar;
+    double rho, cs, sn, phi, theta;  // rotation of the current iteration
+    double anorm2, ddnorm, bnorm;
+    double rnorm, arnorm, anorm, acond, xnorm;
+    double cy;                 // coefficient of the old u in aprod1 (-alpha/beta)
+    double t;                  // rnorm / sqrt(dof) for the standard errors
+    int itn, istop, done, nonfinite;
+};
+
+// Per-solve arguments, read by the graph's kernels from device memory so one
+// instantiated graph serves every call.
+struct SolveArgs {
+    const double *b;
+    double *x, *se;
+    int itmax;
+    double atol, btol, ctol;
+};
+
+// Deterministic grid reduction slots: each kernel writes one partial per
+// block and the last block to finish (ticket counter) sums them in block
+// order, so results do not depend on scheduling.
+struct ReduceSlots {
+    double *partial;     // [kReduceKinds][kMaxPartials]
+    unsigned *counter;   // [kReduceKinds]
+};
+enum ReduceKind { kRedBnorm = 0, kRedU = 1, kRedV = 2, kRedCount = 3 };
+constexpr int kPartialsPerKind = 4 * kMaxPartials;  // up to 4 sums per block
+
+}  // namespace gsr
+
+// Opaque handle behind the C ABI.
+struct gsr_handle_t {
+    int device;
+    int nsm;
+    gsr_config cfg;
+    int lanes;
+    gsr::SysView sys;
+    // device buffers owned by the handle
+    uint32_t *d_star_ptr = nullptr;
+    uint4 *d_rec = nullptr;
+    double *d_val = nullptr;
+    double *d_p = nullptr;              // preconditioner
+    double *d_u = nullptr;              // m
+    double *d_v = nullptr, *d_w = nullptr, *d_z = nullptr, *d_var = nullptr;
+    double *d_q = nullptr, *d_vp = nullptr, *d_vt = nullptr;  // n each
+    double *d_bstage = nullptr, *d_xstage = nullptr, *d_sestage = nullptr, *d_ystage = nullptr;
+    gsr::SolveState *d_state = nullptr;
+    gsr::SolveArgs *d_args = nullptr;
+    double *d_partial = nullptr;
+    unsigned *d_counter = nullptr;
+    int *d_err = nullptr;
+    gsr::SolveState *h_state = nullptr;  // pinned
+    gsr::SolveArgs *h_args = nullptr;    // pinned
+    int64_t device_bytes = 0;
+    // CUDA graph of one whole solve
+    cudaGraphExec_t solve_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int grid_rows = 0, grid_rows2 = 0, grid_vec = 0;
+};
+
+namespace gsr {
+
+// launchers (gsr_kernels.cu)
+cudaError_t launch_aprod1(const gsr_handle_t *h, const double *x, double *y,
+                          int lsqr_mode, cudaStream_t st);
+cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out,
+                          int mode, cudaStream_t st);
+cudaError_t launch_validate(const gsr_handle_t *h, cudaStream_t st);
+cudaError_t launch_planes(const gsr_handle_t *h, const double *rowmajor,
+                          int64_t row0, int64_t nrows, cudaStream_t st);
+cudaError_t launch_pack_rec(const gsr_handle_t *h, const uint32_t *attoff,
+                            const uint16_t *instr, int64_t row0, int64_t nrows,
+                            cudaStream_t st);
+// LSQR pieces (gsr_lsqr.cu)
+cudaError_t build_solve_graph(gsr_handle_t *h);
+cudaError_t launch_precond_finish(const gsr_handle_t *h, double *p, cudaStream_t st);
+
+enum Aprod2Mode { kA2Accumulate = 0, kA2Overwrite = 1, kA2Squares = 2 };
+
+}  // namespace gsr

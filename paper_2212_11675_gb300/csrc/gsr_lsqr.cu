@@ -1,0 +1,374 @@
+// PC-LSQR on the device: preconditioner, LSQR vector updates with the
+// scalar recurrences kept on the GPU, and the CUDA graph of one whole solve.
+//
+// Mathematics (Paige & Saunders 1982, "Algorithm LSQR", damp = 0) on the
+// column-scaled matrix Ap = A diag(p) of the paper's PC-LSQR (§2, §3):
+//   beta_1 u_1 = b, alpha_1 v_1 = Ap^T u_1, w_1 = v_1, z_0 = 0,
+//   phibar_1 = beta_1, rhobar_1 = alpha_1; per iteration i:
+//   beta_{i+1} u_{i+1} = Ap v_i - alpha_i u_i
+//   alpha_{i+1} v_{i+1} = Ap^T u_{i+1} - beta_{i+1} v_i
+//   rho = sqrt(rhobar^2 + beta^2), c = rhobar/rho, s = beta/rho,
+//   theta = s alpha_{i+1}, rhobar = -c alpha_{i+1}, phi = c phibar,
+//   phibar = s phibar, z += (phi/rho) w, var += (w/rho)^2,
+//   w = v_{i+1} - (theta/rho) w.
+// The matrix values are never rescaled: Ap v = A (p o v) and
+// Ap^T u = p o (A^T u), so the row kernels gather vp = p o v and the vector
+// kernels apply p to A^T u.  u is kept unnormalised (u~ = beta u); the
+// aprod 1 pass folds the normalisation into its coefficient -alpha/beta and
+// the vector kernel divides A^T u~ by beta.
+//
+// One iteration = 4 launches: aprod 1 (+ ||u~||^2), aprod 2, vector pass A
+// (v' = p o q / beta - beta v, ||v'||^2, z and var updates, scalar
+// recurrences and stopping rules in the last block), vector pass B
+// (v = v'/alpha, vp, w).  The loop is a conditional WHILE graph node whose
+// flag the last block of pass A clears when LSQR stops.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "gsr_internal.cuh"
+#include "gsr_reduce.cuh"
+
+namespace gsr {
+
+constexpr int kIstopNonfinite = 8;
+
+__device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+// p_j = 1/sqrt(sum of squares), 1 for an empty column (in place)
+__global__ void k_precond_finish(double *p, int64_t n)
+{
+    for (int64_t j = gtid(); j < n; j += gstride()) {
+        const double s = p[j];
+        p[j] = (s > 0.0) ? 1.0 / sqrt(s) : 1.0;
+    }
+}
+
+__global__ void k_zero(double *a, int64_t n)
+{
+    for (int64_t j = gtid(); j < n; j += gstride())
+        a[j] = 0.0;
+}
+
+// u~ = b, beta_1 = ||b||; state reset
+__global__ void __launch_bounds__(kThreads)
+k_init_u(const SolveArgs *args, double *u, int64_t m, SolveState *st, double *partial,
+         unsigned *counter)
+{
+    const double *b = args->b;
+    double acc[1] = {0.0};
+    for (int64_t i = gtid(); i < m; i += gstride()) {
+        const double bi = b[i];
+        u[i] = bi;
+        acc[0] = fma(bi, bi, acc[0]);
+    }
+    if (grid_reduce<1>(acc, partial, counter) && threadIdx.x == 0) {
+        SolveState s = {};
+        s.beta = sqrt(acc[0]);
+        s.bnorm = s.beta;
+        s.rnorm = s.beta;
+        s.nonfinite = !isfinite(s.beta);
+        *st = s;
+    }
+}
+
+// v' = p o q / beta_1, alpha_1 = ||v'||; decides istop = 0 (x = 0 exact)
+__global__ void __launch_bounds__(kThreads)
+k_init_v(const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ v,
+         int64_t n, SolveState *st, double *partial, unsigned *counter,
+         cudaGraphConditionalHandle loop)
+{
+    const double beta = st->beta;
+    const double ib = (beta > 0.0) ? 1.0 / beta : 0.0;
+    double acc[1] = {0.0};
+    for (int64_t j = gtid(); j < n; j += gstride()) {
+        const double t = p[j] * q[j] * ib;
+        v[j] = t;
+        acc[0] = fma(t, t, acc[0]);
+    }
+    if (grid_reduce<1>(acc, partial, counter) && threadIdx.x == 0) {
+        const double alpha = sqrt(acc[0]);
+        st->alpha = alpha;
+        st->rhobar = alpha;
+        st->phibar = beta;
+        st->arnorm = alpha * beta;
+        st->cy = (beta > 0.0) ? -alpha / beta : 0.0;
+        if (!isfinite(alpha) || st->nonfinite) {
+            st->nonfinite = 1;
+            st->istop = kIstopNonfinite;
+            st->done = 1;
+        } else if (alpha * beta == 0.0) {
+            st->istop = 0;
+            st->done = 1;
+        }
+        if (st->done)
+            cudaGraphSetConditional(loop, 0u);
+    }
+}
+
+// v = v'/alpha, vp = p o v, w = v (first) or v - (theta/rho) w; clears the
+// non-astrometric part of q for the next aprod 2
+__global__ void k_vec_b(const double *__restrict__ p, double *__restrict__ v,
+                        double *__restrict__ vp, double *__restrict__ w,
+                        double *__restrict__ q, int64_t n, int64_t att0,
+                        const SolveState *st, int first, double *z, double *var)
+{
+    const double alpha = st->alpha;
+    const double ia = (alpha > 0.0) ? 1.0 / alpha : 1.0;
+    const double t2 = first ? 0.0 : -st->theta / st->rho;
+    for (int64_t j = gtid(); j < n; j += gstride()) {
+        const double vj = v[j] * ia;
+        v[j] = vj;
+        vp[j] = p[j] * vj;
+        w[j] = first ? vj : fma(t2, w[j], vj);
+        if (j >= att0)
+            q[j] = 0.0;
+        if (first) {
+            z[j] = 0.0;
+            var[j] = 0.0;
+        }
+    }
+}
+
+__device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm2,
+                             double dd, double zz, cudaGraphConditionalHandle loop)
+{
+    SolveState s = *st;
+    const double beta = s.beta_new;
+    const double rho = sqrt(s.rhobar * s.rhobar + beta * beta);
+    const double c = s.rhobar / rho;
+    const double sn = beta / rho;
+    double alpha = s.alpha;
+    if (beta > 0.0) {
+        s.anorm2 += s.alpha * s.alpha + beta * beta;
+        alpha = sqrt(vnorm2);
+    }
+    const double phi = c * s.phibar;
+    s.theta = sn * alpha;
+    s.rhobar = -c * alpha;
+    s.phibar = sn * s.phibar;
+    const double tau = sn * phi;
+    s.rho = rho;
+    s.cs = c;
+    s.sn = sn;
+    s.phi = phi;
+    s.alpha = alpha;
+    s.beta = beta;
+    s.cy = (beta > 0.0) ? -alpha / beta : 0.0;
+    s.ddnorm += dd;
+    s.xnorm = sqrt(zz);
+    s.anorm = sqrt(s.anorm2);
+    s.acond = s.anorm * sqrt(s.ddnorm);
+    s.rnorm = s.phibar;
+    s.arnorm = alpha * fabs(tau);
+    s.itn += 1;
+
+    const double test1 = s.rnorm / s.bnorm;
+    const double test2 = (s.anorm * s.rnorm != 0.0) ? s.arnorm / (s.anorm * s.rnorm) : INFINITY;
+    const double test3 = 1.0 / s.acond;
+    const double t1 = test1 / (1.0 + s.anorm * s.xnorm / s.bnorm);
+    const double rtol = args->btol + args->atol * s.anorm * s.xnorm / s.bnorm;
+    int istop = 0;
+    if (s.itn >= args->itmax) istop = 7;
+    if (1.0 + test3 <= 1.0) istop = 6;
+    if (1.0 + test2 <= 1.0) istop = 5;
+    if (1.0 + t1 <= 1.0) istop = 4;
+    if (test3 <= args->ctol) istop = 3;
+    if (test2 <= args->atol) istop = 2;
+    if (test1 <= rtol) istop = 1;
+    const bool bad = !isfinite(rho) || !isfinite(alpha) || !isfinite(s.phibar) ||
+                     !isfinite(s.xnorm) || !isfinite(s.ddnorm) || rho == 0.0;
+    if (bad) {
+        s.nonfinite = 1;
+        istop = kIstopNonfinite;
+    }
+    s.istop = istop;
+    if (istop != 0) {
+        s.done = 1;
+        cudaGraphSetConditional(loop, 0u);
+    }
+    *st = s;
+}
+
+// pass A: v' = p o q / beta - beta v (in place in v), z += (phi/rho) w,
+// var += (w/rho)^2, reductions of ||v'||^2, sum (w/rho)^2, ||z||^2; the
+// last block advances the scalar recurrences and applies the stopping rules
+__global__ void __launch_bounds__(kThreads)
+k_vec_a(const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ v,
+        const double *__restrict__ w, double *__restrict__ z, double *__restrict__ var,
+        int64_t n, SolveState *st, const SolveArgs *args, double *partial,
+        unsigned *counter, cudaGraphConditionalHandle loop)
+{
+    const double beta = st->beta_new;
+    const double rhobar = st->rhobar;
+    const double rho = sqrt(rhobar * rhobar + beta * beta);
+    const double phi = (rhobar / rho) * st->phibar;
+    const double t1 = phi / rho;
+    const double irho = 1.0 / rho;
+    const bool upd = beta > 0.0;
+    const double ib = upd ? 1.0 / beta : 0.0;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = gtid(); j < n; j += gstride()) {
+        if (upd) {
+            const double vn = fma(p[j] * q[j], ib, -beta * v[j]);
+            v[j] = vn;
+            acc[0] = fma(vn, vn, acc[0]);
+        }
+        const double wj = w[j];
+        const double d = wj * irho;
+        acc[1] = fma(d, d, acc[1]);
+        var[j] = fma(d, d, var[j]);
+        const double zj = fma(t1, wj, z[j]);
+        z[j] = zj;
+        acc[2] = fma(zj, zj, acc[2]);
+    }
+    if (grid_reduce<3>(acc, partial, counter) && threadIdx.x == 0)
+        lsqr_scalars(st, args, acc[0], acc[1], acc[2], loop);
+}
+
+// x = p o z, se = p o sqrt(var) * rnorm / sqrt(dof)
+__global__ void k_finalize(const double *__restrict__ p, const double *__restrict__ z,
+                           const double *__restrict__ var, int64_t n, int64_t m,
+                           const SolveState *st, const SolveArgs *args)
+{
+    double *x = args->x;
+    double *se = args->se;
+    const double dof = (m > n) ? (double)(m - n) : 1.0;
+    const double t = st->rnorm / sqrt(dof);
+    for (int64_t j = gtid(); j < n; j += gstride()) {
+        x[j] = p[j] * z[j];
+        if (se)
+            se[j] = p[j] * t * sqrt(var[j]);
+    }
+}
+
+cudaError_t launch_precond_finish(const gsr_handle_t *h, double *p, cudaStream_t st)
+{
+    k_precond_finish<<<h->grid_vec, kThreads, 0, st>>>(p, h->sys.n);
+    return cudaGetLastError();
+}
+
+// column sums of squares -> p (the non-astrometric part must start at zero)
+static cudaError_t enqueue_precond(const gsr_handle_t *h, double *p, cudaStream_t st)
+{
+    const int64_t n = h->sys.n, att0 = h->sys.att0;
+    k_zero<<<h->grid_vec, kThreads, 0, st>>>(p + att0, n - att0);
+    cudaError_t e = launch_aprod2(h, nullptr, p, kA2Squares, st);
+    if (e != cudaSuccess)
+        return e;
+    return launch_precond_finish(h, p, st);
+}
+
+cudaError_t enqueue_precondition(const gsr_handle_t *h, double *p, cudaStream_t st)
+{
+    return enqueue_precond(h, p, st);
+}
+
+static cudaError_t find_leaf(cudaGraph_t g, cudaGraphNode_t *leaf)
+{
+    size_t nn = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &nn);
+    if (e != cudaSuccess || nn == 0)
+        return e != cudaSuccess ? e : cudaErrorInvalidValue;
+    cudaGraphNode_t *nodes = new cudaGraphNode_t[nn];
+    e = cudaGraphGetNodes(g, nodes, &nn);
+    int found = 0;
+    for (size_t i = 0; e == cudaSuccess && i < nn; i++) {
+        size_t nd = 0;
+        e = cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd);
+        if (e == cudaSuccess && nd == 0) {
+            *leaf = nodes[i];
+            found++;
+        }
+    }
+    delete[] nodes;
+    if (e == cudaSuccess && found != 1)
+        e = cudaErrorInvalidValue;
+    return e;
+}
+
+#define GSR_TRY(x)                      \
+    do {                                \
+        cudaError_t e_ = (x);           \
+        if (e_ != cudaSuccess) {        \
+            err = e_;                   \
+            goto fail;                  \
+        }                               \
+    } while (0)
+
+// Build and instantiate the graph of one whole solve:
+//   [precondition, u = b, q = A^T u, v_1, w_1]  ->  WHILE(flag) { iteration }
+//   ->  [x = p o z, se]
+cudaError_t build_solve_graph(gsr_handle_t *h)
+{
+    cudaError_t err = cudaSuccess;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle loop;
+    cudaGraphNode_t pre_leaf, wnode;
+    cudaGraphNodeParams cp = {};
+    cudaGraph_t body;
+    cudaStream_t s = h->cap_stream;
+    const SysView &A = h->sys;
+    double *part = h->d_partial;
+    unsigned *cnt = h->d_counter;
+
+    GSR_TRY(cudaGraphCreate(&g, 0));
+    GSR_TRY(cudaGraphConditionalHandleCreate(&loop, g, 1u, cudaGraphCondAssignDefault));
+
+    // prologue
+    GSR_TRY(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    enqueue_precond(h, h->d_p, s);
+    k_init_u<<<h->grid_vec, kThreads, 0, s>>>(h->d_args, h->d_u, A.m, h->d_state,
+                                               part + kRedBnorm * kPartialsPerKind, cnt + kRedBnorm);
+    k_zero<<<h->grid_vec, kThreads, 0, s>>>(h->d_q + A.att0, A.n - A.att0);
+    launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
+    k_init_v<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, A.n, h->d_state,
+                                               part + kRedV * kPartialsPerKind, cnt + kRedV, loop);
+    k_vec_b<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_v, h->d_vp, h->d_w, h->d_q, A.n, A.att0,
+                                              h->d_state, 1, h->d_z, h->d_var);
+    GSR_TRY(cudaStreamEndCapture(s, &g));
+    GSR_TRY(find_leaf(g, &pre_leaf));
+
+    // WHILE node: one LSQR iteration per trip
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    GSR_TRY(cudaGraphAddNode(&wnode, g, &pre_leaf, nullptr, 1, &cp));
+    body = cp.conditional.phGraph_out[0];
+    GSR_TRY(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_aprod1(h, h->d_vp, h->d_u, 1, s);
+    launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
+    k_vec_a<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, h->d_w, h->d_z, h->d_var, A.n,
+                                              h->d_state, h->d_args, part + kRedV * kPartialsPerKind,
+                                              cnt + kRedV, loop);
+    k_vec_b<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_v, h->d_vp, h->d_w, h->d_q, A.n, A.att0,
+                                              h->d_state, 0, nullptr, nullptr);
+    GSR_TRY(cudaStreamEndCapture(s, &body));
+
+    // epilogue
+    GSR_TRY(cudaStreamBeginCaptureToGraph(s, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    k_finalize<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_z, h->d_var, A.n, A.m, h->d_state,
+                                                 h->d_args);
+    GSR_TRY(cudaStreamEndCapture(s, &g));
+
+    GSR_TRY(cudaGraphInstantiate(&h->solve_exec, g, 0));
+    cudaGraphDestroy(g);
+    return cudaSuccess;
+fail:
+    {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(s, &junk);
+            if (junk && junk != g)
+                cudaGraphDestroy(junk);
+        }
+    }
+    if (g)
+        cudaGraphDestroy(g);
+    cudaGetLastError();
+    return err;
+}
+
+}  // namespace gsr

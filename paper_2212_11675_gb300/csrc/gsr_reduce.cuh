@@ -1,0 +1,77 @@
+// Deterministic block and grid reductions.
+//
+// grid_reduce: every block reduces its K values (fixed tree order), writes
+// them to partial[k * kMaxPartials + blockIdx.x], and takes a ticket; the
+// block that takes the last ticket sums the partials in block order and
+// returns true with the totals in v (all its threads).  The ticket counter is
+// reset by that block, so the same slots serve the next launch.  There is no
+// waiting: blocks that are not last simply return false.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Sum over the block; the result is valid in every thread.  Deterministic.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K])
+{
+    __shared__ double sh[K][kThreads / 32];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const double w = warp_sum(v[k]);
+        if ((threadIdx.x & 31) == 0)
+            sh[k][threadIdx.x >> 5] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; w++)
+            t += sh[k][w];
+        v[k] = t;
+    }
+    __syncthreads();
+}
+
+template <int K>
+__device__ bool grid_reduce(double (&v)[K], double *partial, unsigned *counter)
+{
+    __shared__ bool am_last;
+    block_sum<K>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            partial[k * kMaxPartials + blockIdx.x] = v[k];
+        __threadfence();
+        const unsigned ticket = atomicAdd(counter, 1u);
+        am_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last)
+        return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double t = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            t += __ldcg(partial + k * kMaxPartials + b);
+        v[k] = t;
+    }
+    block_sum<K>(v);
+    if (threadIdx.x == 0)
+        *counter = 0u;
+    return true;
+}
+
+}  // namespace gsr

@@ -1,0 +1,148 @@
+"""Python face of the C ABI: a Solver owning one gsr handle.
+
+Vectors may be CUDA tensors (device pointers are passed straight through) or
+NumPy arrays (host pointers: the library stages them through device memory
+inside the call).  PyTorch only provides device memory and streams here.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import Config, Dims, Result, check, lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(a):
+    """(pointer, keepalive) of a CUDA tensor or a host NumPy array."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data), a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), a
+    raise TypeError("expected a numpy array or a torch tensor, got %r" % type(a))
+
+
+def _check_vec(a, n, name, dtype=np.float64):
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or a.size != n:
+            raise ValueError("%s must be %s[%d]" % (name, np.dtype(dtype).name, n))
+    else:
+        torch = _torch()
+        want = {np.float64: torch.float64}[dtype]
+        if a.dtype != want or a.numel() != n:
+            raise ValueError("%s must be %s[%d]" % (name, want, n))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            torch = _torch()
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Solver:
+    """PC-LSQR solver of one Gaia observation system (paper §3 structure)."""
+
+    def __init__(self, system, conlim: float = 1e8, lanes_per_star: int = 0,
+                 validate: bool = True, precision: int = _lib.GSR_PREC_FP64):
+        L = lib()
+        self._h = ctypes.c_void_p()
+        d = Dims(system.n_stars, system.n_dfa, system.n_instr, int(system.m))
+        cfg = Config()
+        L.gsr_config_default(ctypes.byref(cfg))
+        cfg.conlim = conlim
+        cfg.lanes_per_star = lanes_per_star
+        cfg.validate = 1 if validate else 0
+        cfg.precision = precision
+        arrs = []
+        for a, dt in ((system.star_ptr, np.uint32), (system.attoff, np.uint32),
+                      (system.instr, np.uint16), (system.values, np.float64)):
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=dt)
+            arrs.append(a)
+        ptrs = [_ptr(a)[0] for a in arrs]
+        check(L.gsr_create(ctypes.byref(self._h), ctypes.byref(d), *ptrs, ctypes.byref(cfg)),
+              "gsr_create")
+        self.n_stars, self.n_dfa, self.n_instr = system.n_stars, system.n_dfa, system.n_instr
+        m, n, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(L.gsr_info(self._h, ctypes.byref(m), ctypes.byref(n), ctypes.byref(b)), "gsr_info")
+        self.m, self.n, self.device_bytes = m.value, n.value, b.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().gsr_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def aprod1(self, x, y, stream=None):
+        """y += A x (paper Alg. 1); returns y."""
+        _check_vec(x, self.n, "x")
+        _check_vec(y, self.m, "y")
+        check(lib().gsr_aprod1(self._h, _ptr(x)[0], _ptr(y)[0], _stream(stream)), "gsr_aprod1")
+        return y
+
+    def aprod2(self, y, x, stream=None):
+        """x += A^T y (paper Alg. 2); returns x."""
+        _check_vec(y, self.m, "y")
+        _check_vec(x, self.n, "x")
+        check(lib().gsr_aprod2(self._h, _ptr(y)[0], _ptr(x)[0], _stream(stream)), "gsr_aprod2")
+        return x
+
+    def precondition(self, p, stream=None):
+        """p = 1/||A(:,j)|| (1 for an empty column); returns p."""
+        _check_vec(p, self.n, "p")
+        check(lib().gsr_precondition(self._h, _ptr(p)[0], _stream(stream)), "gsr_precondition")
+        return p
+
+    def lsqr_solve(self, b, itmax, atol=1e-12, btol=1e-12, x=None, se=None, stream=None,
+                   want_se=True):
+        """PC-LSQR: returns (x, se, result dict).  Output buffers default to
+        arrays on the same side (host or device) as b."""
+        _check_vec(b, self.m, "b")
+        if x is None:
+            x = np.empty(self.n) if isinstance(b, np.ndarray) else _torch().empty(
+                self.n, dtype=b.dtype, device=b.device)
+        if se is None and want_se:
+            se = np.empty(self.n) if isinstance(b, np.ndarray) else _torch().empty(
+                self.n, dtype=b.dtype, device=b.device)
+        _check_vec(x, self.n, "x")
+        if se is not None:
+            _check_vec(se, self.n, "se")
+        res = Result()
+        rc = lib().gsr_lsqr_solve(self._h, _ptr(b)[0], int(itmax), float(atol), float(btol),
+                                  _ptr(x)[0], _ptr(se)[0] if se is not None else None,
+                                  ctypes.byref(res), _stream(stream))
+        check(rc, "gsr_lsqr_solve")
+        return x, se, res.as_dict()

@@ -1,0 +1,42 @@
+"""The C-ABI library builds, loads and exports every function include/gsr.h
+declares (no GPU needed: nothing here launches a kernel)."""
+import os
+import re
+
+from paper_2212_11675_gb300 import _lib
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+def declared():
+    names = set()
+    for f in os.listdir(HDR):
+        if f.endswith(".h"):
+            txt = open(os.path.join(HDR, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(gsr_\w+)\s*\(", txt))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for must in ("gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2", "gsr_lsqr_solve",
+                 "gsr_precondition", "gsr_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.lib()
+    missing = [n for n in sorted(declared()) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(_lib.EXPORTS) <= declared()
+
+
+def test_strerror_and_null_handling_without_gpu():
+    L = _lib.lib()
+    assert L.gsr_strerror(_lib.GSR_ERR_INDEX) == b"matrix structure out of range"
+    assert L.gsr_strerror(12345) == b"unknown error"
+    # argument checks happen before any CUDA call
+    assert L.gsr_aprod1(None, None, None, None) == _lib.GSR_ERR_ARG
+    assert L.gsr_lsqr_solve(None, None, 1, 0.0, 0.0, None, None, None, None) == _lib.GSR_ERR_ARG
+    assert L.gsr_destroy(None) == _lib.GSR_OK
