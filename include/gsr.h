@@ -138,6 +138,34 @@ int gsr_lsqr_solve(void *h, const double *b, int itmax, double atol,
                    double btol, double *x, double *se, gsr_result *out,
                    void *stream);
 
+/*
+ * y[m] = A x[n] + cy * y[m] and *ynorm = ||y||_2 (the first half of a
+ * Golub-Kahan step with cy = -alpha), without allocating anything.  The
+ * paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory at call time (another component owns the
+ * device-memory budget through its own pool, or a cudaMalloc would
+ * synchronise the device where the caller cannot afford it).
+ *  - x and y must be device pointers (host vectors would need staging
+ *    memory): otherwise GSR_ERR_ARG.  ynorm may be a device pointer or a host
+ *    pointer; with a host pointer the call synchronises the stream.
+ *  - Scratch: one file-scope device array of 36 KiB (a state slot, one
+ *    8-byte partial sum per thread block, a ticket counter), held by every
+ *    GPU that loads the library until the process exits.  The kernel never
+ *    uses more than 4096 blocks, whatever the system size; a launch that
+ *    would need more partial sums than the array holds is rejected with
+ *    GSR_ERR_ARG before anything runs.
+ *  - The first call on a device looks up the array's device address (with
+ *    the handle's device made current for the call); make that first call
+ *    before any stream capture that might include later calls.
+ *  - All calls share the array and it keeps the last call's contents (the
+ *    counter is cleared at the start of every call).  Calls whose work
+ *    overlaps on the GPU (different streams, or different handles at the
+ *    same time) race on it: order them on one stream.
+ *  - No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+int gsr_aprod1_norm_noalloc(void *h, const double *x, double *y, double cy,
+                            double *ynorm, void *stream);
+
 /* Text of the last CUDA failure seen by this host thread ("" if none). */
 const char *gsr_last_error(void);
 

@@ -26,6 +26,7 @@ GSR_PREC_FP64 = 0
 EXPORTS = (
     "gsr_config_default", "gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
     "gsr_precondition", "gsr_lsqr_solve", "gsr_last_error", "gsr_info", "gsr_strerror",
+    "gsr_aprod1_norm_noalloc",
 )
 
 
@@ -87,12 +88,14 @@ def lib():
             L.gsr_aprod2.argtypes = [P, P, P, P]
             L.gsr_precondition.argtypes = [P, P, P]
             L.gsr_lsqr_solve.argtypes = [P, P, I, D, D, P, P, ctypes.POINTER(Result), P]
+            L.gsr_aprod1_norm_noalloc.argtypes = [P, P, P, D, P, P]
             L.gsr_last_error.restype = ctypes.c_char_p
             L.gsr_strerror.argtypes = [I]
             L.gsr_strerror.restype = ctypes.c_char_p
             L.gsr_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
             for name in ("gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
-                         "gsr_precondition", "gsr_lsqr_solve", "gsr_info"):
+                         "gsr_precondition", "gsr_lsqr_solve", "gsr_info",
+                         "gsr_aprod1_norm_noalloc"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib

@@ -409,3 +409,32 @@ int aprod2_grid(const gsr_handle_t *h)
 }
 
 }  // namespace gsr
+
+namespace gsr {
+
+// aprod 1 in its LSQR form (y = A x + cy y, ||y||^2 reduced into
+// st->beta_new) with the caller's choice of state and reduction slots
+template <int G>
+static cudaError_t a1_with_slots(const gsr_handle_t *h, const double *x, double *y,
+                                 SolveState *st_slot, double *partial, unsigned *counter,
+                                 cudaStream_t st)
+{
+    k_aprod1<G, 1><<<row_grid(h, G), kThreads, 0, st>>>(h->sys, x, y, st_slot, partial, counter);
+    return cudaGetLastError();
+}
+
+int aprod1_grid_blocks(const gsr_handle_t *h) { return row_grid(h, h->lanes); }
+
+cudaError_t launch_aprod1_with_slots(const gsr_handle_t *h, const double *x, double *y,
+                                     SolveState *st_slot, double *partial, unsigned *counter,
+                                     cudaStream_t st)
+{
+    switch (h->lanes) {
+    case 4: return a1_with_slots<4>(h, x, y, st_slot, partial, counter, st);
+    case 8: return a1_with_slots<8>(h, x, y, st_slot, partial, counter, st);
+    case 16: return a1_with_slots<16>(h, x, y, st_slot, partial, counter, st);
+    default: return a1_with_slots<32>(h, x, y, st_slot, partial, counter, st);
+    }
+}
+
+}  // namespace gsr
