@@ -185,6 +185,10 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the solve's kernels from the host (for ncu, which cannot "
+                         "profile kernels inside graphs with conditional nodes)")
+    ap.add_argument("--lanes", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -206,7 +210,7 @@ def main():
     sys_, seed = make_system(args.workload, rank)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    solver = Solver(sys_, conlim=0.0)
+    solver = Solver(sys_, conlim=0.0, force_itmax=True, eager=args.eager, lanes_per_star=args.lanes)
     # right-hand side b = A x_true + noise, built on the device
     xt = torch.tensor(gen.x_true(sys_, seed), device=dev)
     b = torch.tensor(gen.noise(sys_, seed + 1), device=dev)

@@ -69,6 +69,15 @@ typedef struct {
     int lanes_per_star; /* threads cooperating on one star in the row kernels:
                            4, 8, 16 or 32; 0 = library choice */
     int validate;       /* nonzero: gsr_create checks every index and value */
+    int force_itmax;    /* nonzero: only itmax (or a non-finite value) ends
+                           gsr_lsqr_solve; the stopping rules are evaluated
+                           and reported in istop only at the end.  Used to run
+                           a fixed iteration count */
+    int eager;          /* nonzero: gsr_lsqr_solve launches every kernel from
+                           the host and reads the stop flag back after each
+                           iteration, instead of running its CUDA graph (for
+                           profilers that cannot see kernels inside graphs
+                           with conditional nodes); same arithmetic */
 } gsr_config;
 
 typedef struct {
@@ -88,7 +97,8 @@ typedef struct {
     double bnorm;  /* ||b|| */
 } gsr_result;
 
-/* Fill cfg with the defaults (FP64, conlim 1e8, automatic lanes, validate). */
+/* Fill cfg with the defaults (FP64, conlim 1e8, automatic lanes, validate,
+ * stopping rules on). */
 void gsr_config_default(gsr_config *cfg);
 
 /*

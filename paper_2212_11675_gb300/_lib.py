@@ -37,7 +37,8 @@ class Dims(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("conlim", ctypes.c_double),
-                ("lanes_per_star", ctypes.c_int), ("validate", ctypes.c_int)]
+                ("lanes_per_star", ctypes.c_int), ("validate", ctypes.c_int),
+                ("force_itmax", ctypes.c_int), ("eager", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "gsr_internal.cuh"
 
@@ -109,7 +110,8 @@ static void release(gsr_handle_t *h)
         cudaGraphExecDestroy(h->solve_exec);
     if (h->cap_stream)
         cudaStreamDestroy(h->cap_stream);
-    void *dev[] = {h->d_star_ptr, h->d_rec, h->d_val, h->d_p, h->d_u, h->d_v, h->d_w, h->d_z,
+    void *dev[] = {h->d_star_ptr, h->d_rec, h->d_val, h->d_tile_star, h->d_tval, h->d_perm,
+                   h->d_seg, h->d_attS, h->d_p, h->d_u, h->d_v, h->d_w, h->d_z,
                    h->d_var, h->d_q, h->d_vp, h->d_vt, h->d_bstage, h->d_xstage, h->d_sestage,
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err};
     for (void *p : dev)
@@ -141,10 +143,17 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     A.att0 = kNAstro * S;
     A.ins0 = A.att0 + 3 * D;
     A.glb0 = A.ins0 + I;
+    A.nseg = D - 3;
+    const int64_t ntiles = (m + 31) / 32;
 
     TRY(dalloc(h, &h->d_star_ptr, S + 1));
     TRY(dalloc(h, &h->d_rec, m));
     TRY(dalloc(h, &h->d_val, kNPar * mp));
+    TRY(dalloc(h, &h->d_tile_star, ntiles));
+    TRY(dalloc(h, &h->d_tval, (int64_t)kNAtt * mp));
+    TRY(dalloc(h, &h->d_perm, m));
+    TRY(dalloc(h, &h->d_seg, A.nseg + 1));
+    TRY(dalloc(h, &h->d_attS, A.nseg * kNAtt));
     TRY(dalloc(h, &h->d_p, n));
     TRY(dalloc(h, &h->d_u, m));
     TRY(dalloc(h, &h->d_v, n));
@@ -166,6 +175,10 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     A.star_ptr = h->d_star_ptr;
     A.rec = h->d_rec;
     A.val = h->d_val;
+    A.tile_star = h->d_tile_star;
+    A.tval = h->d_tval;
+    A.perm = h->d_perm;
+    A.seg = h->d_seg;
 
     CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     cudaStream_t st = h->cap_stream;
@@ -234,8 +247,40 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     if (err & 8)
         return GSR_ERR_NONFINITE;
 
+    // attitude copy sorted by offset: a stable counting sort on the host
+    // (row order kept inside every offset, so the sums have a fixed order)
+    {
+        std::vector<uint32_t> att_host;
+        const uint32_t *ao = attoff;
+        if (on_device(attoff)) {
+            att_host.resize((size_t)m);
+            CK(cudaMemcpy(att_host.data(), attoff, m * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            ao = att_host.data();
+        }
+        std::vector<uint32_t> seg((size_t)A.nseg + 1, 0), perm((size_t)m);
+        for (int64_t i = 0; i < m; i++) {
+            if ((int64_t)ao[i] >= A.nseg)
+                return GSR_ERR_INDEX;
+            seg[ao[i] + 1]++;
+        }
+        for (int64_t o = 0; o < A.nseg; o++)
+            seg[o + 1] += seg[o];
+        std::vector<uint32_t> pos(seg.begin(), seg.end() - 1);
+        for (int64_t i = 0; i < m; i++)
+            perm[pos[ao[i]]++] = (uint32_t)i;
+        CK(cudaMemcpy(h->d_perm, perm.data(), m * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->d_seg, seg.data(), (A.nseg + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
+    CK(launch_gather_att(h, st));
+    CK(launch_tile_star(h, st));
+    CK(cudaStreamSynchronize(st));
+
     // launch geometry
-    h->lanes = h->cfg.lanes_per_star ? h->cfg.lanes_per_star : 8;
+    h->lanes = h->cfg.lanes_per_star ? h->cfg.lanes_per_star : 16;
+    h->grid_rows = aprod1_grid(h);
+    if (h->grid_rows <= 0)
+        return cuda_fail(cudaGetLastError(), "aprod1 occupancy");
+    h->grid_att = h->nsm * 8;
     int64_t gv = (n + kThreads - 1) / kThreads;
     if (gv > (int64_t)h->nsm * 8) gv = (int64_t)h->nsm * 8;
     if (gv > kMaxPartials) gv = kMaxPartials;
@@ -385,11 +430,26 @@ extern "C" int gsr_lsqr_solve(void *hv, const double *b, int itmax, double atol,
     a->x = dx;
     a->se = dse;
     a->itmax = itmax;
+    a->force_itmax = h->cfg.force_itmax ? 1 : 0;
     a->atol = atol;
     a->btol = btol;
     a->ctol = (h->cfg.conlim > 0.0) ? 1.0 / h->cfg.conlim : 0.0;
     CK(cudaMemcpyAsync(h->d_args, a, sizeof(SolveArgs), cudaMemcpyHostToDevice, st));
-    CK(cudaGraphLaunch(h->solve_exec, st));
+    if (h->cfg.eager) {
+        // every launch from the host, the loop flag read back after each step
+        CK(enqueue_prologue(h, st, 0, 0));
+        CK(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int it = 0; it < itmax && !h->h_state->done; it++) {
+            CK(enqueue_iteration(h, st, 0, 0));
+            CK(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
+                               st));
+            CK(cudaStreamSynchronize(st));
+        }
+        CK(enqueue_epilogue(h, st));
+    } else {
+        CK(cudaGraphLaunch(h->solve_exec, st));
+    }
     CK(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
     if (dx != x)
         CK(cudaMemcpyAsync(x, dx, h->sys.n * sizeof(double), cudaMemcpyDeviceToHost, st));

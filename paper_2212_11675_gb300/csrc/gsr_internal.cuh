@@ -23,9 +23,16 @@ struct SysView {
     const uint32_t *star_ptr;  // [S+1]
     const uint4 *rec;          // [m]
     const double *val;         // [24][mp] value planes (plane k = nonzero k)
+    const uint32_t *tile_star; // [ceil(m/32)] star of the first row of each 32-row tile
+    // attitude values re-ordered by attitude offset (stable in the row index):
+    // entry e is row perm[e]; offset o owns entries seg[o] .. seg[o+1]-1
+    const double *tval;        // [12][mp]
+    const uint32_t *perm;      // [m]
+    const uint32_t *seg;       // [D-2]
     int64_t mp;                // plane stride (m rounded up to 32)
     int64_t S, D, I, m, n;
     int64_t att0, ins0, glb0;  // first column of each section
+    int64_t nseg;              // D-3 attitude offsets
 };
 
 // LSQR scalars kept on the device (Paige & Saunders 1982 notation).
@@ -47,6 +54,7 @@ struct SolveArgs {
     const double *b;
     double *x, *se;
     int itmax;
+    int force_itmax;  // only itmax ends the loop
     double atol, btol, ctol;
 };
 
@@ -73,6 +81,10 @@ struct gsr_handle_t {
     uint32_t *d_star_ptr = nullptr;
     uint4 *d_rec = nullptr;
     double *d_val = nullptr;
+    uint32_t *d_tile_star = nullptr;
+    double *d_tval = nullptr;
+    uint32_t *d_perm = nullptr, *d_seg = nullptr;
+    double *d_attS = nullptr;           // [nseg][12] attitude segment sums
     double *d_p = nullptr;              // preconditioner
     double *d_u = nullptr;              // m
     double *d_v = nullptr, *d_w = nullptr, *d_z = nullptr, *d_var = nullptr;
@@ -89,7 +101,7 @@ struct gsr_handle_t {
     // CUDA graph of one whole solve
     cudaGraphExec_t solve_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
-    int grid_rows = 0, grid_rows2 = 0, grid_vec = 0;
+    int grid_rows = 0, grid_rows2 = 0, grid_vec = 0, grid_att = 0;
 };
 
 namespace gsr {
@@ -105,8 +117,16 @@ cudaError_t launch_planes(const gsr_handle_t *h, const double *rowmajor,
 cudaError_t launch_pack_rec(const gsr_handle_t *h, const uint32_t *attoff,
                             const uint16_t *instr, int64_t row0, int64_t nrows,
                             cudaStream_t st);
+cudaError_t launch_tile_star(const gsr_handle_t *h, cudaStream_t st);
+cudaError_t launch_gather_att(const gsr_handle_t *h, cudaStream_t st);
+int aprod1_grid(const gsr_handle_t *h);
 // LSQR pieces (gsr_lsqr.cu)
 cudaError_t build_solve_graph(gsr_handle_t *h);
+cudaError_t enqueue_prologue(const gsr_handle_t *h, cudaStream_t s,
+                             cudaGraphConditionalHandle loop, int in_graph);
+cudaError_t enqueue_iteration(const gsr_handle_t *h, cudaStream_t s,
+                              cudaGraphConditionalHandle loop, int in_graph);
+cudaError_t enqueue_epilogue(const gsr_handle_t *h, cudaStream_t s);
 cudaError_t launch_precond_finish(const gsr_handle_t *h, double *p, cudaStream_t st);
 
 enum Aprod2Mode { kA2Accumulate = 0, kA2Overwrite = 1, kA2Squares = 2 };

@@ -3,16 +3,26 @@
 // aprod 1 (paper Alg. 1): y_i (+)= sum_k A_ik x_col(i,k)
 // aprod 2 (paper Alg. 2): x_col(i,k) += A_ik y_i
 //
-// Work decomposition: rows are grouped by star (§3), so a group of G lanes
-// of one warp owns one star: it loads the star's five astrometric unknowns
-// once, walks the star's rows G at a time, and for aprod 2 reduces the five
-// astrometric sums inside the group and writes them without atomics (the
-// OpenACC design of the paper makes every one of the 24 updates atomic).
-// Attitude columns are updated with FP64 reductions in L2, instrumental
-// columns are privatised per block in shared memory when they fit, and the
-// global column is reduced per block.  Values live in 24 planes (structure
-// of arrays), so every lane's load of nonzero k is coalesced with its
-// neighbours' within the star.
+// Layout: the 24 nonzeros of the rows are 24 planes (structure of arrays),
+// so the values of consecutive rows are consecutive in memory; a 16-byte
+// record per row carries the attitude offset and the six instrument indices.
+//
+// aprod 1 is row-parallel: lane l of a warp takes row 32 t + l of tile t, so
+// every plane read is a whole aligned 256-byte segment (no half-used cache
+// lines).  The star of a row (for its five astrometric unknowns) comes from a
+// per-tile table of first stars plus a short walk along star_ptr.
+//
+// aprod 2 is split by column section:
+//  - astrometric, instrumental, global: star-parallel pass.  Rows are grouped
+//    by star (§3), so G lanes own one star, accumulate its five sums in
+//    registers and write them without atomics.  Instrumental columns are
+//    privatised per block in shared memory when they fit; the global column
+//    is reduced per block.
+//  - attitude: a pass over a copy of the 12 attitude values sorted by the
+//    attitude offset.  A warp reduces all rows of one offset o into 12 sums
+//    S[o][a][j] (axis a, tap j); column a*D + k then receives
+//    sum_j S[k-j][a][j].  No atomics, and the summation order is fixed, so
+//    this part is deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -22,6 +32,8 @@
 
 namespace gsr {
 
+constexpr int64_t kSmemInstrMax = 6144;  // instrument columns kept in shared memory (48 KB)
+
 __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
 {
     const uint32_t w = (j < 2) ? rc.y : ((j < 4) ? rc.z : rc.w);
@@ -29,53 +41,60 @@ __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
 }
 
 // ---------------------------------------------------------------------------
-// aprod 1.  MODE 0: y += A x.  MODE 1 (LSQR): y = A x + cy * y with cy read
-// from the solve state, and ||y||^2 reduced to state->beta_new.
+// aprod 1, row-parallel.  MODE 0: y += A x.  MODE 1 (LSQR): y = A x + cy y
+// with cy from the solve state and ||y||^2 reduced into state->beta_new.
+// SMEMX: the instrumental part of x is staged in shared memory.
 // ---------------------------------------------------------------------------
-template <int G, int MODE>
+template <int MODE, bool SMEMX>
 __global__ void __launch_bounds__(kThreads)
-k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y,
-         SolveState *st, double *partial, unsigned *counter)
+k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveState *st,
+         double *partial, unsigned *counter)
 {
-    constexpr int GPW = 32 / G;  // stars per warp per sweep
-    const int lane = threadIdx.x & (G - 1);
-    const int gw = (threadIdx.x & 31) / G;
+    extern __shared__ double s_xi[];
+    if (SMEMX) {
+        for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x)
+            s_xi[f] = x[A.ins0 + f];
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t ntiles = (A.m + 31) >> 5;
     const double cy = (MODE == 1) ? st->cy : 1.0;
     const int64_t mp = A.mp;
-    const double xg = x[A.glb0];
+    const double xg = __ldg(x + A.glb0);
     double nrm = 0.0;
 
-    for (int64_t s0 = warp * GPW; s0 < A.S; s0 += nwarps * GPW) {
-        const int64_t s = s0 + gw;
-        uint32_t r0 = 0, r1 = 0;
-        double xa0 = 0, xa1 = 0, xa2 = 0, xa3 = 0, xa4 = 0;
-        if (s < A.S) {
-            r0 = A.star_ptr[s];
-            r1 = A.star_ptr[s + 1];
-            const double *xs = x + kNAstro * s;
-            xa0 = xs[0]; xa1 = xs[1]; xa2 = xs[2]; xa3 = xs[3]; xa4 = xs[4];
-        }
-        for (uint32_t r = r0 + lane; r < r1; r += G) {
-            const uint4 rc = A.rec[r];
+    for (int64_t t = warp; t < ntiles; t += nwarps) {
+        const int64_t r = (t << 5) + lane;
+        if (r < A.m) {
+            uint32_t s = A.tile_star[t];
+            while ((int64_t)A.star_ptr[s + 1] <= r)  // ends at s < S because r < m
+                ++s;
+            const uint4 rc = __ldcs(A.rec + r);
             const double *v = A.val + r;
-            double sum = v[0] * xa0;
-            sum = fma(v[1 * mp], xa1, sum);
-            sum = fma(v[2 * mp], xa2, sum);
-            sum = fma(v[3 * mp], xa3, sum);
-            sum = fma(v[4 * mp], xa4, sum);
+            double vk[kNPar];
+#pragma unroll
+            for (int k = 0; k < kNPar; k++)
+                vk[k] = __ldcs(v + k * mp);
+            const double *xs = x + (int64_t)kNAstro * s;
+            double sum = vk[0] * __ldg(xs);
+#pragma unroll
+            for (int k = 1; k < kNAstro; k++)
+                sum = fma(vk[k], __ldg(xs + k), sum);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const double *xa = x + A.att0 + a * A.D + rc.x;
 #pragma unroll
                 for (int j = 0; j < 4; j++)
-                    sum = fma(v[(5 + 4 * a + j) * mp], xa[j], sum);
+                    sum = fma(vk[5 + 4 * a + j], __ldg(xa + j), sum);
             }
 #pragma unroll
-            for (int j = 0; j < kNInstr; j++)
-                sum = fma(v[(17 + j) * mp], x[A.ins0 + instr_at(rc, j)], sum);
-            sum = fma(v[23 * mp], xg, sum);
+            for (int j = 0; j < kNInstr; j++) {
+                const uint32_t f = instr_at(rc, j);
+                sum = fma(vk[17 + j], SMEMX ? s_xi[f] : __ldg(x + A.ins0 + f), sum);
+            }
+            sum = fma(vk[23], xg, sum);
             double yn;
             if (MODE == 1) {
                 yn = fma(cy, y[r], sum);
@@ -96,15 +115,14 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y,
 }
 
 // ---------------------------------------------------------------------------
-// aprod 2.  MODE kA2Accumulate: out += A^T y.  kA2Overwrite: the astrometric
-// part of out is overwritten with (A^T y)_astro and the rest accumulated into
-// (it must be zero on entry).  kA2Squares: like kA2Overwrite with A_ik^2 in
-// place of A_ik y_i (column sums of squares for the preconditioner).
-// SMEM_INSTR: instrumental columns privatised in shared memory.
+// aprod 2, star-parallel pass over the astrometric, instrumental and global
+// nonzeros.  MODE kA2Accumulate: out += A^T y.  kA2Overwrite: astrometric
+// part overwritten, instrumental/global accumulated into zeroed memory.
+// kA2Squares: as kA2Overwrite with A_ik^2 in place of A_ik y_i.
 // ---------------------------------------------------------------------------
 template <int G, int MODE, bool SMEM_INSTR>
 __global__ void __launch_bounds__(kThreads)
-k_aprod2(SysView A, const double *__restrict__ y, double *__restrict__ out)
+k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out)
 {
     extern __shared__ double s_ins[];
     __shared__ double s_red[kThreads / 32];
@@ -130,42 +148,43 @@ k_aprod2(SysView A, const double *__restrict__ y, double *__restrict__ out)
         }
         double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
         for (uint32_t r = r0 + lane; r < r1; r += G) {
-            const uint4 rc = A.rec[r];
+            const uint4 rc = __ldcs(A.rec + r);
             const double *v = A.val + r;
-            double vk[kNPar];
+            double va[kNAstro], vi[kNInstr], vg;
 #pragma unroll
-            for (int k = 0; k < kNPar; k++)
-                vk[k] = v[k * mp];
+            for (int k = 0; k < kNAstro; k++)
+                va[k] = __ldcs(v + k * mp);
+#pragma unroll
+            for (int j = 0; j < kNInstr; j++)
+                vi[j] = __ldcs(v + (17 + j) * mp);
+            vg = __ldcs(v + 23 * mp);
             double yi;
             if (MODE == kA2Squares) {
                 yi = 1.0;
 #pragma unroll
-                for (int k = 0; k < kNPar; k++)
-                    vk[k] = vk[k] * vk[k];
+                for (int k = 0; k < kNAstro; k++)
+                    va[k] *= va[k];
+#pragma unroll
+                for (int j = 0; j < kNInstr; j++)
+                    vi[j] *= vi[j];
+                vg *= vg;
             } else {
-                yi = y[r];
+                yi = __ldcs(y + r);
             }
-            a0 = fma(vk[0], yi, a0);
-            a1 = fma(vk[1], yi, a1);
-            a2 = fma(vk[2], yi, a2);
-            a3 = fma(vk[3], yi, a3);
-            a4 = fma(vk[4], yi, a4);
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                double *xa = out + A.att0 + a * A.D + rc.x;
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    atomicAdd(xa + j, vk[5 + 4 * a + j] * yi);
-            }
+            a0 = fma(va[0], yi, a0);
+            a1 = fma(va[1], yi, a1);
+            a2 = fma(va[2], yi, a2);
+            a3 = fma(va[3], yi, a3);
+            a4 = fma(va[4], yi, a4);
 #pragma unroll
             for (int j = 0; j < kNInstr; j++) {
                 const uint32_t f = instr_at(rc, j);
                 if (SMEM_INSTR)
-                    atomicAdd(&s_ins[f], vk[17 + j] * yi);
+                    atomicAdd(&s_ins[f], vi[j] * yi);
                 else
-                    atomicAdd(out + A.ins0 + f, vk[17 + j] * yi);
+                    atomicAdd(out + A.ins0 + f, vi[j] * yi);
             }
-            gacc = fma(vk[23], yi, gacc);
+            gacc = fma(vg, yi, gacc);
         }
         // the star's five astrometric sums: reduce over the G lanes
 #pragma unroll
@@ -206,79 +225,151 @@ k_aprod2(SysView A, const double *__restrict__ y, double *__restrict__ out)
 }
 
 // ---------------------------------------------------------------------------
-// launchers
+// aprod 2, attitude part.  Pass 1: one warp per attitude offset o sums the
+// products of the rows with that offset into S[o][4a + j].  SQ: squares of
+// the values (preconditioner) instead of products with y.
 // ---------------------------------------------------------------------------
-static int row_grid(const gsr_handle_t *h, int G)
+template <bool SQ>
+__global__ void __launch_bounds__(kThreads)
+k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
 {
-    int64_t need = (h->sys.S * G + kThreads - 1) / kThreads;
-    if (need < 1)
-        need = 1;
-    if (need > kMaxPartials)
-        need = kMaxPartials;
-    return (int)need;
-}
-
-template <int G>
-static cudaError_t a1_dispatch(const gsr_handle_t *h, const double *x, double *y,
-                               int lsqr_mode, cudaStream_t st)
-{
-    const int grid = row_grid(h, G);
-    if (lsqr_mode)
-        k_aprod1<G, 1><<<grid, kThreads, 0, st>>>(h->sys, x, y, h->d_state,
-                                                  h->d_partial + kRedU * kPartialsPerKind,
-                                                  h->d_counter + kRedU);
-    else
-        k_aprod1<G, 0><<<grid, kThreads, 0, st>>>(h->sys, x, y, nullptr, nullptr, nullptr);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_aprod1(const gsr_handle_t *h, const double *x, double *y,
-                          int lsqr_mode, cudaStream_t st)
-{
-    switch (h->lanes) {
-    case 4: return a1_dispatch<4>(h, x, y, lsqr_mode, st);
-    case 8: return a1_dispatch<8>(h, x, y, lsqr_mode, st);
-    case 16: return a1_dispatch<16>(h, x, y, lsqr_mode, st);
-    default: return a1_dispatch<32>(h, x, y, lsqr_mode, st);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t mp = A.mp;
+    for (int64_t o = warp; o < A.nseg; o += nwarps) {
+        const uint32_t e0 = A.seg[o], e1 = A.seg[o + 1];
+        double acc[kNAtt];
+#pragma unroll
+        for (int k = 0; k < kNAtt; k++)
+            acc[k] = 0.0;
+        for (uint32_t e = e0 + lane; e < e1; e += 32) {
+            const double yi = SQ ? 1.0 : __ldg(y + __ldcs(A.perm + e));
+#pragma unroll
+            for (int k = 0; k < kNAtt; k++) {
+                double v = __ldcs(A.tval + k * mp + e);
+                if (SQ)
+                    v *= v;
+                acc[k] = fma(v, yi, acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kNAtt; k++)
+            acc[k] = warp_sum(acc[k]);
+        if (lane < kNAtt) {
+            double t = acc[0];
+#pragma unroll
+            for (int k = 1; k < kNAtt; k++)
+                if (lane == k)
+                    t = acc[k];
+            S[o * kNAtt + lane] = t;
+        }
     }
 }
 
-constexpr int64_t kSmemInstrMax = 6144;  // 48 KB of shared memory per block
+// Pass 2: column a*D + k receives sum_{j=0..3, 0 <= k-j < nseg} S[k-j][4a+j].
+template <bool ACC>
+__global__ void k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out)
+{
+    const int64_t total = 3 * A.D;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = c / A.D, k = c - a * A.D;
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t o = k - j;
+            if (o >= 0 && o < A.nseg)
+                t += S[o * kNAtt + 4 * a + j];
+        }
+        double *dst = out + A.att0 + c;
+        if (ACC)
+            *dst += t;
+        else
+            *dst = t;
+    }
+}
 
-template <int G, int MODE>
-static cudaError_t a2_dispatch2(const gsr_handle_t *h, const double *y, double *out,
-                                cudaStream_t st)
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int MODE>
+static cudaError_t a1_launch(const gsr_handle_t *h, const double *x, double *y,
+                             SolveState *st_slot, double *partial, unsigned *counter,
+                             cudaStream_t st)
 {
     const bool smem = h->sys.I <= kSmemInstrMax;
     const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
-    int grid = h->grid_rows2;
     if (smem)
-        k_aprod2<G, MODE, true><<<grid, kThreads, shm, st>>>(h->sys, y, out);
+        k_aprod1<MODE, true><<<h->grid_rows, kThreads, shm, st>>>(h->sys, x, y, st_slot, partial,
+                                                                   counter);
     else
-        k_aprod2<G, MODE, false><<<grid, kThreads, 0, st>>>(h->sys, y, out);
+        k_aprod1<MODE, false><<<h->grid_rows, kThreads, 0, st>>>(h->sys, x, y, st_slot, partial,
+                                                                  counter);
     return cudaGetLastError();
 }
 
-template <int G>
-static cudaError_t a2_dispatch(const gsr_handle_t *h, const double *y, double *out,
-                               int mode, cudaStream_t st)
+cudaError_t launch_aprod1(const gsr_handle_t *h, const double *x, double *y, int lsqr_mode,
+                          cudaStream_t st)
 {
-    switch (mode) {
-    case kA2Accumulate: return a2_dispatch2<G, kA2Accumulate>(h, y, out, st);
-    case kA2Overwrite: return a2_dispatch2<G, kA2Overwrite>(h, y, out, st);
-    default: return a2_dispatch2<G, kA2Squares>(h, y, out, st);
+    if (lsqr_mode)
+        return a1_launch<1>(h, x, y, h->d_state, h->d_partial + kRedU * kPartialsPerKind,
+                            h->d_counter + kRedU, st);
+    return a1_launch<0>(h, x, y, nullptr, nullptr, nullptr, st);
+}
+
+int aprod1_grid_blocks(const gsr_handle_t *h) { return h->grid_rows; }
+
+cudaError_t launch_aprod1_with_slots(const gsr_handle_t *h, const double *x, double *y,
+                                     SolveState *st_slot, double *partial, unsigned *counter,
+                                     cudaStream_t st)
+{
+    return a1_launch<1>(h, x, y, st_slot, partial, counter, st);
+}
+
+template <int G, int MODE>
+static cudaError_t a2_stars(const gsr_handle_t *h, const double *y, double *out, cudaStream_t st)
+{
+    const bool smem = h->sys.I <= kSmemInstrMax;
+    const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
+    if (smem)
+        k_aprod2_stars<G, MODE, true><<<h->grid_rows2, kThreads, shm, st>>>(h->sys, y, out);
+    else
+        k_aprod2_stars<G, MODE, false><<<h->grid_rows2, kThreads, 0, st>>>(h->sys, y, out);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t a2_stars_g(const gsr_handle_t *h, const double *y, double *out, cudaStream_t st)
+{
+    switch (h->lanes) {
+    case 4: return a2_stars<4, MODE>(h, y, out, st);
+    case 8: return a2_stars<8, MODE>(h, y, out, st);
+    case 32: return a2_stars<32, MODE>(h, y, out, st);
+    default: return a2_stars<16, MODE>(h, y, out, st);
     }
 }
 
-cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out,
-                          int mode, cudaStream_t st)
+cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out, int mode,
+                          cudaStream_t st)
 {
-    switch (h->lanes) {
-    case 4: return a2_dispatch<4>(h, y, out, mode, st);
-    case 8: return a2_dispatch<8>(h, y, out, mode, st);
-    case 16: return a2_dispatch<16>(h, y, out, mode, st);
-    default: return a2_dispatch<32>(h, y, out, mode, st);
+    cudaError_t e;
+    switch (mode) {
+    case kA2Accumulate: e = a2_stars_g<kA2Accumulate>(h, y, out, st); break;
+    case kA2Overwrite: e = a2_stars_g<kA2Overwrite>(h, y, out, st); break;
+    default: e = a2_stars_g<kA2Squares>(h, y, out, st); break;
     }
+    if (e != cudaSuccess)
+        return e;
+    if (mode == kA2Squares)
+        k_att_segments<true><<<h->grid_att, kThreads, 0, st>>>(h->sys, y, h->d_attS);
+    else
+        k_att_segments<false><<<h->grid_att, kThreads, 0, st>>>(h->sys, y, h->d_attS);
+    if (mode == kA2Accumulate)
+        k_att_combine<true><<<h->grid_vec, kThreads, 0, st>>>(h->sys, h->d_attS, out);
+    else
+        k_att_combine<false><<<h->grid_vec, kThreads, 0, st>>>(h->sys, h->d_attS, out);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -336,6 +427,49 @@ cudaError_t launch_pack_rec(const gsr_handle_t *h, const uint32_t *attoff, const
     return cudaGetLastError();
 }
 
+// tile_star[t] = the star of row 32 t (last s with star_ptr[s] <= 32 t)
+__global__ void k_tile_star(SysView A, uint32_t *tile_star)
+{
+    const int64_t ntiles = (A.m + 31) >> 5;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t << 5;
+        int64_t lo = 0, hi = A.S;  // star_ptr[lo] <= r < star_ptr[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)A.star_ptr[mid] <= r)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        tile_star[t] = (uint32_t)lo;
+    }
+}
+
+cudaError_t launch_tile_star(const gsr_handle_t *h, cudaStream_t st)
+{
+    k_tile_star<<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_tile_star);
+    return cudaGetLastError();
+}
+
+// tval[k][e] = val[5 + k][perm[e]]
+__global__ void k_gather_att(SysView A, double *__restrict__ tval)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A.m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = A.perm[e];
+#pragma unroll
+        for (int k = 0; k < kNAtt; k++)
+            tval[k * A.mp + e] = A.val[(kNAstro + k) * A.mp + r];
+    }
+}
+
+cudaError_t launch_gather_att(const gsr_handle_t *h, cudaStream_t st)
+{
+    k_gather_att<<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_tval);
+    return cudaGetLastError();
+}
+
 // error bits: 1 star_ptr, 2 attoff, 4 instr, 8 non-finite value
 __global__ void k_validate(SysView A, int *err, int check_values)
 {
@@ -370,36 +504,11 @@ cudaError_t launch_validate(const gsr_handle_t *h, cudaStream_t st)
     return cudaGetLastError();
 }
 
-}  // namespace gsr
-
-namespace gsr {
-
-// persistent grid of the aprod 2 kernel: SMs x resident blocks of the
-// instance that will run
-template <int G>
-static int a2_occupancy(const gsr_handle_t *h)
+// ---------------------------------------------------------------------------
+// persistent grids: SMs x resident blocks of the instance that will run
+// ---------------------------------------------------------------------------
+static int cap_grid(const gsr_handle_t *h, int occ)
 {
-    const bool smem = h->sys.I <= kSmemInstrMax;
-    const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
-    int occ = 0;
-    cudaError_t e = smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &occ, k_aprod2<G, kA2Overwrite, true>, kThreads, shm)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &occ, k_aprod2<G, kA2Overwrite, false>, kThreads, 0);
-    if (e != cudaSuccess)
-        return -1;
-    return occ;
-}
-
-int aprod2_grid(const gsr_handle_t *h)
-{
-    int occ;
-    switch (h->lanes) {
-    case 4: occ = a2_occupancy<4>(h); break;
-    case 8: occ = a2_occupancy<8>(h); break;
-    case 16: occ = a2_occupancy<16>(h); break;
-    default: occ = a2_occupancy<32>(h); break;
-    }
     if (occ <= 0)
         return -1;
     int64_t g = (int64_t)h->nsm * occ;
@@ -408,33 +517,41 @@ int aprod2_grid(const gsr_handle_t *h)
     return (int)g;
 }
 
-}  // namespace gsr
-
-namespace gsr {
-
-// aprod 1 in its LSQR form (y = A x + cy y, ||y||^2 reduced into
-// st->beta_new) with the caller's choice of state and reduction slots
-template <int G>
-static cudaError_t a1_with_slots(const gsr_handle_t *h, const double *x, double *y,
-                                 SolveState *st_slot, double *partial, unsigned *counter,
-                                 cudaStream_t st)
+int aprod1_grid(const gsr_handle_t *h)
 {
-    k_aprod1<G, 1><<<row_grid(h, G), kThreads, 0, st>>>(h->sys, x, y, st_slot, partial, counter);
-    return cudaGetLastError();
+    const bool smem = h->sys.I <= kSmemInstrMax;
+    const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
+    int occ = 0;
+    cudaError_t e = smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1<1, true>,
+                                                                         kThreads, shm)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1<1, false>,
+                                                                         kThreads, 0);
+    return e == cudaSuccess ? cap_grid(h, occ) : -1;
 }
 
-int aprod1_grid_blocks(const gsr_handle_t *h) { return row_grid(h, h->lanes); }
-
-cudaError_t launch_aprod1_with_slots(const gsr_handle_t *h, const double *x, double *y,
-                                     SolveState *st_slot, double *partial, unsigned *counter,
-                                     cudaStream_t st)
+template <int G>
+static int a2_occupancy(const gsr_handle_t *h)
 {
+    const bool smem = h->sys.I <= kSmemInstrMax;
+    const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
+    int occ = 0;
+    cudaError_t e = smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               &occ, k_aprod2_stars<G, kA2Overwrite, true>, kThreads, shm)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               &occ, k_aprod2_stars<G, kA2Overwrite, false>, kThreads, 0);
+    return e == cudaSuccess ? occ : -1;
+}
+
+int aprod2_grid(const gsr_handle_t *h)
+{
+    int occ;
     switch (h->lanes) {
-    case 4: return a1_with_slots<4>(h, x, y, st_slot, partial, counter, st);
-    case 8: return a1_with_slots<8>(h, x, y, st_slot, partial, counter, st);
-    case 16: return a1_with_slots<16>(h, x, y, st_slot, partial, counter, st);
-    default: return a1_with_slots<32>(h, x, y, st_slot, partial, counter, st);
+    case 4: occ = a2_occupancy<4>(h); break;
+    case 8: occ = a2_occupancy<8>(h); break;
+    case 32: occ = a2_occupancy<32>(h); break;
+    default: occ = a2_occupancy<16>(h); break;
     }
+    return cap_grid(h, occ);
 }
 
 }  // namespace gsr

@@ -76,7 +76,7 @@ k_init_u(const SolveArgs *args, double *u, int64_t m, SolveState *st, double *pa
 __global__ void __launch_bounds__(kThreads)
 k_init_v(const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ v,
          int64_t n, SolveState *st, double *partial, unsigned *counter,
-         cudaGraphConditionalHandle loop)
+         cudaGraphConditionalHandle loop, int in_graph)
 {
     const double beta = st->beta;
     const double ib = (beta > 0.0) ? 1.0 / beta : 0.0;
@@ -101,7 +101,7 @@ k_init_v(const double *__restrict__ p, const double *__restrict__ q, double *__r
             st->istop = 0;
             st->done = 1;
         }
-        if (st->done)
+        if (st->done && in_graph)
             cudaGraphSetConditional(loop, 0u);
     }
 }
@@ -131,7 +131,7 @@ __global__ void k_vec_b(const double *__restrict__ p, double *__restrict__ v,
 }
 
 __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm2,
-                             double dd, double zz, cudaGraphConditionalHandle loop)
+                             double dd, double zz, cudaGraphConditionalHandle loop, int in_graph)
 {
     SolveState s = *st;
     const double beta = s.beta_new;
@@ -182,10 +182,13 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
         s.nonfinite = 1;
         istop = kIstopNonfinite;
     }
+    if (args->force_itmax && !bad && s.itn < args->itmax)
+        istop = 0;
     s.istop = istop;
     if (istop != 0) {
         s.done = 1;
-        cudaGraphSetConditional(loop, 0u);
+        if (in_graph)
+            cudaGraphSetConditional(loop, 0u);
     }
     *st = s;
 }
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(kThreads)
 k_vec_a(const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ v,
         const double *__restrict__ w, double *__restrict__ z, double *__restrict__ var,
         int64_t n, SolveState *st, const SolveArgs *args, double *partial,
-        unsigned *counter, cudaGraphConditionalHandle loop)
+        unsigned *counter, cudaGraphConditionalHandle loop, int in_graph)
 {
     const double beta = st->beta_new;
     const double rhobar = st->rhobar;
@@ -223,7 +226,7 @@ k_vec_a(const double *__restrict__ p, const double *__restrict__ q, double *__re
         acc[2] = fma(zj, zj, acc[2]);
     }
     if (grid_reduce<3>(acc, partial, counter) && threadIdx.x == 0)
-        lsqr_scalars(st, args, acc[0], acc[1], acc[2], loop);
+        lsqr_scalars(st, args, acc[0], acc[1], acc[2], loop, in_graph);
 }
 
 // x = p o z, se = p o sqrt(var) * rnorm / sqrt(dof)
@@ -296,6 +299,57 @@ static cudaError_t find_leaf(cudaGraph_t g, cudaGraphNode_t *leaf)
         }                               \
     } while (0)
 
+// The three parts of one solve.  `in_graph` says whether the kernels run
+// inside the solve graph (and may clear its loop flag).
+cudaError_t enqueue_prologue(const gsr_handle_t *h, cudaStream_t s,
+                             cudaGraphConditionalHandle loop, int in_graph)
+{
+    const SysView &A = h->sys;
+    double *part = h->d_partial;
+    unsigned *cnt = h->d_counter;
+    cudaError_t e = enqueue_precond(h, h->d_p, s);
+    if (e != cudaSuccess)
+        return e;
+    k_init_u<<<h->grid_vec, kThreads, 0, s>>>(h->d_args, h->d_u, A.m, h->d_state,
+                                               part + kRedBnorm * kPartialsPerKind, cnt + kRedBnorm);
+    k_zero<<<h->grid_vec, kThreads, 0, s>>>(h->d_q + A.att0, A.n - A.att0);
+    e = launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
+    if (e != cudaSuccess)
+        return e;
+    k_init_v<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, A.n, h->d_state,
+                                               part + kRedV * kPartialsPerKind, cnt + kRedV, loop,
+                                               in_graph);
+    k_vec_b<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_v, h->d_vp, h->d_w, h->d_q, A.n, A.att0,
+                                              h->d_state, 1, h->d_z, h->d_var);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_iteration(const gsr_handle_t *h, cudaStream_t s,
+                              cudaGraphConditionalHandle loop, int in_graph)
+{
+    const SysView &A = h->sys;
+    cudaError_t e = launch_aprod1(h, h->d_vp, h->d_u, 1, s);
+    if (e == cudaSuccess)
+        e = launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
+    if (e != cudaSuccess)
+        return e;
+    k_vec_a<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, h->d_w, h->d_z, h->d_var, A.n,
+                                              h->d_state, h->d_args,
+                                              h->d_partial + kRedV * kPartialsPerKind,
+                                              h->d_counter + kRedV, loop, in_graph);
+    k_vec_b<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_v, h->d_vp, h->d_w, h->d_q, A.n, A.att0,
+                                              h->d_state, 0, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_epilogue(const gsr_handle_t *h, cudaStream_t s)
+{
+    const SysView &A = h->sys;
+    k_finalize<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_z, h->d_var, A.n, A.m, h->d_state,
+                                                 h->d_args);
+    return cudaGetLastError();
+}
+
 // Build and instantiate the graph of one whole solve:
 //   [precondition, u = b, q = A^T u, v_1, w_1]  ->  WHILE(flag) { iteration }
 //   ->  [x = p o z, se]
@@ -308,24 +362,12 @@ cudaError_t build_solve_graph(gsr_handle_t *h)
     cudaGraphNodeParams cp = {};
     cudaGraph_t body;
     cudaStream_t s = h->cap_stream;
-    const SysView &A = h->sys;
-    double *part = h->d_partial;
-    unsigned *cnt = h->d_counter;
 
     GSR_TRY(cudaGraphCreate(&g, 0));
     GSR_TRY(cudaGraphConditionalHandleCreate(&loop, g, 1u, cudaGraphCondAssignDefault));
 
-    // prologue
     GSR_TRY(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    enqueue_precond(h, h->d_p, s);
-    k_init_u<<<h->grid_vec, kThreads, 0, s>>>(h->d_args, h->d_u, A.m, h->d_state,
-                                               part + kRedBnorm * kPartialsPerKind, cnt + kRedBnorm);
-    k_zero<<<h->grid_vec, kThreads, 0, s>>>(h->d_q + A.att0, A.n - A.att0);
-    launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
-    k_init_v<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, A.n, h->d_state,
-                                               part + kRedV * kPartialsPerKind, cnt + kRedV, loop);
-    k_vec_b<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_v, h->d_vp, h->d_w, h->d_q, A.n, A.att0,
-                                              h->d_state, 1, h->d_z, h->d_var);
+    enqueue_prologue(h, s, loop, 1);
     GSR_TRY(cudaStreamEndCapture(s, &g));
     GSR_TRY(find_leaf(g, &pre_leaf));
 
@@ -337,19 +379,11 @@ cudaError_t build_solve_graph(gsr_handle_t *h)
     GSR_TRY(cudaGraphAddNode(&wnode, g, &pre_leaf, nullptr, 1, &cp));
     body = cp.conditional.phGraph_out[0];
     GSR_TRY(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    launch_aprod1(h, h->d_vp, h->d_u, 1, s);
-    launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
-    k_vec_a<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, h->d_w, h->d_z, h->d_var, A.n,
-                                              h->d_state, h->d_args, part + kRedV * kPartialsPerKind,
-                                              cnt + kRedV, loop);
-    k_vec_b<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_v, h->d_vp, h->d_w, h->d_q, A.n, A.att0,
-                                              h->d_state, 0, nullptr, nullptr);
+    enqueue_iteration(h, s, loop, 1);
     GSR_TRY(cudaStreamEndCapture(s, &body));
 
-    // epilogue
     GSR_TRY(cudaStreamBeginCaptureToGraph(s, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
-    k_finalize<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_z, h->d_var, A.n, A.m, h->d_state,
-                                                 h->d_args);
+    enqueue_epilogue(h, s);
     GSR_TRY(cudaStreamEndCapture(s, &g));
 
     GSR_TRY(cudaGraphInstantiate(&h->solve_exec, g, 0));

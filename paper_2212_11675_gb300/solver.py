@@ -61,7 +61,8 @@ class Solver:
     """PC-LSQR solver of one Gaia observation system (paper §3 structure)."""
 
     def __init__(self, system, conlim: float = 1e8, lanes_per_star: int = 0,
-                 validate: bool = True, precision: int = _lib.GSR_PREC_FP64):
+                 validate: bool = True, precision: int = _lib.GSR_PREC_FP64,
+                 force_itmax: bool = False, eager: bool = False):
         L = lib()
         self._h = ctypes.c_void_p()
         d = Dims(system.n_stars, system.n_dfa, system.n_instr, int(system.m))
@@ -71,6 +72,8 @@ class Solver:
         cfg.lanes_per_star = lanes_per_star
         cfg.validate = 1 if validate else 0
         cfg.precision = precision
+        cfg.force_itmax = 1 if force_itmax else 0
+        cfg.eager = 1 if eager else 0
         arrs = []
         for a, dt in ((system.star_ptr, np.uint32), (system.attoff, np.uint32),
                       (system.instr, np.uint16), (system.values, np.float64)):

@@ -187,14 +187,17 @@ def test_solve_zero_rhs_gives_zero():
     assert not x.any().item()
 
 
-def test_solve_with_host_buffers():
+@pytest.mark.parametrize("eager", [False, True])
+def test_solve_with_host_buffers(eager):
     sys = ragged(seed=12)
     b = _rhs(sys, 5)
     ref = oracle.pc_lsqr(sys, b, 40, 0.0, 0.0)
-    with _solver(sys) as s:
+    with _solver(sys, eager=eager) as s:
         x, se, res = s.lsqr_solve(b, 40, 0.0, 0.0)
     assert isinstance(x, np.ndarray) and res["itn"] == 40
     assert np.linalg.norm(x - ref["x"]) <= 1e-9 * np.linalg.norm(ref["x"])
+    tol = max(1e-9, 50.0 * oracle_sensitivity(sys, b, 40)["se"])
+    assert np.max(np.abs(se - ref["se"])) <= tol * ref["se"].max()
 
 
 def test_errors_are_reported_not_faulted():
