@@ -52,6 +52,11 @@ extern "C" {
 #define GSR_ERR_NONFINITE (-6)   /* NaN or Inf in the input or in the recurrences */
 #define GSR_ERR_UNSUPPORTED (-7) /* configuration not supported by this build */
 
+/* Accumulation of the instrumental columns in aprod 2. */
+#define GSR_INSTR_AUTO 0     /* shared memory per block when I <= 6144, else replicas */
+#define GSR_INSTR_SMEM 1     /* shared memory per block (needs I <= 6144) */
+#define GSR_INSTR_REPLICAS 2 /* one replica per SM in device memory, L2 reductions */
+
 /* Storage and arithmetic of the matrix values. */
 #define GSR_PREC_FP64 0 /* IEEE double values, native FP64 arithmetic */
 
@@ -78,6 +83,7 @@ typedef struct {
                            iteration, instead of running its CUDA graph (for
                            profilers that cannot see kernels inside graphs
                            with conditional nodes); same arithmetic */
+    int instr_mode;     /* GSR_INSTR_*; default GSR_INSTR_AUTO */
 } gsr_config;
 
 typedef struct {

@@ -22,6 +22,7 @@ GSR_ERR_NONFINITE = -6
 GSR_ERR_UNSUPPORTED = -7
 
 GSR_PREC_FP64 = 0
+GSR_INSTR_AUTO, GSR_INSTR_SMEM, GSR_INSTR_REPLICAS = 0, 1, 2
 
 EXPORTS = (
     "gsr_config_default", "gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
@@ -38,7 +39,8 @@ class Dims(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("conlim", ctypes.c_double),
                 ("lanes_per_star", ctypes.c_int), ("validate", ctypes.c_int),
-                ("force_itmax", ctypes.c_int), ("eager", ctypes.c_int)]
+                ("force_itmax", ctypes.c_int), ("eager", ctypes.c_int),
+                ("instr_mode", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

@@ -111,7 +111,7 @@ static void release(gsr_handle_t *h)
     if (h->cap_stream)
         cudaStreamDestroy(h->cap_stream);
     void *dev[] = {h->d_star_ptr, h->d_rec, h->d_val, h->d_tile_star, h->d_tval, h->d_perm,
-                   h->d_seg, h->d_attS, h->d_p, h->d_u, h->d_v, h->d_w, h->d_z,
+                   h->d_seg, h->d_attS, h->d_irep, h->d_p, h->d_u, h->d_v, h->d_w, h->d_z,
                    h->d_var, h->d_q, h->d_vp, h->d_vt, h->d_bstage, h->d_xstage, h->d_sestage,
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err};
     for (void *p : dev)
@@ -276,7 +276,9 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     CK(cudaStreamSynchronize(st));
 
     // launch geometry
-    h->lanes = h->cfg.lanes_per_star ? h->cfg.lanes_per_star : 16;
+    // measured at the medium size: 8 lanes per star with shared-memory
+    // instrument sums, 32 with replicas
+    h->lanes = h->cfg.lanes_per_star ? h->cfg.lanes_per_star : (instr_in_smem(h) ? 8 : 32);
     h->grid_rows = aprod1_grid(h);
     if (h->grid_rows <= 0)
         return cuda_fail(cudaGetLastError(), "aprod1 occupancy");
@@ -285,6 +287,11 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     if (gv > (int64_t)h->nsm * 8) gv = (int64_t)h->nsm * 8;
     if (gv > kMaxPartials) gv = kMaxPartials;
     h->grid_vec = (int)(gv < 1 ? 1 : gv);
+    if (!instr_in_smem(h)) {
+        h->nrep = h->nsm;
+        TRY(dalloc(h, &h->d_irep, (int64_t)h->nrep * I));
+        CK(cudaMemset(h->d_irep, 0, (size_t)h->nrep * I * sizeof(double)));
+    }
     h->grid_rows2 = aprod2_grid(h);
     if (h->grid_rows2 <= 0)
         return cuda_fail(cudaGetLastError(), "aprod2 occupancy");
@@ -316,6 +323,10 @@ extern "C" int gsr_create(void **out, const gsr_dims *d, const uint32_t *star_pt
         return GSR_ERR_ARG;
     if (!(c.conlim >= 0.0))
         return GSR_ERR_ARG;
+    if (c.instr_mode < GSR_INSTR_AUTO || c.instr_mode > GSR_INSTR_REPLICAS)
+        return GSR_ERR_ARG;
+    if (c.instr_mode == GSR_INSTR_SMEM && d->n_instr > 6144)
+        return GSR_ERR_UNSUPPORTED;
     gsr_handle_t *h = new (std::nothrow) gsr_handle_t();
     if (!h)
         return GSR_ERR_OOM;

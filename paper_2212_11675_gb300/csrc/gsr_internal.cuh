@@ -85,6 +85,8 @@ struct gsr_handle_t {
     double *d_tval = nullptr;
     uint32_t *d_perm = nullptr, *d_seg = nullptr;
     double *d_attS = nullptr;           // [nseg][12] attitude segment sums
+    double *d_irep = nullptr;           // [nrep][I] instrumental replicas
+    int nrep = 0;
     double *d_p = nullptr;              // preconditioner
     double *d_u = nullptr;              // m
     double *d_v = nullptr, *d_w = nullptr, *d_z = nullptr, *d_var = nullptr;
@@ -120,6 +122,7 @@ cudaError_t launch_pack_rec(const gsr_handle_t *h, const uint32_t *attoff,
 cudaError_t launch_tile_star(const gsr_handle_t *h, cudaStream_t st);
 cudaError_t launch_gather_att(const gsr_handle_t *h, cudaStream_t st);
 int aprod1_grid(const gsr_handle_t *h);
+bool instr_in_smem(const gsr_handle_t *h);
 // LSQR pieces (gsr_lsqr.cu)
 cudaError_t build_solve_graph(gsr_handle_t *h);
 cudaError_t enqueue_prologue(const gsr_handle_t *h, cudaStream_t s,

@@ -77,24 +77,32 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
 #pragma unroll
             for (int k = 0; k < kNPar; k++)
                 vk[k] = __ldcs(v + k * mp);
+            // four independent partial sums (astrometric, attitude axes 0-1,
+            // attitude axis 2 + global, instrumental) keep the FP64 pipe fed
             const double *xs = x + (int64_t)kNAstro * s;
-            double sum = vk[0] * __ldg(xs);
+            double s0 = vk[0] * __ldg(xs);
 #pragma unroll
             for (int k = 1; k < kNAstro; k++)
-                sum = fma(vk[k], __ldg(xs + k), sum);
+                s0 = fma(vk[k], __ldg(xs + k), s0);
+            const double *xa = x + A.att0 + rc.x;
+            double s1 = vk[5] * __ldg(xa);
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const double *xa = x + A.att0 + a * A.D + rc.x;
+            for (int j = 1; j < 4; j++)
+                s1 = fma(vk[5 + j], __ldg(xa + j), s1);
 #pragma unroll
-                for (int j = 0; j < 4; j++)
-                    sum = fma(vk[5 + 4 * a + j], __ldg(xa + j), sum);
-            }
+            for (int j = 0; j < 4; j++)
+                s1 = fma(vk[9 + j], __ldg(xa + A.D + j), s1);
+            double s2 = vk[23] * xg;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                s2 = fma(vk[13 + j], __ldg(xa + 2 * A.D + j), s2);
+            double s3 = 0.0;
 #pragma unroll
             for (int j = 0; j < kNInstr; j++) {
                 const uint32_t f = instr_at(rc, j);
-                sum = fma(vk[17 + j], SMEMX ? s_xi[f] : __ldg(x + A.ins0 + f), sum);
+                s3 = fma(vk[17 + j], SMEMX ? s_xi[f] : __ldg(x + A.ins0 + f), s3);
             }
-            sum = fma(vk[23], xg, sum);
+            const double sum = (s0 + s1) + (s2 + s3);
             double yn;
             if (MODE == 1) {
                 yn = fma(cy, y[r], sum);
@@ -122,7 +130,8 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
 // ---------------------------------------------------------------------------
 template <int G, int MODE, bool SMEM_INSTR>
 __global__ void __launch_bounds__(kThreads)
-k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out)
+k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out,
+               double *__restrict__ rep, int nrep)
 {
     extern __shared__ double s_ins[];
     __shared__ double s_red[kThreads / 32];
@@ -181,26 +190,55 @@ k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out
                 const uint32_t f = instr_at(rc, j);
                 if (SMEM_INSTR)
                     atomicAdd(&s_ins[f], vi[j] * yi);
-                else
-                    atomicAdd(out + A.ins0 + f, vi[j] * yi);
+                else  // reduction in L2 into this block's replica
+                    atomicAdd(rep + (blockIdx.x % nrep) * A.I + f, vi[j] * yi);
             }
             gacc = fma(vg, yi, gacc);
         }
-        // the star's five astrometric sums: reduce over the G lanes
+        // the star's five astrometric sums over the G lanes
+        if constexpr (G >= 8) {
+            // reduce-scatter: the first three exchanges halve a padded set of
+            // 8 sums (4 + 2 + 1 adds), the remaining ones add whole lanes;
+            // lane l then holds sum number kidx of the star
+            double r8[8] = {a0, a1, a2, a3, a4, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, off);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, off);
-            a2 += __shfl_xor_sync(0xffffffffu, a2, off);
-            a3 += __shfl_xor_sync(0xffffffffu, a3, off);
-            a4 += __shfl_xor_sync(0xffffffffu, a4, off);
-        }
-        if (lane == 0 && s < A.S) {
-            double *xs = out + kNAstro * s;
-            if (MODE == kA2Accumulate) {
-                xs[0] += a0; xs[1] += a1; xs[2] += a2; xs[3] += a3; xs[4] += a4;
-            } else {
-                xs[0] = a0; xs[1] = a1; xs[2] = a2; xs[3] = a3; xs[4] = a4;
+            for (int hw = 4, off = G / 2; hw >= 1; hw >>= 1, off >>= 1) {
+                const bool upper = (lane & off) != 0;
+#pragma unroll
+                for (int k = 0; k < hw; k++) {
+                    const double send = upper ? r8[k] : r8[k + hw];
+                    const double keep = upper ? r8[k + hw] : r8[k];
+                    r8[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                }
+            }
+#pragma unroll
+            for (int off = G / 16; off > 0; off >>= 1)
+                r8[0] += __shfl_xor_sync(0xffffffffu, r8[0], off);
+            const int kidx = ((lane & (G / 2)) ? 4 : 0) | ((lane & (G / 4)) ? 2 : 0) |
+                             ((lane & (G / 8)) ? 1 : 0);
+            if (s < A.S && (lane & (G / 8 - 1)) == 0 && kidx < kNAstro) {
+                double *xs = out + kNAstro * s + kidx;
+                if (MODE == kA2Accumulate)
+                    *xs += r8[0];
+                else
+                    *xs = r8[0];
+            }
+        } else {
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+                a3 += __shfl_xor_sync(0xffffffffu, a3, off);
+                a4 += __shfl_xor_sync(0xffffffffu, a4, off);
+            }
+            if (lane == 0 && s < A.S) {
+                double *xs = out + kNAstro * s;
+                if (MODE == kA2Accumulate) {
+                    xs[0] += a0; xs[1] += a1; xs[2] += a2; xs[3] += a3; xs[4] += a4;
+                } else {
+                    xs[0] = a0; xs[1] = a1; xs[2] = a2; xs[3] = a3; xs[4] = a4;
+                }
             }
         }
     }
@@ -253,40 +291,79 @@ k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
                 acc[k] = fma(v, yi, acc[k]);
             }
         }
+        // reduce-scatter over the warp: after the butterfly, lane pair
+        // (2k, 2k+1) holds the total of sum k (16 adds per lane, not 60)
+        double r16[16];
 #pragma unroll
-        for (int k = 0; k < kNAtt; k++)
-            acc[k] = warp_sum(acc[k]);
-        if (lane < kNAtt) {
-            double t = acc[0];
+        for (int k = 0; k < 16; k++)
+            r16[k] = k < kNAtt ? acc[k] : 0.0;
 #pragma unroll
-            for (int k = 1; k < kNAtt; k++)
-                if (lane == k)
-                    t = acc[k];
-            S[o * kNAtt + lane] = t;
+        for (int half = 8; half >= 1; half >>= 1) {
+            const bool upper = (lane & (2 * half)) != 0;  // keeps the upper half
+#pragma unroll
+            for (int k = 0; k < half; k++) {
+                const double send = upper ? r16[k] : r16[k + half];
+                const double keep = upper ? r16[k + half] : r16[k];
+                r16[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * half);
+            }
         }
+        const double tot = r16[0] + __shfl_xor_sync(0xffffffffu, r16[0], 1);
+        const int k_of_lane = lane >> 1;  // bits 4..1 of the lane pick the sum
+        if ((lane & 1) == 0 && k_of_lane < kNAtt)
+            S[o * kNAtt + k_of_lane] = tot;
     }
 }
 
-// Pass 2: column a*D + k receives sum_{j=0..3, 0 <= k-j < nseg} S[k-j][4a+j].
+// Pass 2, fused with the instrumental replicas.  Blocks [0, nb_att) combine
+// the attitude columns: column a*D + k receives sum_{j=0..3} S[k-j][4a+j]
+// (0 <= k-j < nseg).  The remaining blocks (when rep != null) each take 32
+// instrument columns: 8 threads per column sum every 8th replica, the 8
+// partials are added in a fixed order, and the replicas are cleared for the
+// next call.
 template <bool ACC>
-__global__ void k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out)
+__global__ void __launch_bounds__(kThreads)
+k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out,
+              double *__restrict__ rep, int nrep, int nb_att)
 {
-    const int64_t total = 3 * A.D;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = c / A.D, k = c - a * A.D;
-        double t = 0.0;
+    if ((int)blockIdx.x < nb_att) {
+        const int64_t total = 3 * A.D;
+        for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+             c += (int64_t)nb_att * blockDim.x) {
+            const int64_t a = c / A.D, k = c - a * A.D;
+            double t = 0.0;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int64_t o = k - j;
-            if (o >= 0 && o < A.nseg)
-                t += S[o * kNAtt + 4 * a + j];
+            for (int j = 0; j < 4; j++) {
+                const int64_t o = k - j;
+                if (o >= 0 && o < A.nseg)
+                    t += S[o * kNAtt + 4 * a + j];
+            }
+            double *dst = out + A.att0 + c;
+            if (ACC)
+                *dst += t;
+            else
+                *dst = t;
         }
-        double *dst = out + A.att0 + c;
-        if (ACC)
-            *dst += t;
-        else
-            *dst = t;
+        return;
+    }
+    __shared__ double part[8][32];
+    const int64_t f = (int64_t)(blockIdx.x - nb_att) * 32 + (threadIdx.x & 31);
+    const int q = threadIdx.x >> 5;  // 0..7
+    double t = 0.0;
+    if (f < A.I) {
+        for (int r = q; r < nrep; r += 8) {
+            double *p = rep + (int64_t)r * A.I + f;
+            t += *p;
+            *p = 0.0;
+        }
+    }
+    part[q][threadIdx.x & 31] = t;
+    __syncthreads();
+    if (q == 0 && f < A.I) {
+        double u = part[0][threadIdx.x];
+#pragma unroll
+        for (int k = 1; k < 8; k++)
+            u += part[k][threadIdx.x];
+        out[A.ins0 + f] += u;
     }
 }
 
@@ -327,15 +404,26 @@ cudaError_t launch_aprod1_with_slots(const gsr_handle_t *h, const double *x, dou
     return a1_launch<1>(h, x, y, st_slot, partial, counter, st);
 }
 
+bool instr_in_smem(const gsr_handle_t *h)
+{
+    if (h->cfg.instr_mode == GSR_INSTR_REPLICAS)
+        return false;
+    return h->sys.I <= kSmemInstrMax;
+}
+
 template <int G, int MODE>
 static cudaError_t a2_stars(const gsr_handle_t *h, const double *y, double *out, cudaStream_t st)
 {
-    const bool smem = h->sys.I <= kSmemInstrMax;
-    const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
-    if (smem)
-        k_aprod2_stars<G, MODE, true><<<h->grid_rows2, kThreads, shm, st>>>(h->sys, y, out);
-    else
-        k_aprod2_stars<G, MODE, false><<<h->grid_rows2, kThreads, 0, st>>>(h->sys, y, out);
+    if (instr_in_smem(h)) {
+        const size_t shm = (size_t)h->sys.I * sizeof(double);
+        k_aprod2_stars<G, MODE, true><<<h->grid_rows2, kThreads, shm, st>>>(h->sys, y, out,
+                                                                             nullptr, 1);
+        return cudaGetLastError();
+    }
+    // the replicas are zero on entry (cleared at creation and by every
+    // combine that reads them)
+    k_aprod2_stars<G, MODE, false><<<h->grid_rows2, kThreads, 0, st>>>(h->sys, y, out, h->d_irep,
+                                                                        h->nrep);
     return cudaGetLastError();
 }
 
@@ -365,10 +453,16 @@ cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out, i
         k_att_segments<true><<<h->grid_att, kThreads, 0, st>>>(h->sys, y, h->d_attS);
     else
         k_att_segments<false><<<h->grid_att, kThreads, 0, st>>>(h->sys, y, h->d_attS);
+    const int nb_att = (int)((3 * h->sys.D + kThreads - 1) / kThreads < 4 * h->nsm
+                                 ? (3 * h->sys.D + kThreads - 1) / kThreads
+                                 : 4 * h->nsm);
+    const int nb_ins = instr_in_smem(h) ? 0 : (int)((h->sys.I + 31) / 32);
     if (mode == kA2Accumulate)
-        k_att_combine<true><<<h->grid_vec, kThreads, 0, st>>>(h->sys, h->d_attS, out);
+        k_att_combine<true><<<nb_att + nb_ins, kThreads, 0, st>>>(h->sys, h->d_attS, out,
+                                                                   h->d_irep, h->nrep, nb_att);
     else
-        k_att_combine<false><<<h->grid_vec, kThreads, 0, st>>>(h->sys, h->d_attS, out);
+        k_att_combine<false><<<nb_att + nb_ins, kThreads, 0, st>>>(h->sys, h->d_attS, out,
+                                                                    h->d_irep, h->nrep, nb_att);
     return cudaGetLastError();
 }
 
@@ -532,7 +626,7 @@ int aprod1_grid(const gsr_handle_t *h)
 template <int G>
 static int a2_occupancy(const gsr_handle_t *h)
 {
-    const bool smem = h->sys.I <= kSmemInstrMax;
+    const bool smem = instr_in_smem(h);
     const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
     int occ = 0;
     cudaError_t e = smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(

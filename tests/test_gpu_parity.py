@@ -67,8 +67,21 @@ def test_aprod_parity_ragged_and_empty_stars():
 
 
 def test_aprod_parity_instruments_beyond_shared_memory():
-    # I above the shared-memory privatisation limit takes the L2-atomic path
+    # I above the shared-memory privatisation limit takes the replica path
     check_aprods(small(300, 50, 7000, seed=9), 8)
+
+
+@pytest.mark.parametrize("mode", [_lib.GSR_INSTR_SMEM, _lib.GSR_INSTR_REPLICAS])
+def test_aprod_parity_instrument_modes(mode):
+    sys = gen.make("tiny")
+    rng = np.random.default_rng(8)
+    y = rng.standard_normal(sys.m)
+    ref = oracle.aprod2(sys, y)
+    with _solver(sys, instr_mode=mode) as s:
+        xd = torch.zeros(sys.n, dtype=torch.float64, device=DEV)
+        s.aprod2(torch.tensor(y, device=DEV), xd)
+        g = xd.cpu().numpy()
+    assert np.linalg.norm(g - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
 def test_aprod_parity_single_star():
