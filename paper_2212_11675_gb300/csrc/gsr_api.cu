@@ -2,6 +2,7 @@
 // validation of the Gaia system), the two products, the preconditioner and
 // the whole PC-LSQR solve.  No torch types cross this boundary.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -445,6 +446,7 @@ extern "C" int gsr_lsqr_solve(void *hv, const double *b, int itmax, double atol,
     a->atol = atol;
     a->btol = btol;
     a->ctol = (h->cfg.conlim > 0.0) ? 1.0 / h->cfg.conlim : 0.0;
+    a->isdof = 1.0 / sqrt((h->sys.m > h->sys.n) ? (double)(h->sys.m - h->sys.n) : 1.0);
     CK(cudaMemcpyAsync(h->d_args, a, sizeof(SolveArgs), cudaMemcpyHostToDevice, st));
     if (h->cfg.eager) {
         // every launch from the host, the loop flag read back after each step

@@ -45,6 +45,14 @@ struct SolveState {
     double rnorm, arnorm, anorm, acond, xnorm;
     double cy;                 // coefficient of the old u in aprod1 (-alpha/beta)
     double t;                  // rnorm / sqrt(dof) for the standard errors
+    // derived once per iteration by the last block of the kernel that
+    // produced their inputs (FP64 divisions and square roots are expensive
+    // on this part, so no other thread recomputes them)
+    double ib;                 // 1/beta_new (0 if beta_new = 0)
+    double t1;                 // phi/rho of the pending rotation
+    double irho;               // 1/rho of the pending rotation
+    double ia;                 // 1/alpha (1 if alpha = 0)
+    double t2;                 // -theta/rho for the w update
     int itn, istop, done, nonfinite;
 };
 
@@ -56,6 +64,7 @@ struct SolveArgs {
     int itmax;
     int force_itmax;  // only itmax ends the loop
     double atol, btol, ctol;
+    double isdof;     // 1/sqrt(m - n), or 1 when m <= n
 };
 
 // Deterministic grid reduction slots: each kernel writes one partial per

@@ -116,8 +116,24 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
     if (MODE == 1) {
         double v1[1] = {nrm};
         if (grid_reduce<1>(v1, partial, counter)) {
+            // beta_{i+1} and the rotation that eliminates it; the two
+            // independent square roots and reciprocals run in two warps
+            __shared__ double sq[2];
+            const double rhobar = st->rhobar;
+            if (threadIdx.x == 0) {
+                const double beta = sqrt(v1[0]);
+                sq[0] = beta;
+                st->beta_new = beta;
+                st->ib = (beta > 0.0) ? 1.0 / beta : 0.0;
+            }
+            if (threadIdx.x == 32) {
+                const double irho = 1.0 / sqrt(rhobar * rhobar + v1[0]);
+                sq[1] = irho;
+                st->irho = irho;
+            }
+            __syncthreads();
             if (threadIdx.x == 0)
-                st->beta_new = sqrt(v1[0]);
+                st->t1 = rhobar * sq[1] * st->phibar * sq[1];
         }
     }
 }

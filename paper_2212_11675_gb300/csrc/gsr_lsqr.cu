@@ -68,6 +68,7 @@ k_init_u(const SolveArgs *args, double *u, int64_t m, SolveState *st, double *pa
         s.bnorm = s.beta;
         s.rnorm = s.beta;
         s.nonfinite = !isfinite(s.beta);
+        s.ib = (s.beta > 0.0) ? 1.0 / s.beta : 0.0;
         *st = s;
     }
 }
@@ -75,11 +76,11 @@ k_init_u(const SolveArgs *args, double *u, int64_t m, SolveState *st, double *pa
 // v' = p o q / beta_1, alpha_1 = ||v'||; decides istop = 0 (x = 0 exact)
 __global__ void __launch_bounds__(kThreads)
 k_init_v(const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ v,
-         int64_t n, SolveState *st, double *partial, unsigned *counter,
+         int64_t n, SolveState *st, const SolveArgs *args, double *partial, unsigned *counter,
          cudaGraphConditionalHandle loop, int in_graph)
 {
     const double beta = st->beta;
-    const double ib = (beta > 0.0) ? 1.0 / beta : 0.0;
+    const double ib = st->ib;
     double acc[1] = {0.0};
     for (int64_t j = gtid(); j < n; j += gstride()) {
         const double t = p[j] * q[j] * ib;
@@ -92,7 +93,10 @@ k_init_v(const double *__restrict__ p, const double *__restrict__ q, double *__r
         st->rhobar = alpha;
         st->phibar = beta;
         st->arnorm = alpha * beta;
+        st->t = beta * args->isdof;
         st->cy = (beta > 0.0) ? -alpha / beta : 0.0;
+        st->ia = (alpha > 0.0) ? 1.0 / alpha : 1.0;
+        st->t2 = 0.0;
         if (!isfinite(alpha) || st->nonfinite) {
             st->nonfinite = 1;
             st->istop = kIstopNonfinite;
@@ -113,9 +117,8 @@ __global__ void k_vec_b(const double *__restrict__ p, double *__restrict__ v,
                         double *__restrict__ q, int64_t n, int64_t att0,
                         const SolveState *st, int first, double *z, double *var)
 {
-    const double alpha = st->alpha;
-    const double ia = (alpha > 0.0) ? 1.0 / alpha : 1.0;
-    const double t2 = first ? 0.0 : -st->theta / st->rho;
+    const double ia = st->ia;
+    const double t2 = first ? 0.0 : st->t2;
     for (int64_t j = gtid(); j < n; j += gstride()) {
         const double vj = v[j] * ia;
         v[j] = vj;
@@ -130,20 +133,38 @@ __global__ void k_vec_b(const double *__restrict__ p, double *__restrict__ v,
     }
 }
 
+// Scalar recurrences of one LSQR iteration, run by the whole last block of
+// pass A.  The four independent square roots go to four different warps;
+// everything else is one thread, with products by reciprocals already
+// known (1/rho from the aprod 1 pass) instead of divisions, because FP64
+// divisions and square roots are long instruction sequences on this part.
 __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm2,
                              double dd, double zz, cudaGraphConditionalHandle loop, int in_graph)
 {
+    __shared__ double sq[4];
+    const double beta = st->beta_new;
+    const bool upd = beta > 0.0;
+    const double anorm2 = upd ? st->anorm2 + st->alpha * st->alpha + beta * beta : st->anorm2;
+    const double ddnorm = st->ddnorm + dd;
+    if (threadIdx.x == 0)
+        sq[0] = upd ? sqrt(vnorm2) : st->alpha;
+    if (threadIdx.x == 32)
+        sq[1] = sqrt(zz);
+    if (threadIdx.x == 64)
+        sq[2] = sqrt(anorm2);
+    if (threadIdx.x == 96)
+        sq[3] = sqrt(ddnorm);
+    __syncthreads();
+    if (threadIdx.x != 0)
+        return;
     SolveState s = *st;
-    const double beta = s.beta_new;
+    const double alpha = sq[0];
+    const double irho = s.irho;
     const double rho = sqrt(s.rhobar * s.rhobar + beta * beta);
-    const double c = s.rhobar / rho;
-    const double sn = beta / rho;
-    double alpha = s.alpha;
-    if (beta > 0.0) {
-        s.anorm2 += s.alpha * s.alpha + beta * beta;
-        alpha = sqrt(vnorm2);
-    }
+    const double c = s.rhobar * irho;
+    const double sn = beta * irho;
     const double phi = c * s.phibar;
+    s.anorm2 = anorm2;
     s.theta = sn * alpha;
     s.rhobar = -c * alpha;
     s.phibar = sn * s.phibar;
@@ -154,28 +175,30 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
     s.phi = phi;
     s.alpha = alpha;
     s.beta = beta;
-    s.cy = (beta > 0.0) ? -alpha / beta : 0.0;
-    s.ddnorm += dd;
-    s.xnorm = sqrt(zz);
-    s.anorm = sqrt(s.anorm2);
-    s.acond = s.anorm * sqrt(s.ddnorm);
+    s.cy = -alpha * s.ib;
+    s.ddnorm = ddnorm;
+    s.xnorm = sq[1];
+    s.anorm = sq[2];
+    s.acond = s.anorm * sq[3];
+    s.ia = (alpha > 0.0) ? 1.0 / alpha : 1.0;
+    s.t2 = -s.theta * irho;
     s.rnorm = s.phibar;
     s.arnorm = alpha * fabs(tau);
     s.itn += 1;
+    s.t = s.rnorm * args->isdof;
 
-    const double test1 = s.rnorm / s.bnorm;
-    const double test2 = (s.anorm * s.rnorm != 0.0) ? s.arnorm / (s.anorm * s.rnorm) : INFINITY;
-    const double test3 = 1.0 / s.acond;
-    const double t1 = test1 / (1.0 + s.anorm * s.xnorm / s.bnorm);
-    const double rtol = args->btol + args->atol * s.anorm * s.xnorm / s.bnorm;
+    // stopping rules (P&S 1982 §6) in multiplied form; a later rule wins
+    const double anx = s.anorm * s.xnorm;
+    const double rtol_b = args->btol * s.bnorm + args->atol * anx;  // rtol * bnorm
+    const double anr = s.anorm * s.rnorm;
     int istop = 0;
     if (s.itn >= args->itmax) istop = 7;
-    if (1.0 + test3 <= 1.0) istop = 6;
-    if (1.0 + test2 <= 1.0) istop = 5;
-    if (1.0 + t1 <= 1.0) istop = 4;
-    if (test3 <= args->ctol) istop = 3;
-    if (test2 <= args->atol) istop = 2;
-    if (test1 <= rtol) istop = 1;
+    if (1.0 + 1.0 / s.acond <= 1.0) istop = 6;
+    if (anr != 0.0 && 1.0 + s.arnorm / anr <= 1.0) istop = 5;
+    if (1.0 + s.rnorm / (s.bnorm + anx) <= 1.0) istop = 4;
+    if (args->ctol * s.acond >= 1.0 && args->ctol > 0.0) istop = 3;
+    if (anr != 0.0 && s.arnorm <= args->atol * anr) istop = 2;
+    if (s.rnorm <= rtol_b) istop = 1;
     const bool bad = !isfinite(rho) || !isfinite(alpha) || !isfinite(s.phibar) ||
                      !isfinite(s.xnorm) || !isfinite(s.ddnorm) || rho == 0.0;
     if (bad) {
@@ -203,13 +226,10 @@ k_vec_a(const double *__restrict__ p, const double *__restrict__ q, double *__re
         unsigned *counter, cudaGraphConditionalHandle loop, int in_graph)
 {
     const double beta = st->beta_new;
-    const double rhobar = st->rhobar;
-    const double rho = sqrt(rhobar * rhobar + beta * beta);
-    const double phi = (rhobar / rho) * st->phibar;
-    const double t1 = phi / rho;
-    const double irho = 1.0 / rho;
+    const double t1 = st->t1;
+    const double irho = st->irho;
     const bool upd = beta > 0.0;
-    const double ib = upd ? 1.0 / beta : 0.0;
+    const double ib = st->ib;
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t j = gtid(); j < n; j += gstride()) {
         if (upd) {
@@ -225,7 +245,7 @@ k_vec_a(const double *__restrict__ p, const double *__restrict__ q, double *__re
         z[j] = zj;
         acc[2] = fma(zj, zj, acc[2]);
     }
-    if (grid_reduce<3>(acc, partial, counter) && threadIdx.x == 0)
+    if (grid_reduce<3>(acc, partial, counter))
         lsqr_scalars(st, args, acc[0], acc[1], acc[2], loop, in_graph);
 }
 
@@ -236,8 +256,7 @@ __global__ void k_finalize(const double *__restrict__ p, const double *__restric
 {
     double *x = args->x;
     double *se = args->se;
-    const double dof = (m > n) ? (double)(m - n) : 1.0;
-    const double t = st->rnorm / sqrt(dof);
+    const double t = st->t;
     for (int64_t j = gtid(); j < n; j += gstride()) {
         x[j] = p[j] * z[j];
         if (se)
@@ -316,7 +335,7 @@ cudaError_t enqueue_prologue(const gsr_handle_t *h, cudaStream_t s,
     e = launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
     if (e != cudaSuccess)
         return e;
-    k_init_v<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, A.n, h->d_state,
+    k_init_v<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, A.n, h->d_state, h->d_args,
                                                part + kRedV * kPartialsPerKind, cnt + kRedV, loop,
                                                in_graph);
     k_vec_b<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_v, h->d_vp, h->d_w, h->d_q, A.n, A.att0,
