@@ -33,6 +33,8 @@ def lib():
         L.or_n_unknowns.restype = _I
         L.or_aprod1.argtypes = sysargs + [_P, _P]
         L.or_aprod2.argtypes = sysargs + [_P, _P]
+        L.or_aprod1_f32.argtypes = sysargs + [_P, _P]
+        L.or_aprod2_f32.argtypes = sysargs + [_P, _P]
         L.or_colnorms.argtypes = sysargs + [_P]
         L.or_precondition.argtypes = sysargs + [_P, _P]
         L.or_lsqr.argtypes = sysargs + [_P, _I, _D, _D, _D, _P, _P, _P, _P]
@@ -71,6 +73,24 @@ def aprod2(sys, y, x=None, values=None):
     y = np.ascontiguousarray(y, dtype=np.float64)
     x = np.zeros(sys.n) if x is None else np.array(x, dtype=np.float64, copy=True)
     lib().or_aprod2(*a, _ptr(y), _ptr(x))
+    return x
+
+
+def aprod1_f32(sys, x, y=None):
+    """y += A32 x32: binary32 values, vector entries and products, summed in double."""
+    keep, a = _sysargs(sys)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros(sys.m) if y is None else np.array(y, dtype=np.float64, copy=True)
+    lib().or_aprod1_f32(*a, _ptr(x), _ptr(y))
+    return y
+
+
+def aprod2_f32(sys, y, x=None):
+    """x += A32^T y32: binary32 values, vector entries and products, summed in double."""
+    keep, a = _sysargs(sys)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    x = np.zeros(sys.n) if x is None else np.array(x, dtype=np.float64, copy=True)
+    lib().or_aprod2_f32(*a, _ptr(y), _ptr(x))
     return x
 
 

@@ -30,6 +30,11 @@
  *     se_j = p_j * sqrt(var_j) * rnorm / sqrt(m - n)   (m > n; else / 1)
  *   the solution and the standard errors are multiplied by p at the end.
  *
+ *   single-precision products (the inner operator of the mixed-precision
+ *   solve): every value and every vector entry is rounded to IEEE binary32,
+ *   their product is formed in binary32 (round to nearest), and the products
+ *   are summed in double precision in the loop order of Alg. 1 / Alg. 2.
+ *
  * Parity of the standard errors beyond these pins (P&S's var lower bound and
  * its limit diag((A^T A)^-1)) is not fixed by the paper.
  */
@@ -100,6 +105,77 @@ void or_aprod2(int64_t S, int64_t D, int64_t I,
             for (int j = 0; j < N_INSTR; j++, k++)
                 x[ins0 + instr[N_INSTR * i + j]] += a[k] * yi;
             x[glb0] += a[k] * yi;
+        }
+    }
+}
+
+/* y += A32 x32 with binary32 products summed in double (see header) */
+void or_aprod1_f32(int64_t S, int64_t D, int64_t I,
+                   const uint32_t *star_ptr, const uint32_t *attoff,
+                   const uint16_t *instr, const double *values,
+                   const double *x, double *y)
+{
+    const int64_t att0 = N_ASTRO * S;
+    const int64_t ins0 = att0 + N_AXES * D;
+    const int64_t glb0 = ins0 + I;
+    for (int64_t s = 0; s < S; s++) {
+        for (int64_t i = star_ptr[s]; i < (int64_t)star_ptr[s + 1]; i++) {
+            const double *a = values + N_PAR * i;
+            double sum = 0.0;
+            int64_t k = 0;
+            for (int j = 0; j < N_ASTRO; j++, k++) {
+                volatile float pr = (float)a[k] * (float)x[N_ASTRO * s + j];
+                sum += (double)pr;
+            }
+            for (int ax = 0; ax < N_AXES; ax++)
+                for (int j = 0; j < N_PARAXIS; j++, k++) {
+                    volatile float pr = (float)a[k] * (float)x[att0 + ax * D + attoff[i] + j];
+                    sum += (double)pr;
+                }
+            for (int j = 0; j < N_INSTR; j++, k++) {
+                volatile float pr = (float)a[k] * (float)x[ins0 + instr[N_INSTR * i + j]];
+                sum += (double)pr;
+            }
+            {
+                volatile float pr = (float)a[k] * (float)x[glb0];
+                sum += (double)pr;
+            }
+            y[i] += sum;
+        }
+    }
+}
+
+/* x += A32^T y32 with binary32 products summed in double */
+void or_aprod2_f32(int64_t S, int64_t D, int64_t I,
+                   const uint32_t *star_ptr, const uint32_t *attoff,
+                   const uint16_t *instr, const double *values,
+                   const double *y, double *x)
+{
+    const int64_t att0 = N_ASTRO * S;
+    const int64_t ins0 = att0 + N_AXES * D;
+    const int64_t glb0 = ins0 + I;
+    for (int64_t s = 0; s < S; s++) {
+        for (int64_t i = star_ptr[s]; i < (int64_t)star_ptr[s + 1]; i++) {
+            const double *a = values + N_PAR * i;
+            const float yi = (float)y[i];
+            int64_t k = 0;
+            for (int j = 0; j < N_ASTRO; j++, k++) {
+                volatile float pr = (float)a[k] * yi;
+                x[N_ASTRO * s + j] += (double)pr;
+            }
+            for (int ax = 0; ax < N_AXES; ax++)
+                for (int j = 0; j < N_PARAXIS; j++, k++) {
+                    volatile float pr = (float)a[k] * yi;
+                    x[att0 + ax * D + attoff[i] + j] += (double)pr;
+                }
+            for (int j = 0; j < N_INSTR; j++, k++) {
+                volatile float pr = (float)a[k] * yi;
+                x[ins0 + instr[N_INSTR * i + j]] += (double)pr;
+            }
+            {
+                volatile float pr = (float)a[k] * yi;
+                x[glb0] += (double)pr;
+            }
         }
     }
 }

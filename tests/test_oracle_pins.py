@@ -223,3 +223,37 @@ def test_zero_rhs_gives_istop_zero():
     r = oracle.pc_lsqr(sys, np.zeros(sys.m), 10)
     assert r["istop"] == 0 and r["itn"] == 0
     assert not r["x"].any()
+
+
+def test_single_precision_products_dense_restatement():
+    """The binary32-product operator against a dense NumPy restatement:
+    float32 elementwise products, summed in float64."""
+    sys = small(20, 10, 9)
+    cols = columns(sys)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(sys.n)
+    y = rng.standard_normal(sys.m)
+    a32 = sys.values.astype(np.float32)
+    prod1 = (a32 * x.astype(np.float32)[cols]).astype(np.float64)      # float32 products
+    np.testing.assert_allclose(oracle.aprod1_f32(sys, x), prod1.sum(axis=1), rtol=1e-14, atol=1e-13)
+    prod2 = (a32 * y.astype(np.float32)[:, None]).astype(np.float64)
+    ref2 = np.zeros(sys.n)
+    np.add.at(ref2, cols.ravel(), prod2.ravel())
+    np.testing.assert_allclose(oracle.aprod2_f32(sys, y), ref2, rtol=1e-13, atol=1e-12)
+
+
+def test_single_precision_products_exact_on_small_integers():
+    """Small-integer values and vectors have exact binary32 products: the
+    binary32-product operator then equals the FP64 one exactly."""
+    sys = small(15, 8, 7)
+    rng = np.random.default_rng(6)
+    sys.values = rng.integers(-7, 8, size=sys.values.shape).astype(np.float64)
+    x = rng.integers(-9, 10, size=sys.n).astype(np.float64)
+    y = rng.integers(-9, 10, size=sys.m).astype(np.float64)
+    np.testing.assert_array_equal(oracle.aprod1_f32(sys, x), oracle.aprod1(sys, x))
+    np.testing.assert_array_equal(oracle.aprod2_f32(sys, y), oracle.aprod2(sys, y))
+    # and it differs from FP64 by single-precision rounding on general inputs
+    sys2 = small(15, 8, 7)
+    xg = rng.standard_normal(sys2.n)
+    d = np.abs(oracle.aprod1_f32(sys2, xg) - oracle.aprod1(sys2, xg))
+    assert 0 < d.max() < 1e-5 * np.abs(oracle.aprod1(sys2, xg)).max()
