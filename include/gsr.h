@@ -58,7 +58,9 @@ extern "C" {
 #define GSR_INSTR_REPLICAS 2 /* one replica per SM in device memory, L2 reductions */
 
 /* Storage and arithmetic of the matrix values. */
-#define GSR_PREC_FP64 0 /* IEEE double values, native FP64 arithmetic */
+#define GSR_PREC_FP64 0  /* IEEE double values, native FP64 arithmetic */
+#define GSR_PREC_MIXED 1 /* as FP64, plus a binary32 copy of the values for the
+                            inner iterations of gsr_mixed_solve */
 
 typedef struct {
     int64_t n_stars;  /* S >= 1 */
@@ -181,6 +183,46 @@ int gsr_lsqr_solve(void *h, const double *b, int itmax, double atol,
  */
 int gsr_aprod1_norm_noalloc(void *h, const double *x, double *y, double cy,
                             double *ynorm, void *stream);
+
+typedef struct {
+    int converged;  /* 1 when the refinement stopping rule was met */
+    int outer;      /* refinement steps done */
+    int inner;      /* conjugate-gradient iterations in total */
+    double rnorm;   /* ||b - A x|| of the returned x, in FP64 */
+    double arnorm;  /* ||diag(p) A^T (b - A x)||, in FP64 */
+    double anorm;   /* ||A diag(p)||_F = sqrt(number of nonempty columns) */
+} gsr_mixed_result;
+
+/*
+ * The products of Alg. 1 / Alg. 2 on the binary32 copy A32 of A, the inner
+ * operator of gsr_mixed_solve: values and vector entries are rounded to
+ * binary32, each product is formed in binary32 and the products are summed
+ * with double-float (FP64-class) accumulation.  y[m] += A32 x[n] and
+ * x[n] += A32^T y[m].  Handles created with GSR_PREC_MIXED only
+ * (GSR_ERR_UNSUPPORTED otherwise).  Binary32 subnormal products (below
+ * 1.2e-38 in magnitude) of the instrumental columns count as zero.
+ */
+int gsr_aprod1_f32(void *h, const double *x, double *y, void *stream);
+int gsr_aprod2_f32(void *h, const double *y, double *x, void *stream);
+
+/*
+ * Mixed-precision PC least squares: the FP64 solution of min ||A x - b||
+ * (the same solution as gsr_lsqr_solve at convergence), with binary32 values
+ * in the inner iterations.  Outer loop in FP64 (iterative refinement of the
+ * normal equations): r = b - A x, c = diag(p) A^T r; stop when
+ * ||c|| <= atol * ||A diag(p)||_F * ||r|| (Paige & Saunders' rule S2 on
+ * exact terms) or after max_outer refinement steps; otherwise solve
+ * (diag(p) A32^T A32 diag(p)) z = c by conjugate gradients until
+ * ||residual|| <= inner_tol * ||c|| or max_inner iterations, and set
+ * x += p o z.  The fixed point is A^T (b - A x) = 0 exactly.  x[n] is the
+ * output; no standard errors are produced (use gsr_lsqr_solve).  Handles
+ * created with GSR_PREC_MIXED only.  Errors: GSR_ERR_ARG,
+ * GSR_ERR_UNSUPPORTED, GSR_ERR_NONFINITE, GSR_ERR_CUDA.  Synchronises the
+ * stream once per refinement step.
+ */
+int gsr_mixed_solve(void *h, const double *b, int max_outer, int max_inner,
+                    double inner_tol, double atol, double *x,
+                    gsr_mixed_result *out, void *stream);
 
 /* Text of the last CUDA failure seen by this host thread ("" if none). */
 const char *gsr_last_error(void);

@@ -22,12 +22,13 @@ GSR_ERR_NONFINITE = -6
 GSR_ERR_UNSUPPORTED = -7
 
 GSR_PREC_FP64 = 0
+GSR_PREC_MIXED = 1
 GSR_INSTR_AUTO, GSR_INSTR_SMEM, GSR_INSTR_REPLICAS = 0, 1, 2
 
 EXPORTS = (
     "gsr_config_default", "gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
     "gsr_precondition", "gsr_lsqr_solve", "gsr_last_error", "gsr_info", "gsr_strerror",
-    "gsr_aprod1_norm_noalloc",
+    "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32", "gsr_mixed_solve",
 )
 
 
@@ -48,6 +49,15 @@ class Result(ctypes.Structure):
                 ("arnorm", ctypes.c_double), ("anorm", ctypes.c_double),
                 ("acond", ctypes.c_double), ("xnorm", ctypes.c_double),
                 ("bnorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MixedResult(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("outer", ctypes.c_int), ("inner", ctypes.c_int),
+                ("rnorm", ctypes.c_double), ("arnorm", ctypes.c_double),
+                ("anorm", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,13 +102,17 @@ def lib():
             L.gsr_precondition.argtypes = [P, P, P]
             L.gsr_lsqr_solve.argtypes = [P, P, I, D, D, P, P, ctypes.POINTER(Result), P]
             L.gsr_aprod1_norm_noalloc.argtypes = [P, P, P, D, P, P]
+            L.gsr_aprod1_f32.argtypes = [P, P, P, P]
+            L.gsr_aprod2_f32.argtypes = [P, P, P, P]
+            L.gsr_mixed_solve.argtypes = [P, P, I, I, D, D, P, ctypes.POINTER(MixedResult), P]
             L.gsr_last_error.restype = ctypes.c_char_p
             L.gsr_strerror.argtypes = [I]
             L.gsr_strerror.restype = ctypes.c_char_p
             L.gsr_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
             for name in ("gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
                          "gsr_precondition", "gsr_lsqr_solve", "gsr_info",
-                         "gsr_aprod1_norm_noalloc"):
+                         "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32",
+                         "gsr_mixed_solve"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib

@@ -109,12 +109,22 @@ static void release(gsr_handle_t *h)
     cudaSetDevice(h->device);
     if (h->solve_exec)
         cudaGraphExecDestroy(h->solve_exec);
+    if (h->cg_exec)
+        cudaGraphExecDestroy(h->cg_exec);
+    if (h->h_cg)
+        cudaFreeHost(h->h_cg);
+    if (h->h_cgargs)
+        cudaFreeHost(h->h_cgargs);
+    if (h->h_onorm)
+        cudaFreeHost(h->h_onorm);
     if (h->cap_stream)
         cudaStreamDestroy(h->cap_stream);
     void *dev[] = {h->d_star_ptr, h->d_rec, h->d_val, h->d_tile_star, h->d_tval, h->d_perm,
                    h->d_seg, h->d_attS, h->d_irep, h->d_p, h->d_u, h->d_v, h->d_w, h->d_z,
                    h->d_var, h->d_q, h->d_vp, h->d_vt, h->d_bstage, h->d_xstage, h->d_sestage,
-                   h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err};
+                   h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err,
+                   h->d_val32, h->d_tval32, h->d_x32, h->d_q32, h->d_c, h->d_s, h->d_d, h->d_t,
+                   h->d_zc, h->d_xm, h->d_r, h->d_xneg, h->d_onorm, h->d_cg, h->d_cgargs};
     for (void *p : dev)
         if (p)
             cudaFree(p);
@@ -126,6 +136,51 @@ static void release(gsr_handle_t *h)
     if (cur >= 0)
         cudaSetDevice(cur);
     delete h;
+}
+
+// binary32 copies of the value planes and of the offset-sorted attitude
+// values, the mixed-precision workspace and the inner CG graph
+static int create_mixed(gsr_handle_t *h, cudaStream_t st)
+{
+    SysView &A = h->sys;
+    const int64_t m = A.m, n = A.n, mp = A.mp;
+    TRY(dalloc(h, &h->d_val32, kNPar * mp));
+    TRY(dalloc(h, &h->d_tval32, (int64_t)kNAtt * mp));
+    TRY(dalloc(h, &h->d_x32, n));
+    TRY(dalloc(h, &h->d_q32, m));
+    TRY(dalloc(h, &h->d_c, n));
+    TRY(dalloc(h, &h->d_s, n));
+    TRY(dalloc(h, &h->d_d, n));
+    TRY(dalloc(h, &h->d_t, n));
+    TRY(dalloc(h, &h->d_zc, n));
+    TRY(dalloc(h, &h->d_xm, n));
+    TRY(dalloc(h, &h->d_r, m));
+    TRY(dalloc(h, &h->d_xneg, n));
+    TRY(dalloc(h, &h->d_onorm, 4));
+    TRY(dalloc(h, &h->d_cg, 1));
+    TRY(dalloc(h, &h->d_cgargs, 1));
+    CK(cudaMallocHost((void **)&h->h_cg, sizeof(CgState)));
+    CK(cudaMallocHost((void **)&h->h_cgargs, sizeof(CgArgs)));
+    CK(cudaMallocHost((void **)&h->h_onorm, 4 * sizeof(double)));
+    CK(launch_to_f32(h, h->d_val, h->d_val32, kNPar * mp, st));
+    CK(launch_to_f32(h, h->d_tval, h->d_tval32, kNAtt * mp, st));
+    A.val32 = h->d_val32;
+    A.tval32 = h->d_tval32;
+    // ||A diag(p)||_F^2 = number of nonempty columns (column sums of squares > 0)
+    CK(cudaMemsetAsync(h->d_s, 0, n * sizeof(double), st));
+    CK(launch_aprod2(h, nullptr, h->d_s, kA2Squares, st));
+    CK(launch_count_pos(h, h->d_s, h->d_onorm, st));
+    CK(cudaMemcpyAsync(h->h_onorm, h->d_onorm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h->n_nonempty = h->h_onorm[0];
+    h->grid_rows32 = aprod1_f32_grid(h);
+    h->grid_rows2_32 = aprod2_f32_grid(h);
+    if (h->grid_rows32 <= 0 || h->grid_rows2_32 <= 0)
+        return cuda_fail(cudaGetLastError(), "mixed occupancy");
+    cudaError_t e = build_cg_graph(h);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "build_cg_graph");
+    return GSR_OK;
 }
 
 static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_ptr,
@@ -288,7 +343,7 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     if (gv > (int64_t)h->nsm * 8) gv = (int64_t)h->nsm * 8;
     if (gv > kMaxPartials) gv = kMaxPartials;
     h->grid_vec = (int)(gv < 1 ? 1 : gv);
-    if (!instr_in_smem(h)) {
+    if (!instr_in_smem(h) || h->cfg.precision == GSR_PREC_MIXED) {
         h->nrep = h->nsm;
         TRY(dalloc(h, &h->d_irep, (int64_t)h->nrep * I));
         CK(cudaMemset(h->d_irep, 0, (size_t)h->nrep * I * sizeof(double)));
@@ -300,6 +355,8 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     cudaError_t e = build_solve_graph(h);
     if (e != cudaSuccess)
         return cuda_fail(e, "build_solve_graph");
+    if (h->cfg.precision == GSR_PREC_MIXED)
+        return create_mixed(h, st);
     return GSR_OK;
 }
 
@@ -317,7 +374,7 @@ extern "C" int gsr_create(void **out, const gsr_dims *d, const uint32_t *star_pt
         c = *cfg;
     else
         gsr_config_default(&c);
-    if (c.precision != GSR_PREC_FP64)
+    if (c.precision != GSR_PREC_FP64 && c.precision != GSR_PREC_MIXED)
         return GSR_ERR_UNSUPPORTED;
     if (c.lanes_per_star != 0 && c.lanes_per_star != 4 && c.lanes_per_star != 8 &&
         c.lanes_per_star != 16 && c.lanes_per_star != 32)
@@ -481,4 +538,101 @@ extern "C" int gsr_lsqr_solve(void *hv, const double *b, int itmax, double atol,
         out->bnorm = s.bnorm;
     }
     return s.nonfinite ? GSR_ERR_NONFINITE : GSR_OK;
+}
+
+extern "C" int gsr_aprod1_f32(void *hv, const double *x, double *y, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !x || !y)
+        return GSR_ERR_ARG;
+    if (h->cfg.precision != GSR_PREC_MIXED)
+        return GSR_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *dx, *dy;
+    TRY(stage(h, &h->d_xstage, h->sys.n, x, &dx, true, st));
+    TRY(stage(h, &h->d_ystage, h->sys.m, y, &dy, true, st));
+    CK(launch_aprod1_f32_api(h, dx, dy, st));
+    if (dy != y) {
+        CK(cudaMemcpyAsync(y, dy, h->sys.m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return GSR_OK;
+}
+
+extern "C" int gsr_aprod2_f32(void *hv, const double *y, double *x, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !x || !y)
+        return GSR_ERR_ARG;
+    if (h->cfg.precision != GSR_PREC_MIXED)
+        return GSR_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *dx, *dy;
+    TRY(stage(h, &h->d_ystage, h->sys.m, y, &dy, true, st));
+    TRY(stage(h, &h->d_xstage, h->sys.n, x, &dx, true, st));
+    CK(launch_aprod2_f32_api(h, dy, dx, st));
+    if (dx != x) {
+        CK(cudaMemcpyAsync(x, dx, h->sys.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return GSR_OK;
+}
+
+extern "C" int gsr_mixed_solve(void *hv, const double *b, int max_outer, int max_inner,
+                               double inner_tol, double atol, double *x, gsr_mixed_result *out,
+                               void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !b || !x || max_outer < 0 || max_inner < 1 || !(inner_tol >= 0.0) || !(atol >= 0.0))
+        return GSR_ERR_ARG;
+    if (h->cfg.precision != GSR_PREC_MIXED)
+        return GSR_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const SysView &A = h->sys;
+    double *db;
+    TRY(stage(h, &h->d_bstage, A.m, b, &db, true, st));
+    CK(enqueue_precondition(h, h->d_p, st));
+    CK(cudaMemsetAsync(h->d_xm, 0, A.n * sizeof(double), st));
+    CK(cudaMemcpyAsync(h->d_r, db, A.m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    h->h_cgargs->max_inner = max_inner;
+    h->h_cgargs->tol = inner_tol;
+    CK(cudaMemcpyAsync(h->d_cgargs, h->h_cgargs, sizeof(CgArgs), cudaMemcpyHostToDevice, st));
+    const double anorm = sqrt(h->n_nonempty);
+    gsr_mixed_result res = {};
+    res.anorm = anorm;
+    for (int k = 0;; k++) {
+        // FP64 normal residual c = A^T r and the stopping rule
+        CK(cudaMemsetAsync(h->d_c, 0, A.n * sizeof(double), st));
+        CK(launch_aprod2(h, h->d_r, h->d_c, kA2Accumulate, st));
+        CK(launch_outer_norms(h, h->d_r, st));
+        CK(cudaMemcpyAsync(h->h_onorm, h->d_onorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        res.arnorm = sqrt(h->h_onorm[0]);
+        res.rnorm = sqrt(h->h_onorm[1]);
+        if (!isfinite(res.arnorm) || !isfinite(res.rnorm))
+            return GSR_ERR_NONFINITE;
+        if (res.arnorm <= atol * anorm * res.rnorm) {
+            res.converged = 1;
+            break;
+        }
+        if (k >= max_outer)
+            break;
+        // inner CG on (diag(p) A32^T A32 diag(p)) z = p o c, then x += p o z
+        CK(run_cg(h, st, max_inner));
+        CK(cudaMemcpyAsync(h->h_cg, h->d_cg, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+        // r = b - A x in FP64
+        CK(cudaMemcpyAsync(h->d_r, db, A.m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(launch_neg(h, h->d_xm, h->d_xneg, A.n, st));
+        CK(launch_aprod1(h, h->d_xneg, h->d_r, 0, st));
+        CK(cudaStreamSynchronize(st));
+        if (h->h_cg->nonfinite)
+            return GSR_ERR_NONFINITE;
+        res.outer = k + 1;
+        res.inner += h->h_cg->it;
+    }
+    CK(cudaMemcpyAsync(x, h->d_xm, A.n * sizeof(double), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    if (out)
+        *out = res;
+    return GSR_OK;
 }

@@ -23,6 +23,8 @@ struct SysView {
     const uint32_t *star_ptr;  // [S+1]
     const uint4 *rec;          // [m]
     const double *val;         // [24][mp] value planes (plane k = nonzero k)
+    const float *val32;        // [24][mp] binary32 copy (mixed precision), or null
+    const float *tval32;       // [12][mp] binary32 offset-sorted attitude copy, or null
     const uint32_t *tile_star; // [ceil(m/32)] star of the first row of each 32-row tile
     // attitude values re-ordered by attitude offset (stable in the row index):
     // entry e is row perm[e]; offset o owns entries seg[o] .. seg[o+1]-1
@@ -54,6 +56,17 @@ struct SolveState {
     double ia;                 // 1/alpha (1 if alpha = 0)
     double t2;                 // -theta/rho for the w update
     int itn, istop, done, nonfinite;
+};
+
+// Conjugate-gradient state of the mixed-precision inner solve.
+struct CgState {
+    double gamma, gamma0, stop2;  // |s|^2, its start value, tol^2 |s_0|^2
+    double xi, alpha, beta;       // |q|^2, step, direction update
+    int it, done, nonfinite, pad;
+};
+struct CgArgs {
+    int max_inner;
+    double tol;
 };
 
 // Per-solve arguments, read by the graph's kernels from device memory so one
@@ -96,6 +109,17 @@ struct gsr_handle_t {
     double *d_attS = nullptr;           // [nseg][12] attitude segment sums
     double *d_irep = nullptr;           // [nrep][I] instrumental replicas
     int nrep = 0;
+    // mixed precision
+    float *d_val32 = nullptr, *d_tval32 = nullptr;
+    float *d_x32 = nullptr, *d_q32 = nullptr;
+    double *d_c = nullptr, *d_s = nullptr, *d_d = nullptr, *d_t = nullptr, *d_zc = nullptr;
+    double *d_xm = nullptr, *d_r = nullptr, *d_xneg = nullptr, *d_onorm = nullptr;
+    gsr::CgState *d_cg = nullptr, *h_cg = nullptr;
+    gsr::CgArgs *d_cgargs = nullptr, *h_cgargs = nullptr;
+    double *h_onorm = nullptr;
+    cudaGraphExec_t cg_exec = nullptr;
+    int grid_rows32 = 0, grid_rows2_32 = 0;
+    double n_nonempty = 0.0;
     double *d_p = nullptr;              // preconditioner
     double *d_u = nullptr;              // m
     double *d_v = nullptr, *d_w = nullptr, *d_z = nullptr, *d_var = nullptr;
@@ -132,6 +156,20 @@ cudaError_t launch_tile_star(const gsr_handle_t *h, cudaStream_t st);
 cudaError_t launch_gather_att(const gsr_handle_t *h, cudaStream_t st);
 int aprod1_grid(const gsr_handle_t *h);
 bool instr_in_smem(const gsr_handle_t *h);
+cudaError_t launch_att_combine(const gsr_handle_t *h, double *out, int nb_att, int nb_ins,
+                               bool accumulate, cudaStream_t st);
+// mixed precision (gsr_mixed.cu)
+cudaError_t launch_aprod1_f32_api(const gsr_handle_t *h, const double *x, double *y, cudaStream_t st);
+cudaError_t launch_aprod2_f32_api(const gsr_handle_t *h, const double *y, double *x, cudaStream_t st);
+cudaError_t build_cg_graph(gsr_handle_t *h);
+cudaError_t run_cg(gsr_handle_t *h, cudaStream_t st, int max_inner);
+cudaError_t launch_outer_norms(const gsr_handle_t *h, const double *r, cudaStream_t st);
+cudaError_t launch_neg(const gsr_handle_t *h, const double *a, double *b, int64_t n, cudaStream_t st);
+cudaError_t launch_count_pos(const gsr_handle_t *h, const double *a, double *out, cudaStream_t st);
+cudaError_t launch_to_f32(const gsr_handle_t *h, const double *a, float *b, int64_t n, cudaStream_t st);
+int aprod1_f32_grid(const gsr_handle_t *h);
+int aprod2_f32_grid(const gsr_handle_t *h);
+cudaError_t enqueue_precondition(const gsr_handle_t *h, double *p, cudaStream_t st);
 // LSQR pieces (gsr_lsqr.cu)
 cudaError_t build_solve_graph(gsr_handle_t *h);
 cudaError_t enqueue_prologue(const gsr_handle_t *h, cudaStream_t s,

@@ -473,7 +473,13 @@ cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out, i
                                  ? (3 * h->sys.D + kThreads - 1) / kThreads
                                  : 4 * h->nsm);
     const int nb_ins = instr_in_smem(h) ? 0 : (int)((h->sys.I + 31) / 32);
-    if (mode == kA2Accumulate)
+    return launch_att_combine(h, out, nb_att, nb_ins, mode == kA2Accumulate, st);
+}
+
+cudaError_t launch_att_combine(const gsr_handle_t *h, double *out, int nb_att, int nb_ins,
+                               bool accumulate, cudaStream_t st)
+{
+    if (accumulate)
         k_att_combine<true><<<nb_att + nb_ins, kThreads, 0, st>>>(h->sys, h->d_attS, out,
                                                                    h->d_irep, h->nrep, nb_att);
     else

@@ -286,7 +286,7 @@ cudaError_t enqueue_precondition(const gsr_handle_t *h, double *p, cudaStream_t 
     return enqueue_precond(h, p, st);
 }
 
-static cudaError_t find_leaf(cudaGraph_t g, cudaGraphNode_t *leaf)
+cudaError_t find_graph_leaf(cudaGraph_t g, cudaGraphNode_t *leaf)
 {
     size_t nn = 0;
     cudaError_t e = cudaGraphGetNodes(g, nullptr, &nn);
@@ -388,7 +388,7 @@ cudaError_t build_solve_graph(gsr_handle_t *h)
     GSR_TRY(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     enqueue_prologue(h, s, loop, 1);
     GSR_TRY(cudaStreamEndCapture(s, &g));
-    GSR_TRY(find_leaf(g, &pre_leaf));
+    GSR_TRY(find_graph_leaf(g, &pre_leaf));
 
     // WHILE node: one LSQR iteration per trip
     cp.type = cudaGraphNodeTypeConditional;

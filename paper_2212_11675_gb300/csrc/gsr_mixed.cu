@@ -1,0 +1,610 @@
+// Mixed-precision PC solve: binary32 storage of A for the inner iterations,
+// FP64 refinement of the normal-equation residual.
+//
+// Inner operator (the products of aprod 1 / aprod 2 of Alg. 1 / Alg. 2 on
+// the binary32 copy A32 of A): every product of a binary32 value with a
+// binary32 vector entry is formed in binary32, and the products are
+// accumulated as double-float pairs (hi + lo, Knuth's error-free TwoSum) on
+// the FP32 pipes, which is as accurate as FP64 accumulation for these sums.
+// GB300 runs FP64 at 2 FMA per clock per SM and FP32 at 128, so the inner
+// passes stay on the FP32 pipes and read half the bytes of the FP64 form.
+//
+// Outer loop (host driven, FP64): with p the column-norm preconditioner,
+//   r = b - A x,  c = p o (A^T r)         (FP64 kernels of gsr_kernels.cu)
+//   stop when ||c|| <= atol ||A diag(p)||_F ||r||   (P&S rule S2, exact terms)
+//   solve (diag(p) A32^T A32 diag(p)) z = c approximately by CG
+//   x += p o z
+// The fixed point is A^T (b - A x) = 0, the FP64 least-squares solution.
+//
+// CG on the normal equations (Hestenes-Stiefel) with s_0 = c, d_0 = s_0:
+//   q = A32 (p o d), alpha = |s|^2 / |q|^2, z += alpha d,
+//   s -= alpha p o (A32^T q), beta = |s_new|^2 / |s|^2, d = s + beta d.
+// One inner iteration = 4 launches in a CUDA graph with a conditional WHILE
+// node, like the LSQR loop.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gsr_internal.cuh"
+#include "gsr_reduce.cuh"
+
+namespace gsr {
+
+// ---------------------------------------------------------------------------
+// double-float helpers (round-to-nearest intrinsics keep the compiler from
+// contracting or reassociating the error-free transformations)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_acc(float &hi, float &lo, float p)
+{
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+// exact binary32 -> binary64 by bit manipulation on the integer pipe (the
+// FP64 pipe converts at 2 per clock per SM); binary32 subnormals, which need
+// a renormalisation, become signed zero (|value| < 1.2e-38)
+__device__ __forceinline__ double f2d(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    const uint32_t sign = u & 0x80000000u;
+    const uint32_t mant = u & 0x7fffffu;
+    const uint32_t e64 = (e == 0xffu) ? 0x7ffu : (e + (1023u - 127u));
+    const uint32_t hi = (e == 0u) ? sign : (sign | (e64 << 20) | (mant >> 3));
+    const uint32_t lo = (e == 0u) ? 0u : (mant << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ double df_to_d(float hi, float lo) { return f2d(hi) + f2d(lo); }
+
+__device__ __forceinline__ uint32_t instr_at32(const uint4 &rc, int j)
+{
+    const uint32_t w = (j < 2) ? rc.y : ((j < 4) ? rc.z : rc.w);
+    return (j & 1) ? (w >> 16) : (w & 0xffffu);
+}
+
+constexpr int64_t kSmemInstrMax32 = 12288;  // binary32 instrument entries in shared memory
+
+// ---------------------------------------------------------------------------
+// inner aprod 1: row-parallel, binary32 products, double-float sums.
+// MODE 0: y (FP64) += A32 x32.  MODE 1 (CG): q32 = fl32(A32 x32), |q|^2
+// reduced and alpha = gamma / |q|^2 stored by the last block.
+// ---------------------------------------------------------------------------
+template <int MODE, bool SMEMX>
+__global__ void __launch_bounds__(kThreads)
+k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
+             float *__restrict__ q32, CgState *cg, double *partial, unsigned *counter)
+{
+    extern __shared__ float s_x32[];
+    if (SMEMX) {
+        for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x)
+            s_x32[f] = x32[A.ins0 + f];
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t ntiles = (A.m + 31) >> 5;
+    const int64_t mp = A.mp;
+    const float xg = __ldg(x32 + A.glb0);
+    double nrm = 0.0;
+    for (int64_t t = warp; t < ntiles; t += nwarps) {
+        const int64_t r = (t << 5) + lane;
+        if (r < A.m) {
+            uint32_t s = A.tile_star[t];
+            while ((int64_t)A.star_ptr[s + 1] <= r)
+                ++s;
+            const uint4 rc = __ldcs(A.rec + r);
+            const float *v = A.val32 + r;
+            float vk[kNPar];
+#pragma unroll
+            for (int k = 0; k < kNPar; k++)
+                vk[k] = __ldcs(v + k * mp);
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;  // two independent pairs
+            const float *xs = x32 + (int64_t)kNAstro * s;
+#pragma unroll
+            for (int k = 0; k < kNAstro; k++)
+                df_acc(h0, l0, __fmul_rn(vk[k], __ldg(xs + k)));
+            const float *xa = x32 + A.att0 + rc.x;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    df_acc(h1, l1, __fmul_rn(vk[5 + 4 * a + j], __ldg(xa + a * A.D + j)));
+#pragma unroll
+            for (int j = 0; j < kNInstr; j++) {
+                const uint32_t f = instr_at32(rc, j);
+                df_acc(h0, l0, __fmul_rn(vk[17 + j], SMEMX ? s_x32[f] : __ldg(x32 + A.ins0 + f)));
+            }
+            df_acc(h1, l1, __fmul_rn(vk[23], xg));
+            // combine the two pairs
+            df_acc(h0, l0, h1);
+            l0 = __fadd_rn(l0, l1);
+            if (MODE == 0) {
+                y[r] += df_to_d(h0, l0);
+            } else {
+                const float qv = __fadd_rn(h0, l0);
+                q32[r] = qv;
+                const double qd = f2d(qv);
+                nrm = fma(qd, qd, nrm);
+            }
+        }
+    }
+    if (MODE == 1) {
+        double v1[1] = {nrm};
+        if (grid_reduce<1>(v1, partial, counter) && threadIdx.x == 0) {
+            const double xi = v1[0];
+            cg->xi = xi;
+            cg->alpha = (xi > 0.0) ? cg->gamma / xi : 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inner aprod 2, star-parallel over astrometric, instrumental and global
+// nonzeros.  MODE kA2Accumulate: out += A32^T y32.  kA2Overwrite: astro
+// part written, instrumental/global accumulated into zeroed memory.
+// Instrumental products go to per-SM replicas (FP64 reductions in L2).
+// ---------------------------------------------------------------------------
+template <int G, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict__ out,
+                   double *__restrict__ rep, int nrep)
+{
+    __shared__ double s_red[kThreads / 32];
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & (G - 1);
+    const int gw = (threadIdx.x & 31) / G;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t mp = A.mp;
+    double *myrep = rep + (int64_t)(blockIdx.x % nrep) * A.I;
+    float gh = 0.f, gl = 0.f;
+
+    for (int64_t s0 = warp * GPW; s0 < A.S; s0 += nwarps * GPW) {
+        const int64_t s = s0 + gw;
+        uint32_t r0 = 0, r1 = 0;
+        if (s < A.S) {
+            r0 = A.star_ptr[s];
+            r1 = A.star_ptr[s + 1];
+        }
+        float ah[kNAstro], al[kNAstro];
+#pragma unroll
+        for (int k = 0; k < kNAstro; k++)
+            ah[k] = al[k] = 0.f;
+        for (uint32_t r = r0 + lane; r < r1; r += G) {
+            const uint4 rc = __ldcs(A.rec + r);
+            const float *v = A.val32 + r;
+            const float yi = __ldcs(y32 + r);
+#pragma unroll
+            for (int k = 0; k < kNAstro; k++)
+                df_acc(ah[k], al[k], __fmul_rn(__ldcs(v + k * mp), yi));
+#pragma unroll
+            for (int j = 0; j < kNInstr; j++) {
+                const float pr = __fmul_rn(__ldcs(v + (17 + j) * mp), yi);
+                atomicAdd(myrep + instr_at32(rc, j), f2d(pr));
+            }
+            df_acc(gh, gl, __fmul_rn(__ldcs(v + 23 * mp), yi));
+        }
+        double a0 = df_to_d(ah[0], al[0]), a1 = df_to_d(ah[1], al[1]), a2 = df_to_d(ah[2], al[2]);
+        double a3 = df_to_d(ah[3], al[3]), a4 = df_to_d(ah[4], al[4]);
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+            a3 += __shfl_xor_sync(0xffffffffu, a3, off);
+            a4 += __shfl_xor_sync(0xffffffffu, a4, off);
+        }
+        if (lane == 0 && s < A.S) {
+            double *xs = out + kNAstro * s;
+            if (MODE == kA2Accumulate) {
+                xs[0] += a0; xs[1] += a1; xs[2] += a2; xs[3] += a3; xs[4] += a4;
+            } else {
+                xs[0] = a0; xs[1] = a1; xs[2] = a2; xs[3] = a3; xs[4] = a4;
+            }
+        }
+    }
+    double g = warp_sum(df_to_d(gh, gl));
+    if ((threadIdx.x & 31) == 0)
+        s_red[threadIdx.x >> 5] = g;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; w++)
+            t += s_red[w];
+        atomicAdd(out + A.glb0, t);
+    }
+}
+
+// inner aprod 2, attitude part over the offset-sorted binary32 copy
+__global__ void __launch_bounds__(kThreads)
+k_att_segments_f32(SysView A, const float *__restrict__ y32, double *__restrict__ S)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t mp = A.mp;
+    for (int64_t o = warp; o < A.nseg; o += nwarps) {
+        const uint32_t e0 = A.seg[o], e1 = A.seg[o + 1];
+        float h[kNAtt], l[kNAtt];
+#pragma unroll
+        for (int k = 0; k < kNAtt; k++)
+            h[k] = l[k] = 0.f;
+        for (uint32_t e = e0 + lane; e < e1; e += 32) {
+            const float yi = __ldg(y32 + __ldcs(A.perm + e));
+#pragma unroll
+            for (int k = 0; k < kNAtt; k++)
+                df_acc(h[k], l[k], __fmul_rn(__ldcs(A.tval32 + k * mp + e), yi));
+        }
+        double r16[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            r16[k] = k < kNAtt ? df_to_d(h[k], l[k]) : 0.0;
+#pragma unroll
+        for (int half = 8; half >= 1; half >>= 1) {
+            const bool upper = (lane & (2 * half)) != 0;
+#pragma unroll
+            for (int k = 0; k < half; k++) {
+                const double send = upper ? r16[k] : r16[k + half];
+                const double keep = upper ? r16[k + half] : r16[k];
+                r16[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * half);
+            }
+        }
+        const double tot = r16[0] + __shfl_xor_sync(0xffffffffu, r16[0], 1);
+        const int kk = lane >> 1;
+        if ((lane & 1) == 0 && kk < kNAtt)
+            S[o * kNAtt + kk] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// vector kernels (FP64)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t gtid32() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride32() { return (int64_t)gridDim.x * blockDim.x; }
+
+__global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n)
+{
+    for (int64_t j = gtid32(); j < n; j += gstride32())
+        b[j] = __double2float_rn(a[j]);
+}
+
+// s = p o c, d = s, z = 0, xp32 = fl32(p o d), gamma = |s|^2; clears the
+// instrumental/global part of t for the first inner aprod 2
+__global__ void __launch_bounds__(kThreads)
+k_cg_init(const double *__restrict__ p, const double *__restrict__ c, double *__restrict__ s,
+          double *__restrict__ d, double *__restrict__ z, float *__restrict__ xp32,
+          double *__restrict__ t, int64_t n, int64_t ins0, CgState *cg, const CgArgs *args,
+          double *partial, unsigned *counter, cudaGraphConditionalHandle loop, int in_graph)
+{
+    double acc[1] = {0.0};
+    for (int64_t j = gtid32(); j < n; j += gstride32()) {
+        const double sj = p[j] * c[j];
+        s[j] = sj;
+        d[j] = sj;
+        z[j] = 0.0;
+        xp32[j] = __double2float_rn(p[j] * sj);
+        if (j >= ins0)
+            t[j] = 0.0;
+        acc[0] = fma(sj, sj, acc[0]);
+    }
+    if (grid_reduce<1>(acc, partial, counter) && threadIdx.x == 0) {
+        CgState g = {};
+        g.gamma = acc[0];
+        g.gamma0 = acc[0];
+        g.stop2 = args->tol * args->tol * acc[0];
+        if (!(acc[0] > 0.0) || args->max_inner < 1) {
+            g.done = 1;
+            if (in_graph)
+                cudaGraphSetConditional(loop, 0u);
+        }
+        *cg = g;
+    }
+}
+
+// s -= alpha p o t, z += alpha d, gamma' = |s|^2; the last block forms beta
+// and applies the inner stopping rule
+__global__ void __launch_bounds__(kThreads)
+k_cg_vec1(const double *__restrict__ p, const double *__restrict__ t, double *__restrict__ s,
+          const double *__restrict__ d, double *__restrict__ z, int64_t n, CgState *cg,
+          const CgArgs *args, double *partial, unsigned *counter,
+          cudaGraphConditionalHandle loop, int in_graph)
+{
+    const double alpha = cg->alpha;
+    double acc[1] = {0.0};
+    for (int64_t j = gtid32(); j < n; j += gstride32()) {
+        const double sj = fma(-alpha, p[j] * t[j], s[j]);
+        s[j] = sj;
+        z[j] = fma(alpha, d[j], z[j]);
+        acc[0] = fma(sj, sj, acc[0]);
+    }
+    if (grid_reduce<1>(acc, partial, counter) && threadIdx.x == 0) {
+        CgState g = *cg;
+        const double gnew = acc[0];
+        g.beta = gnew / g.gamma;
+        g.gamma = gnew;
+        g.it += 1;
+        const bool bad = !isfinite(gnew) || !isfinite(g.alpha);
+        if (bad)
+            g.nonfinite = 1;
+        if (bad || g.it >= args->max_inner || gnew <= g.stop2 || g.xi <= 0.0) {
+            g.done = 1;
+            if (in_graph)
+                cudaGraphSetConditional(loop, 0u);
+        }
+        *cg = g;
+    }
+}
+
+// d = s + beta d, xp32 = fl32(p o d); clears the instrumental/global part of t
+__global__ void k_cg_vec2(const double *__restrict__ p, const double *__restrict__ s,
+                          double *__restrict__ d, float *__restrict__ xp32, double *__restrict__ t,
+                          int64_t n, int64_t ins0, const CgState *cg)
+{
+    const double beta = cg->beta;
+    for (int64_t j = gtid32(); j < n; j += gstride32()) {
+        const double dj = fma(beta, d[j], s[j]);
+        d[j] = dj;
+        xp32[j] = __double2float_rn(p[j] * dj);
+        if (j >= ins0)
+            t[j] = 0.0;
+    }
+}
+
+// x += p o z
+__global__ void k_axpy_p(const double *__restrict__ p, const double *__restrict__ z,
+                         double *__restrict__ x, int64_t n)
+{
+    for (int64_t j = gtid32(); j < n; j += gstride32())
+        x[j] = fma(p[j], z[j], x[j]);
+}
+
+// y = b - y_neg_source ... (r = b; r -= A x is done as r = b, aprod1 with -x)
+__global__ void k_neg(const double *__restrict__ a, double *__restrict__ b, int64_t n)
+{
+    for (int64_t j = gtid32(); j < n; j += gstride32())
+        b[j] = -a[j];
+}
+
+// |p o c|^2 and |r|^2 for the outer stopping rule
+__global__ void __launch_bounds__(kThreads)
+k_outer_norms(const double *__restrict__ p, const double *__restrict__ c, int64_t n,
+              const double *__restrict__ r, int64_t m, double *out2, double *partial,
+              unsigned *counter)
+{
+    double acc[2] = {0.0, 0.0};
+    for (int64_t j = gtid32(); j < n; j += gstride32()) {
+        const double v = p[j] * c[j];
+        acc[0] = fma(v, v, acc[0]);
+    }
+    for (int64_t i = gtid32(); i < m; i += gstride32())
+        acc[1] = fma(r[i], r[i], acc[1]);
+    if (grid_reduce<2>(acc, partial, counter) && threadIdx.x == 0) {
+        out2[0] = acc[0];
+        out2[1] = acc[1];
+    }
+}
+
+// number of nonempty columns from the column sums of squares
+__global__ void k_count_pos(const double *__restrict__ a, int64_t n, double *partial,
+                            unsigned *counter, double *out)
+{
+    double acc[1] = {0.0};
+    for (int64_t j = gtid32(); j < n; j += gstride32())
+        acc[0] += (a[j] > 0.0) ? 1.0 : 0.0;
+    if (grid_reduce<1>(acc, partial, counter) && threadIdx.x == 0)
+        *out = acc[0];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+bool x32_in_smem(const gsr_handle_t *h) { return h->sys.I <= kSmemInstrMax32; }
+
+template <int MODE>
+static cudaError_t a1f_launch(const gsr_handle_t *h, const float *x32, double *y, float *q32,
+                              cudaStream_t st)
+{
+    double *part = h->d_partial + kRedU * kPartialsPerKind;
+    unsigned *cnt = h->d_counter + kRedU;
+    if (x32_in_smem(h))
+        k_aprod1_f32<MODE, true><<<h->grid_rows32, kThreads, (size_t)h->sys.I * sizeof(float), st>>>(
+            h->sys, x32, y, q32, h->d_cg, part, cnt);
+    else
+        k_aprod1_f32<MODE, false><<<h->grid_rows32, kThreads, 0, st>>>(h->sys, x32, y, q32, h->d_cg,
+                                                                        part, cnt);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t a2f_launch(const gsr_handle_t *h, const float *y32, double *out, cudaStream_t st)
+{
+    const int G = 8;
+    k_aprod2_f32_stars<G, MODE><<<h->grid_rows2_32, kThreads, 0, st>>>(h->sys, y32, out, h->d_irep,
+                                                                        h->nrep);
+    k_att_segments_f32<<<h->grid_att, kThreads, 0, st>>>(h->sys, y32, h->d_attS);
+    const int nb_att = (int)((3 * h->sys.D + kThreads - 1) / kThreads < 4 * h->nsm
+                                 ? (3 * h->sys.D + kThreads - 1) / kThreads
+                                 : 4 * h->nsm);
+    const int nb_ins = (int)((h->sys.I + 31) / 32);
+    launch_att_combine(h, out, nb_att, nb_ins, MODE == kA2Accumulate, st);
+    return cudaGetLastError();
+}
+
+// API forms (FP64 vectors in and out)
+cudaError_t launch_aprod1_f32_api(const gsr_handle_t *h, const double *x, double *y, cudaStream_t st)
+{
+    k_to_f32<<<h->grid_vec, kThreads, 0, st>>>(x, h->d_x32, h->sys.n);
+    return a1f_launch<0>(h, h->d_x32, y, nullptr, st);
+}
+
+cudaError_t launch_aprod2_f32_api(const gsr_handle_t *h, const double *y, double *x, cudaStream_t st)
+{
+    k_to_f32<<<h->grid_vec, kThreads, 0, st>>>(y, h->d_q32, h->sys.m);
+    return a2f_launch<kA2Accumulate>(h, h->d_q32, x, st);
+}
+
+static cudaError_t cg_prologue(const gsr_handle_t *h, cudaStream_t s, cudaGraphConditionalHandle loop,
+                               int in_graph)
+{
+    const SysView &A = h->sys;
+    k_cg_init<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_c, h->d_s, h->d_d, h->d_zc, h->d_x32,
+                                                h->d_t, A.n, A.ins0, h->d_cg, h->d_cgargs,
+                                                h->d_partial + kRedBnorm * kPartialsPerKind,
+                                                h->d_counter + kRedBnorm, loop, in_graph);
+    return cudaGetLastError();
+}
+
+static cudaError_t cg_iteration(const gsr_handle_t *h, cudaStream_t s, cudaGraphConditionalHandle loop,
+                                int in_graph)
+{
+    const SysView &A = h->sys;
+    cudaError_t e = a1f_launch<1>(h, h->d_x32, nullptr, h->d_q32, s);
+    if (e == cudaSuccess)
+        e = a2f_launch<kA2Overwrite>(h, h->d_q32, h->d_t, s);
+    if (e != cudaSuccess)
+        return e;
+    k_cg_vec1<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc, A.n, h->d_cg,
+                                                h->d_cgargs, h->d_partial + kRedV * kPartialsPerKind,
+                                                h->d_counter + kRedV, loop, in_graph);
+    k_cg_vec2<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_s, h->d_d, h->d_x32, h->d_t, A.n, A.ins0,
+                                                h->d_cg);
+    return cudaGetLastError();
+}
+
+#define CG_TRY(x)                       \
+    do {                                \
+        cudaError_t e_ = (x);           \
+        if (e_ != cudaSuccess) {        \
+            err = e_;                   \
+            goto fail;                  \
+        }                               \
+    } while (0)
+
+cudaError_t find_graph_leaf(cudaGraph_t g, cudaGraphNode_t *leaf);
+
+// graph: [CG init] -> WHILE(flag) { CG iteration } -> [x += p o z]
+cudaError_t build_cg_graph(gsr_handle_t *h)
+{
+    cudaError_t err = cudaSuccess;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle loop;
+    cudaGraphNode_t pre_leaf, wnode;
+    cudaGraphNodeParams cp = {};
+    cudaGraph_t body;
+    cudaStream_t s = h->cap_stream;
+    CG_TRY(cudaGraphCreate(&g, 0));
+    CG_TRY(cudaGraphConditionalHandleCreate(&loop, g, 1u, cudaGraphCondAssignDefault));
+    CG_TRY(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cg_prologue(h, s, loop, 1);
+    CG_TRY(cudaStreamEndCapture(s, &g));
+    CG_TRY(find_graph_leaf(g, &pre_leaf));
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CG_TRY(cudaGraphAddNode(&wnode, g, &pre_leaf, nullptr, 1, &cp));
+    body = cp.conditional.phGraph_out[0];
+    CG_TRY(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cg_iteration(h, s, loop, 1);
+    CG_TRY(cudaStreamEndCapture(s, &body));
+    CG_TRY(cudaStreamBeginCaptureToGraph(s, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    k_axpy_p<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_zc, h->d_xm, h->sys.n);
+    CG_TRY(cudaStreamEndCapture(s, &g));
+    CG_TRY(cudaGraphInstantiate(&h->cg_exec, g, 0));
+    cudaGraphDestroy(g);
+    return cudaSuccess;
+fail:
+    {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(s, &junk);
+            if (junk && junk != g)
+                cudaGraphDestroy(junk);
+        }
+    }
+    if (g)
+        cudaGraphDestroy(g);
+    cudaGetLastError();
+    return err;
+}
+
+// one inner solve: graph, or host-driven launches in eager mode
+cudaError_t run_cg(gsr_handle_t *h, cudaStream_t st, int max_inner)
+{
+    if (!h->cfg.eager)
+        return cudaGraphLaunch(h->cg_exec, st);
+    cudaError_t e = cg_prologue(h, st, 0, 0);
+    for (int it = 0; e == cudaSuccess && it < max_inner; it++) {
+        e = cudaMemcpyAsync(h->h_cg, h->d_cg, sizeof(CgState), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess || h->h_cg->done)
+            break;
+        e = cg_iteration(h, st, 0, 0);
+    }
+    if (e == cudaSuccess) {
+        k_axpy_p<<<h->grid_vec, kThreads, 0, st>>>(h->d_p, h->d_zc, h->d_xm, h->sys.n);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t launch_outer_norms(const gsr_handle_t *h, const double *r, cudaStream_t st)
+{
+    k_outer_norms<<<h->grid_vec, kThreads, 0, st>>>(h->d_p, h->d_c, h->sys.n, r, h->sys.m,
+                                                     h->d_onorm, h->d_partial + kRedU * kPartialsPerKind,
+                                                     h->d_counter + kRedU);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neg(const gsr_handle_t *h, const double *a, double *b, int64_t n, cudaStream_t st)
+{
+    k_neg<<<h->grid_vec, kThreads, 0, st>>>(a, b, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_pos(const gsr_handle_t *h, const double *a, double *out, cudaStream_t st)
+{
+    k_count_pos<<<h->grid_vec, kThreads, 0, st>>>(a, h->sys.n, h->d_partial + kRedU * kPartialsPerKind,
+                                                   h->d_counter + kRedU, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const gsr_handle_t *h, const double *a, float *b, int64_t n, cudaStream_t st)
+{
+    k_to_f32<<<h->nsm * 8, kThreads, 0, st>>>(a, b, n);
+    return cudaGetLastError();
+}
+
+int aprod1_f32_grid(const gsr_handle_t *h)
+{
+    int occ = 0;
+    cudaError_t e = x32_in_smem(h)
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              &occ, k_aprod1_f32<1, true>, kThreads, (size_t)h->sys.I * sizeof(float))
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1_f32<1, false>,
+                                                                        kThreads, 0);
+    if (e != cudaSuccess || occ <= 0)
+        return -1;
+    int64_t g = (int64_t)h->nsm * occ;
+    return (int)(g > kMaxPartials ? kMaxPartials : g);
+}
+
+int aprod2_f32_grid(const gsr_handle_t *h)
+{
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, k_aprod2_f32_stars<8, kA2Overwrite>, kThreads, 0);
+    if (e != cudaSuccess || occ <= 0)
+        return -1;
+    int64_t g = (int64_t)h->nsm * occ;
+    return (int)(g > kMaxPartials ? kMaxPartials : g);
+}
+
+}  // namespace gsr

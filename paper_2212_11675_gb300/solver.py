@@ -11,7 +11,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import Config, Dims, Result, check, lib
+from ._lib import Config, Dims, MixedResult, Result, check, lib
 
 
 def _torch():
@@ -123,6 +123,37 @@ class Solver:
         _check_vec(x, self.n, "x")
         check(lib().gsr_aprod2(self._h, _ptr(y)[0], _ptr(x)[0], _stream(stream)), "gsr_aprod2")
         return x
+
+    def aprod1_f32(self, x, y, stream=None):
+        """y += A32 x with binary32 products (mixed-precision handles); returns y."""
+        _check_vec(x, self.n, "x")
+        _check_vec(y, self.m, "y")
+        check(lib().gsr_aprod1_f32(self._h, _ptr(x)[0], _ptr(y)[0], _stream(stream)),
+              "gsr_aprod1_f32")
+        return y
+
+    def aprod2_f32(self, y, x, stream=None):
+        """x += A32^T y with binary32 products (mixed-precision handles); returns x."""
+        _check_vec(y, self.m, "y")
+        _check_vec(x, self.n, "x")
+        check(lib().gsr_aprod2_f32(self._h, _ptr(y)[0], _ptr(x)[0], _stream(stream)),
+              "gsr_aprod2_f32")
+        return x
+
+    def mixed_solve(self, b, max_outer=10, max_inner=100, inner_tol=1e-4, atol=1e-12, x=None,
+                    stream=None):
+        """Mixed-precision PC least squares (binary32 inner CG, FP64 refinement);
+        returns (x, result dict)."""
+        _check_vec(b, self.m, "b")
+        if x is None:
+            x = np.empty(self.n) if isinstance(b, np.ndarray) else _torch().empty(
+                self.n, dtype=b.dtype, device=b.device)
+        _check_vec(x, self.n, "x")
+        res = MixedResult()
+        check(lib().gsr_mixed_solve(self._h, _ptr(b)[0], int(max_outer), int(max_inner),
+                                    float(inner_tol), float(atol), _ptr(x)[0], ctypes.byref(res),
+                                    _stream(stream)), "gsr_mixed_solve")
+        return x, res.as_dict()
 
     def precondition(self, p, stream=None):
         """p = 1/||A(:,j)|| (1 for an empty column); returns p."""
