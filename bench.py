@@ -157,6 +157,59 @@ def time_kernel(fn, stream, reps, torch):
     return e0.elapsed_time(e1) / reps * 1e-3
 
 
+def time_to_solution(sys_, b, torch, stream, target=1e-9, reps=3):
+    """Time for the FP64 PC-LSQR and for the mixed-precision solve to reach a
+    solution within `target` (relative) of the FP64 least-squares solution,
+    on the same GPU.  Each form is run with a ladder of tolerances; the
+    fastest setting that meets the target is reported."""
+    from paper_2212_11675_gb300 import _lib
+    from paper_2212_11675_gb300.solver import Solver
+
+    def timed(fn):
+        best = None
+        out = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best, out
+
+    res = {"target_rel_err": target}
+    with Solver(sys_, conlim=0.0, precision=_lib.GSR_PREC_MIXED) as s:
+        xr, _, rr = s.lsqr_solve(b, 20000, 1e-15, 1e-15, stream=stream, want_se=False)
+        nref = float(torch.linalg.norm(xr))
+        res["reference"] = {"itn": rr["itn"], "istop": rr["istop"]}
+        best = None
+        for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13, 1e-14):
+            ms, out = timed(lambda: s.lsqr_solve(b, 20000, tol, tol, stream=stream, want_se=False))
+            err = float(torch.linalg.norm(out[0] - xr)) / nref
+            if err <= target:
+                best = {"ms": ms, "itn": out[2]["itn"], "atol": tol, "rel_err": err}
+                break
+        res["fp64"] = best
+        bestm = None
+        for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
+            for itol in (1e-2, 1e-3, 1e-4):
+                ms, out = timed(lambda: s.mixed_solve(b, max_outer=30, max_inner=500,
+                                                      inner_tol=itol, atol=tol, stream=stream))
+                err = float(torch.linalg.norm(out[0] - xr)) / nref
+                if err <= target and (bestm is None or ms < bestm["ms"]):
+                    bestm = {"ms": ms, "outer": out[1]["outer"], "inner": out[1]["inner"],
+                             "atol": tol, "inner_tol": itol, "rel_err": err}
+            if bestm is not None:
+                break
+        res["mixed"] = bestm
+        if best and bestm:
+            res["speedup"] = best["ms"] / bestm["ms"]
+    return res
+
+
 def cpu_baseline(sys_, seed, seconds):
     """The oracle timed on a bounded sample: LSQR iterations of the same system."""
     import oracle
@@ -189,6 +242,8 @@ def main():
                     help="launch the solve's kernels from the host (for ncu, which cannot "
                          "profile kernels inside graphs with conditional nodes)")
     ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision vs FP64 time-to-solution comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -304,7 +359,13 @@ def main():
                                         "fp64_TFLOP/s": tf_a2, "fp64_frac": tf_a2 / FP64_NOMINAL_TFLOPS}},
                  "aprod_GB/s": (bytes_a1 + bytes_a2) / (t_a1 + t_a2) / 1e9})
 
-    launches_per_step = 9 + 4 * (iters // args.steps)
+    mixed = None
+    if not args.no_mixed and rank == 0:
+        mixed = time_to_solution(sys_, b, torch, stream)
+
+    # per solve: 12 prologue launches (preconditioner 5, init 7), 6 per LSQR
+    # iteration (aprod 1, aprod 2 as 3 kernels, 2 vector passes), 1 epilogue
+    launches_per_step = 13 + 6 * (iters // args.steps)
     line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -315,6 +376,8 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches_per_step * args.steps}
+    if mixed is not None:
+        line["mixed_vs_fp64"] = mixed
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sys_, seed, args.cpu_seconds)
     if rank == 0:

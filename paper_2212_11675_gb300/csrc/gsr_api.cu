@@ -339,8 +339,10 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     if (h->grid_rows <= 0)
         return cuda_fail(cudaGetLastError(), "aprod1 occupancy");
     h->grid_att = h->nsm * 8;
+    // vector kernels: two blocks per SM (each thread takes several entries,
+    // so the per-block reduction epilogue stays a small share of the work)
     int64_t gv = (n + kThreads - 1) / kThreads;
-    if (gv > (int64_t)h->nsm * 8) gv = (int64_t)h->nsm * 8;
+    if (gv > (int64_t)h->nsm * 2) gv = (int64_t)h->nsm * 2;
     if (gv > kMaxPartials) gv = kMaxPartials;
     h->grid_vec = (int)(gv < 1 ? 1 : gv);
     if (!instr_in_smem(h) || h->cfg.precision == GSR_PREC_MIXED) {

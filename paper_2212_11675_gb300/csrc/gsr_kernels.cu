@@ -332,10 +332,9 @@ k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
 
 // Pass 2, fused with the instrumental replicas.  Blocks [0, nb_att) combine
 // the attitude columns: column a*D + k receives sum_{j=0..3} S[k-j][4a+j]
-// (0 <= k-j < nseg).  The remaining blocks (when rep != null) each take 32
-// instrument columns: 8 threads per column sum every 8th replica, the 8
-// partials are added in a fixed order, and the replicas are cleared for the
-// next call.
+// (0 <= k-j < nseg).  The remaining blocks (when rep != null) take 8
+// instrument columns each, one warp per column, summing the replicas in a
+// fixed order and clearing them for the next call.
 template <bool ACC>
 __global__ void __launch_bounds__(kThreads)
 k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out,
@@ -361,25 +360,20 @@ k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out,
         }
         return;
     }
-    __shared__ double part[8][32];
-    const int64_t f = (int64_t)(blockIdx.x - nb_att) * 32 + (threadIdx.x & 31);
-    const int q = threadIdx.x >> 5;  // 0..7
-    double t = 0.0;
+    // replicas: warp w of the block sums instrument f = 8 b + w over the
+    // replicas (lane l takes replicas l, l+32, ...), clearing them
+    const int lane = threadIdx.x & 31;
+    const int64_t f = (int64_t)(blockIdx.x - nb_att) * (kThreads / 32) + (threadIdx.x >> 5);
     if (f < A.I) {
-        for (int r = q; r < nrep; r += 8) {
+        double t = 0.0;
+        for (int r = lane; r < nrep; r += 32) {
             double *p = rep + (int64_t)r * A.I + f;
             t += *p;
             *p = 0.0;
         }
-    }
-    part[q][threadIdx.x & 31] = t;
-    __syncthreads();
-    if (q == 0 && f < A.I) {
-        double u = part[0][threadIdx.x];
-#pragma unroll
-        for (int k = 1; k < 8; k++)
-            u += part[k][threadIdx.x];
-        out[A.ins0 + f] += u;
+        t = warp_sum(t);
+        if (lane == 0)
+            out[A.ins0 + f] += t;
     }
 }
 
@@ -472,7 +466,7 @@ cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out, i
     const int nb_att = (int)((3 * h->sys.D + kThreads - 1) / kThreads < 4 * h->nsm
                                  ? (3 * h->sys.D + kThreads - 1) / kThreads
                                  : 4 * h->nsm);
-    const int nb_ins = instr_in_smem(h) ? 0 : (int)((h->sys.I + 31) / 32);
+    const int nb_ins = instr_in_smem(h) ? 0 : (int)((h->sys.I + kThreads / 32 - 1) / (kThreads / 32));
     return launch_att_combine(h, out, nb_att, nb_ins, mode == kA2Accumulate, st);
 }
 

@@ -91,36 +91,53 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
     const int64_t mp = A.mp;
     const float xg = __ldg(x32 + A.glb0);
     double nrm = 0.0;
-    for (int64_t t = warp; t < ntiles; t += nwarps) {
-        const int64_t r = (t << 5) + lane;
-        if (r < A.m) {
-            uint32_t s = A.tile_star[t];
-            while ((int64_t)A.star_ptr[s + 1] <= r)
-                ++s;
-            const uint4 rc = __ldcs(A.rec + r);
-            const float *v = A.val32 + r;
-            float vk[kNPar];
+    // two tiles per step: all loads of both rows are issued before the sums
+    for (int64_t t0 = warp; t0 < ntiles; t0 += 2 * nwarps) {
+        float vk[2][kNPar];
+        uint4 rc[2];
+        uint32_t st[2];
+        bool ok[2];
 #pragma unroll
-            for (int k = 0; k < kNPar; k++)
-                vk[k] = __ldcs(v + k * mp);
+        for (int u = 0; u < 2; u++) {
+            const int64_t t = t0 + u * nwarps;
+            const int64_t r = (t << 5) + lane;
+            ok[u] = (t < ntiles) && (r < A.m);
+            st[u] = 0;
+            if (ok[u]) {
+                uint32_t s = A.tile_star[t];
+                while ((int64_t)A.star_ptr[s + 1] <= r)
+                    ++s;
+                st[u] = s;
+                rc[u] = __ldcs(A.rec + r);
+                const float *v = A.val32 + r;
+#pragma unroll
+                for (int k = 0; k < kNPar; k++)
+                    vk[u][k] = __ldcs(v + k * mp);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            if (!ok[u])
+                continue;
+            const int64_t r = ((t0 + u * nwarps) << 5) + lane;
             float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;  // two independent pairs
-            const float *xs = x32 + (int64_t)kNAstro * s;
+            const float *xs = x32 + (int64_t)kNAstro * st[u];
 #pragma unroll
             for (int k = 0; k < kNAstro; k++)
-                df_acc(h0, l0, __fmul_rn(vk[k], __ldg(xs + k)));
-            const float *xa = x32 + A.att0 + rc.x;
+                df_acc(h0, l0, __fmul_rn(vk[u][k], __ldg(xs + k)));
+            const float *xa = x32 + A.att0 + rc[u].x;
 #pragma unroll
             for (int a = 0; a < 3; a++)
 #pragma unroll
                 for (int j = 0; j < 4; j++)
-                    df_acc(h1, l1, __fmul_rn(vk[5 + 4 * a + j], __ldg(xa + a * A.D + j)));
+                    df_acc(h1, l1, __fmul_rn(vk[u][5 + 4 * a + j], __ldg(xa + a * A.D + j)));
 #pragma unroll
             for (int j = 0; j < kNInstr; j++) {
-                const uint32_t f = instr_at32(rc, j);
-                df_acc(h0, l0, __fmul_rn(vk[17 + j], SMEMX ? s_x32[f] : __ldg(x32 + A.ins0 + f)));
+                const uint32_t f = instr_at32(rc[u], j);
+                df_acc(h0, l0,
+                       __fmul_rn(vk[u][17 + j], SMEMX ? s_x32[f] : __ldg(x32 + A.ins0 + f)));
             }
-            df_acc(h1, l1, __fmul_rn(vk[23], xg));
-            // combine the two pairs
+            df_acc(h1, l1, __fmul_rn(vk[u][23], xg));
             df_acc(h0, l0, h1);
             l0 = __fadd_rn(l0, l1);
             if (MODE == 0) {
@@ -149,12 +166,18 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
 // part written, instrumental/global accumulated into zeroed memory.
 // Instrumental products go to per-SM replicas (FP64 reductions in L2).
 // ---------------------------------------------------------------------------
-template <int G, int MODE>
+template <int G, int MODE, bool SMEM_INSTR>
 __global__ void __launch_bounds__(kThreads)
 k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict__ out,
                    double *__restrict__ rep, int nrep)
 {
+    extern __shared__ double s_ins[];
     __shared__ double s_red[kThreads / 32];
+    if (SMEM_INSTR) {
+        for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x)
+            s_ins[f] = 0.0;
+        __syncthreads();
+    }
     constexpr int GPW = 32 / G;
     const int lane = threadIdx.x & (G - 1);
     const int gw = (threadIdx.x & 31) / G;
@@ -185,7 +208,10 @@ k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict_
 #pragma unroll
             for (int j = 0; j < kNInstr; j++) {
                 const float pr = __fmul_rn(__ldcs(v + (17 + j) * mp), yi);
-                atomicAdd(myrep + instr_at32(rc, j), f2d(pr));
+                if (SMEM_INSTR)
+                    atomicAdd(&s_ins[instr_at32(rc, j)], f2d(pr));
+                else
+                    atomicAdd(myrep + instr_at32(rc, j), f2d(pr));
             }
             df_acc(gh, gl, __fmul_rn(__ldcs(v + 23 * mp), yi));
         }
@@ -218,6 +244,13 @@ k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict_
             t += s_red[w];
         atomicAdd(out + A.glb0, t);
     }
+    if (SMEM_INSTR) {
+        for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x) {
+            const double t = s_ins[f];
+            if (t != 0.0)
+                atomicAdd(out + A.ins0 + f, t);
+        }
+    }
 }
 
 // inner aprod 2, attitude part over the offset-sorted binary32 copy
@@ -234,7 +267,23 @@ k_att_segments_f32(SysView A, const float *__restrict__ y32, double *__restrict_
 #pragma unroll
         for (int k = 0; k < kNAtt; k++)
             h[k] = l[k] = 0.f;
-        for (uint32_t e = e0 + lane; e < e1; e += 32) {
+        uint32_t e = e0 + lane;
+        for (; e + 32 < e1; e += 64) {  // two entries per lane in flight
+            const uint32_t ra = __ldcs(A.perm + e), rb = __ldcs(A.perm + e + 32);
+            float va[kNAtt], vb[kNAtt];
+#pragma unroll
+            for (int k = 0; k < kNAtt; k++) {
+                va[k] = __ldcs(A.tval32 + k * mp + e);
+                vb[k] = __ldcs(A.tval32 + k * mp + e + 32);
+            }
+            const float ya = __ldg(y32 + ra), yb = __ldg(y32 + rb);
+#pragma unroll
+            for (int k = 0; k < kNAtt; k++) {
+                df_acc(h[k], l[k], __fmul_rn(va[k], ya));
+                df_acc(h[k], l[k], __fmul_rn(vb[k], yb));
+            }
+        }
+        if (e < e1) {
             const float yi = __ldg(y32 + __ldcs(A.perm + e));
 #pragma unroll
             for (int k = 0; k < kNAtt; k++)
@@ -424,13 +473,19 @@ template <int MODE>
 static cudaError_t a2f_launch(const gsr_handle_t *h, const float *y32, double *out, cudaStream_t st)
 {
     const int G = 8;
-    k_aprod2_f32_stars<G, MODE><<<h->grid_rows2_32, kThreads, 0, st>>>(h->sys, y32, out, h->d_irep,
-                                                                        h->nrep);
+    const bool smem = instr_in_smem(h);
+    if (smem)
+        k_aprod2_f32_stars<G, MODE, true><<<h->grid_rows2_32, kThreads,
+                                             (size_t)h->sys.I * sizeof(double), st>>>(
+            h->sys, y32, out, h->d_irep, h->nrep);
+    else
+        k_aprod2_f32_stars<G, MODE, false><<<h->grid_rows2_32, kThreads, 0, st>>>(
+            h->sys, y32, out, h->d_irep, h->nrep);
     k_att_segments_f32<<<h->grid_att, kThreads, 0, st>>>(h->sys, y32, h->d_attS);
     const int nb_att = (int)((3 * h->sys.D + kThreads - 1) / kThreads < 4 * h->nsm
                                  ? (3 * h->sys.D + kThreads - 1) / kThreads
                                  : 4 * h->nsm);
-    const int nb_ins = (int)((h->sys.I + 31) / 32);
+    const int nb_ins = smem ? 0 : (int)((h->sys.I + kThreads / 32 - 1) / (kThreads / 32));
     launch_att_combine(h, out, nb_att, nb_ins, MODE == kA2Accumulate, st);
     return cudaGetLastError();
 }
@@ -599,8 +654,12 @@ int aprod1_f32_grid(const gsr_handle_t *h)
 int aprod2_f32_grid(const gsr_handle_t *h)
 {
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, k_aprod2_f32_stars<8, kA2Overwrite>, kThreads, 0);
+    cudaError_t e = instr_in_smem(h)
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              &occ, k_aprod2_f32_stars<8, kA2Overwrite, true>, kThreads,
+                              (size_t)h->sys.I * sizeof(double))
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              &occ, k_aprod2_f32_stars<8, kA2Overwrite, false>, kThreads, 0);
     if (e != cudaSuccess || occ <= 0)
         return -1;
     int64_t g = (int64_t)h->nsm * occ;

@@ -23,24 +23,37 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // Sum over the block; the result is valid in every thread.  Deterministic.
+// Warps reduce their lanes; only warp 0 then adds the per-warp partials (FP64
+// adds are expensive on this part, so no other thread repeats them).
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K])
 {
-    __shared__ double sh[K][kThreads / 32];
+    constexpr int NW = kThreads / 32;
+    __shared__ double sh[K][NW];
+    __shared__ double res[K];
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < K; k++) {
         const double w = warp_sum(v[k]);
-        if ((threadIdx.x & 31) == 0)
+        if (lane == 0)
             sh[k][threadIdx.x >> 5] = w;
     }
     __syncthreads();
+    if (threadIdx.x < 32) {
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        double t = 0.0;
-        for (int w = 0; w < kThreads / 32; w++)
-            t += sh[k][w];
-        v[k] = t;
+        for (int k = 0; k < K; k++) {
+            double t = (lane < NW) ? sh[k][lane] : 0.0;
+#pragma unroll
+            for (int off = NW / 2; off > 0; off >>= 1)
+                t += __shfl_xor_sync(0xffffffffu, t, off);
+            if (lane == 0)
+                res[k] = t;
+        }
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        v[k] = res[k];
     __syncthreads();
 }
 
