@@ -224,6 +224,43 @@ int gsr_mixed_solve(void *h, const double *b, int max_outer, int max_inner,
                     double inner_tol, double atol, double *x,
                     gsr_mixed_result *out, void *stream);
 
+/*
+ * Replace nonzero k (0..23, in the order of the column map above) of every
+ * row with values[m] (host or device).  k = 23 is the global (PPN gamma)
+ * column.  The derived copies (offset-sorted attitude values, binary32
+ * copy) follow.  Solves started afterwards use the new values.
+ */
+int gsr_set_values(void *h, int k, const double *values, void *stream);
+
+typedef struct {
+    int iterations;    /* conjugate-gradient iterations done */
+    int converged;     /* 1 when rel_resid <= tol */
+    double rel_resid;  /* ||diag(p)(g - A^T A q)|| / ||diag(p) g|| (recurrence) */
+} gsr_cg_result;
+
+/*
+ * Normal equations (A^T A) q = g[n] in FP64 by conjugate gradients on the
+ * column-scaled system (diag(p) A^T A diag(p)) z = diag(p) g, q = p o z,
+ * until rel_resid <= tol or max_iter iterations.  q[n] is the output.  With
+ * x the least-squares solution, q is the adjoint of the map b -> x:
+ * for a loss L(x) with g = dL/dx, dL/db = A q.  Errors: GSR_ERR_ARG,
+ * GSR_ERR_NONFINITE, GSR_ERR_CUDA.
+ */
+int gsr_normal_solve(void *h, const double *g, int max_iter, double tol,
+                     double *q, gsr_cg_result *out, void *stream);
+
+/*
+ * Backward pass of the least-squares solve x = argmin ||A x - b|| (full
+ * column rank): given b[m], the solution x[n] and gx[n] = dL/dx, computes
+ * q = (A^T A)^{-1} gx (gsr_normal_solve), grad_b[m] = dL/db = A q and, when
+ * grad_glob is not NULL, grad_glob[m] = dL/dA(i, G) = r_i q_G - s_i x_G for
+ * the global column G, with r = b - A x and s = A q (the derivative of the
+ * normal equations A^T A x = A^T b with respect to the values of column G).
+ */
+int gsr_lsq_backward(void *h, const double *b, const double *x, const double *gx,
+                     int max_iter, double tol, double *grad_b, double *grad_glob,
+                     gsr_cg_result *out, void *stream);
+
 /* Text of the last CUDA failure seen by this host thread ("" if none). */
 const char *gsr_last_error(void);
 

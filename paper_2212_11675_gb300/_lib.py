@@ -29,6 +29,7 @@ EXPORTS = (
     "gsr_config_default", "gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
     "gsr_precondition", "gsr_lsqr_solve", "gsr_last_error", "gsr_info", "gsr_strerror",
     "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32", "gsr_mixed_solve",
+    "gsr_set_values", "gsr_normal_solve", "gsr_lsq_backward",
 )
 
 
@@ -58,6 +59,14 @@ class MixedResult(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int), ("outer", ctypes.c_int), ("inner", ctypes.c_int),
                 ("rnorm", ctypes.c_double), ("arnorm", ctypes.c_double),
                 ("anorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CgResult(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_resid", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -105,6 +114,9 @@ def lib():
             L.gsr_aprod1_f32.argtypes = [P, P, P, P]
             L.gsr_aprod2_f32.argtypes = [P, P, P, P]
             L.gsr_mixed_solve.argtypes = [P, P, I, I, D, D, P, ctypes.POINTER(MixedResult), P]
+            L.gsr_set_values.argtypes = [P, I, P, P]
+            L.gsr_normal_solve.argtypes = [P, P, I, D, P, ctypes.POINTER(CgResult), P]
+            L.gsr_lsq_backward.argtypes = [P, P, P, P, I, D, P, P, ctypes.POINTER(CgResult), P]
             L.gsr_last_error.restype = ctypes.c_char_p
             L.gsr_strerror.argtypes = [I]
             L.gsr_strerror.restype = ctypes.c_char_p
@@ -112,7 +124,8 @@ def lib():
             for name in ("gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
                          "gsr_precondition", "gsr_lsqr_solve", "gsr_info",
                          "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32",
-                         "gsr_mixed_solve"):
+                         "gsr_mixed_solve", "gsr_set_values", "gsr_normal_solve",
+                         "gsr_lsq_backward"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib

@@ -111,6 +111,8 @@ static void release(gsr_handle_t *h)
         cudaGraphExecDestroy(h->solve_exec);
     if (h->cg_exec)
         cudaGraphExecDestroy(h->cg_exec);
+    if (h->cg64_exec)
+        cudaGraphExecDestroy(h->cg64_exec);
     if (h->h_cg)
         cudaFreeHost(h->h_cg);
     if (h->h_cgargs)
@@ -124,7 +126,8 @@ static void release(gsr_handle_t *h)
                    h->d_var, h->d_q, h->d_vp, h->d_vt, h->d_bstage, h->d_xstage, h->d_sestage,
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err,
                    h->d_val32, h->d_tval32, h->d_x32, h->d_q32, h->d_c, h->d_s, h->d_d, h->d_t,
-                   h->d_zc, h->d_xm, h->d_r, h->d_xneg, h->d_onorm, h->d_cg, h->d_cgargs};
+                   h->d_zc, h->d_xm, h->d_r, h->d_xneg, h->d_onorm, h->d_cg, h->d_cgargs,
+                   h->d_xp64, h->d_q64};
     for (void *p : dev)
         if (p)
             cudaFree(p);
@@ -148,20 +151,6 @@ static int create_mixed(gsr_handle_t *h, cudaStream_t st)
     TRY(dalloc(h, &h->d_tval32, (int64_t)kNAtt * mp));
     TRY(dalloc(h, &h->d_x32, n));
     TRY(dalloc(h, &h->d_q32, m));
-    TRY(dalloc(h, &h->d_c, n));
-    TRY(dalloc(h, &h->d_s, n));
-    TRY(dalloc(h, &h->d_d, n));
-    TRY(dalloc(h, &h->d_t, n));
-    TRY(dalloc(h, &h->d_zc, n));
-    TRY(dalloc(h, &h->d_xm, n));
-    TRY(dalloc(h, &h->d_r, m));
-    TRY(dalloc(h, &h->d_xneg, n));
-    TRY(dalloc(h, &h->d_onorm, 4));
-    TRY(dalloc(h, &h->d_cg, 1));
-    TRY(dalloc(h, &h->d_cgargs, 1));
-    CK(cudaMallocHost((void **)&h->h_cg, sizeof(CgState)));
-    CK(cudaMallocHost((void **)&h->h_cgargs, sizeof(CgArgs)));
-    CK(cudaMallocHost((void **)&h->h_onorm, 4 * sizeof(double)));
     CK(launch_to_f32(h, h->d_val, h->d_val32, kNPar * mp, st));
     CK(launch_to_f32(h, h->d_tval, h->d_tval32, kNAtt * mp, st));
     A.val32 = h->d_val32;
@@ -357,6 +346,27 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     cudaError_t e = build_solve_graph(h);
     if (e != cudaSuccess)
         return cuda_fail(e, "build_solve_graph");
+    // conjugate-gradient workspace (normal-equation solves of the adjoint and
+    // of the mixed-precision refinement)
+    TRY(dalloc(h, &h->d_c, n));
+    TRY(dalloc(h, &h->d_s, n));
+    TRY(dalloc(h, &h->d_d, n));
+    TRY(dalloc(h, &h->d_t, n));
+    TRY(dalloc(h, &h->d_zc, n));
+    TRY(dalloc(h, &h->d_xm, n));
+    TRY(dalloc(h, &h->d_xp64, n));
+    TRY(dalloc(h, &h->d_xneg, n));
+    TRY(dalloc(h, &h->d_r, m));
+    TRY(dalloc(h, &h->d_q64, m));
+    TRY(dalloc(h, &h->d_onorm, 4));
+    TRY(dalloc(h, &h->d_cg, 1));
+    TRY(dalloc(h, &h->d_cgargs, 1));
+    CK(cudaMallocHost((void **)&h->h_cg, sizeof(CgState)));
+    CK(cudaMallocHost((void **)&h->h_cgargs, sizeof(CgArgs)));
+    CK(cudaMallocHost((void **)&h->h_onorm, 4 * sizeof(double)));
+    e = build_cg64_graph(h);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "build_cg64_graph");
     if (h->cfg.precision == GSR_PREC_MIXED)
         return create_mixed(h, st);
     return GSR_OK;
@@ -636,5 +646,103 @@ extern "C" int gsr_mixed_solve(void *hv, const double *b, int max_outer, int max
     CK(cudaStreamSynchronize(st));
     if (out)
         *out = res;
+    return GSR_OK;
+}
+
+extern "C" int gsr_set_values(void *hv, int k, const double *values, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !values || k < 0 || k >= kNPar)
+        return GSR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *dv;
+    TRY(stage(h, &h->d_ystage, h->sys.m, values, &dv, true, st));
+    CK(launch_set_plane(h, k, dv, st));
+    if (h->cfg.precision == GSR_PREC_MIXED)
+        CK(launch_f32_plane(h, k, st));
+    if (dv != values)
+        CK(cudaStreamSynchronize(st));
+    return GSR_OK;
+}
+
+// (diag(p) A^T A diag(p)) z = diag(p) g by FP64 CG, q = p o z, into h->d_xm
+static int normal_solve_dev(gsr_handle_t *h, const double *dg, int max_iter, double tol,
+                            gsr_cg_result *res, cudaStream_t st)
+{
+    const SysView &A = h->sys;
+    CK(enqueue_precondition(h, h->d_p, st));
+    CK(cudaMemcpyAsync(h->d_c, dg, A.n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(h->d_xm, 0, A.n * sizeof(double), st));
+    h->h_cgargs->max_inner = max_iter;
+    h->h_cgargs->tol = tol;
+    CK(cudaMemcpyAsync(h->d_cgargs, h->h_cgargs, sizeof(CgArgs), cudaMemcpyHostToDevice, st));
+    CK(run_cg64(h, st, max_iter));
+    CK(cudaMemcpyAsync(h->h_cg, h->d_cg, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const CgState &g = *h->h_cg;
+    if (res) {
+        res->iterations = g.it;
+        res->converged = (g.gamma <= g.stop2) ? 1 : 0;
+        res->rel_resid = (g.gamma0 > 0.0) ? sqrt(g.gamma / g.gamma0) : 0.0;
+    }
+    if (g.nonfinite)
+        return GSR_ERR_NONFINITE;
+    return GSR_OK;
+}
+
+extern "C" int gsr_normal_solve(void *hv, const double *g, int max_iter, double tol, double *q,
+                                gsr_cg_result *out, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !g || !q || max_iter < 1 || !(tol >= 0.0))
+        return GSR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *dg;
+    TRY(stage(h, &h->d_xstage, h->sys.n, g, &dg, true, st));
+    TRY(normal_solve_dev(h, dg, max_iter, tol, out, st));
+    CK(cudaMemcpyAsync(q, h->d_xm, h->sys.n * sizeof(double), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    return GSR_OK;
+}
+
+extern "C" int gsr_lsq_backward(void *hv, const double *b, const double *x, const double *gx,
+                                int max_iter, double tol, double *grad_b, double *grad_glob,
+                                gsr_cg_result *out, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !b || !x || !gx || !grad_b || max_iter < 1 || !(tol >= 0.0))
+        return GSR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const SysView &A = h->sys;
+    double *dgx, *dgb, *db, *dx;
+    TRY(stage(h, &h->d_xstage, A.n, gx, &dgx, true, st));
+    TRY(normal_solve_dev(h, dgx, max_iter, tol, out, st));  // q in d_xm
+    // s = A q = dL/db
+    TRY(stage(h, &h->d_ystage, A.m, grad_b, &dgb, false, st));
+    CK(cudaMemsetAsync(dgb, 0, A.m * sizeof(double), st));
+    CK(launch_aprod1(h, h->d_xm, dgb, 0, st));
+    if (grad_glob) {
+        // r = b - A x, then grad_glob = r q_G - s x_G
+        TRY(stage(h, &h->d_bstage, A.m, b, &db, true, st));
+        if (on_device(x)) {
+            dx = (double *)x;
+        } else {
+            CK(cudaMemcpyAsync(h->d_xneg, x, A.n * sizeof(double), cudaMemcpyHostToDevice, st));
+            dx = h->d_xneg;
+        }
+        CK(cudaMemcpyAsync(h->d_r, db, A.m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(launch_neg(h, dx, h->d_t, A.n, st));
+        CK(launch_aprod1(h, h->d_t, h->d_r, 0, st));
+        double *dgg = grad_glob;
+        const bool gg_dev = on_device(grad_glob);
+        if (!gg_dev)
+            dgg = h->d_q64;  // m doubles of scratch
+        CK(launch_grad_global(h, h->d_r, dgb, h->d_xm, dx, dgg, st));
+        if (!gg_dev)
+            CK(cudaMemcpyAsync(grad_glob, dgg, A.m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    if (dgb != grad_b)
+        CK(cudaMemcpyAsync(grad_b, dgb, A.m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     return GSR_OK;
 }

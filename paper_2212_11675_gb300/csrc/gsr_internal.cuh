@@ -118,6 +118,8 @@ struct gsr_handle_t {
     gsr::CgArgs *d_cgargs = nullptr, *h_cgargs = nullptr;
     double *h_onorm = nullptr;
     cudaGraphExec_t cg_exec = nullptr;
+    cudaGraphExec_t cg64_exec = nullptr;   // FP64 normal-equation CG
+    double *d_xp64 = nullptr, *d_q64 = nullptr;
     int grid_rows32 = 0, grid_rows2_32 = 0;
     double n_nonempty = 0.0;
     double *d_p = nullptr;              // preconditioner
@@ -144,6 +146,13 @@ namespace gsr {
 // launchers (gsr_kernels.cu)
 cudaError_t launch_aprod1(const gsr_handle_t *h, const double *x, double *y,
                           int lsqr_mode, cudaStream_t st);
+cudaError_t launch_aprod1_cg(const gsr_handle_t *h, const double *x, double *y, cudaStream_t st);
+cudaError_t launch_set_plane(const gsr_handle_t *h, int k, const double *v, cudaStream_t st);
+cudaError_t launch_grad_global(const gsr_handle_t *h, const double *r, const double *s,
+                               const double *q, const double *x, double *grad, cudaStream_t st);
+cudaError_t build_cg64_graph(gsr_handle_t *h);
+cudaError_t run_cg64(gsr_handle_t *h, cudaStream_t st, int max_iter);
+cudaError_t launch_f32_plane(const gsr_handle_t *h, int k, cudaStream_t st);
 cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out,
                           int mode, cudaStream_t st);
 cudaError_t launch_validate(const gsr_handle_t *h, cudaStream_t st);

@@ -43,12 +43,14 @@ __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
 // ---------------------------------------------------------------------------
 // aprod 1, row-parallel.  MODE 0: y += A x.  MODE 1 (LSQR): y = A x + cy y
 // with cy from the solve state and ||y||^2 reduced into state->beta_new.
-// SMEMX: the instrumental part of x is staged in shared memory.
+// MODE 2 (conjugate gradients): y = A x, ||y||^2 into cg->xi and the step
+// cg->alpha = cg->gamma / ||y||^2.  SMEMX: the instrumental part of x is
+// staged in shared memory.
 // ---------------------------------------------------------------------------
 template <int MODE, bool SMEMX>
 __global__ void __launch_bounds__(kThreads)
 k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveState *st,
-         double *partial, unsigned *counter)
+         double *partial, unsigned *counter, CgState *cg)
 {
     extern __shared__ double s_xi[];
     if (SMEMX) {
@@ -107,10 +109,20 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
             if (MODE == 1) {
                 yn = fma(cy, y[r], sum);
                 nrm = fma(yn, yn, nrm);
+            } else if (MODE == 2) {
+                yn = sum;
+                nrm = fma(yn, yn, nrm);
             } else {
                 yn = y[r] + sum;
             }
             y[r] = yn;
+        }
+    }
+    if (MODE == 2) {
+        double v1[1] = {nrm};
+        if (grid_reduce<1>(v1, partial, counter) && threadIdx.x == 0) {
+            cg->xi = v1[0];
+            cg->alpha = (v1[0] > 0.0) ? cg->gamma / v1[0] : 0.0;
         }
     }
     if (MODE == 1) {
@@ -383,17 +395,23 @@ k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out,
 template <int MODE>
 static cudaError_t a1_launch(const gsr_handle_t *h, const double *x, double *y,
                              SolveState *st_slot, double *partial, unsigned *counter,
-                             cudaStream_t st)
+                             cudaStream_t st, CgState *cg = nullptr)
 {
     const bool smem = h->sys.I <= kSmemInstrMax;
     const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
     if (smem)
         k_aprod1<MODE, true><<<h->grid_rows, kThreads, shm, st>>>(h->sys, x, y, st_slot, partial,
-                                                                   counter);
+                                                                   counter, cg);
     else
         k_aprod1<MODE, false><<<h->grid_rows, kThreads, 0, st>>>(h->sys, x, y, st_slot, partial,
-                                                                  counter);
+                                                                  counter, cg);
     return cudaGetLastError();
+}
+
+cudaError_t launch_aprod1_cg(const gsr_handle_t *h, const double *x, double *y, cudaStream_t st)
+{
+    return a1_launch<2>(h, x, y, nullptr, h->d_partial + kRedU * kPartialsPerKind,
+                        h->d_counter + kRedU, st, h->d_cg);
 }
 
 cudaError_t launch_aprod1(const gsr_handle_t *h, const double *x, double *y, int lsqr_mode,
@@ -577,6 +595,48 @@ __global__ void k_gather_att(SysView A, double *__restrict__ tval)
 cudaError_t launch_gather_att(const gsr_handle_t *h, cudaStream_t st)
 {
     k_gather_att<<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_tval);
+    return cudaGetLastError();
+}
+
+// plane k of A <- v (and the dependent copies: offset-sorted attitude plane)
+__global__ void k_set_plane(SysView A, int k, const double *__restrict__ v, double *__restrict__ val)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        val[k * A.mp + i] = v[i];
+}
+
+__global__ void k_regather_att_plane(SysView A, int k, double *__restrict__ tval)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A.m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        tval[(k - kNAstro) * A.mp + e] = A.val[k * A.mp + A.perm[e]];
+}
+
+cudaError_t launch_set_plane(const gsr_handle_t *h, int k, const double *v, cudaStream_t st)
+{
+    k_set_plane<<<h->nsm * 8, kThreads, 0, st>>>(h->sys, k, v, h->d_val);
+    if (k >= kNAstro && k < kNAstro + kNAtt)
+        k_regather_att_plane<<<h->nsm * 8, kThreads, 0, st>>>(h->sys, k, h->d_tval);
+    return cudaGetLastError();
+}
+
+// grad[i] = r_i q_G - s_i x_G (derivative of the loss with respect to the
+// global-column value of row i, for the least-squares solution x)
+__global__ void k_grad_global(const double *__restrict__ r, const double *__restrict__ s,
+                              const double *__restrict__ q, const double *__restrict__ x, int64_t glb0,
+                              int64_t m, double *__restrict__ grad)
+{
+    const double qg = q[glb0], xg = x[glb0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        grad[i] = fma(r[i], qg, -s[i] * xg);
+}
+
+cudaError_t launch_grad_global(const gsr_handle_t *h, const double *r, const double *s,
+                               const double *q, const double *x, double *grad, cudaStream_t st)
+{
+    k_grad_global<<<h->nsm * 8, kThreads, 0, st>>>(r, s, q, x, h->sys.glb0, h->sys.m, grad);
     return cudaGetLastError();
 }
 

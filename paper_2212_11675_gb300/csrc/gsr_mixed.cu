@@ -324,9 +324,10 @@ __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, in
 
 // s = p o c, d = s, z = 0, xp32 = fl32(p o d), gamma = |s|^2; clears the
 // instrumental/global part of t for the first inner aprod 2
+template <typename XT>
 __global__ void __launch_bounds__(kThreads)
 k_cg_init(const double *__restrict__ p, const double *__restrict__ c, double *__restrict__ s,
-          double *__restrict__ d, double *__restrict__ z, float *__restrict__ xp32,
+          double *__restrict__ d, double *__restrict__ z, XT *__restrict__ xp32,
           double *__restrict__ t, int64_t n, int64_t ins0, CgState *cg, const CgArgs *args,
           double *partial, unsigned *counter, cudaGraphConditionalHandle loop, int in_graph)
 {
@@ -336,7 +337,7 @@ k_cg_init(const double *__restrict__ p, const double *__restrict__ c, double *__
         s[j] = sj;
         d[j] = sj;
         z[j] = 0.0;
-        xp32[j] = __double2float_rn(p[j] * sj);
+        xp32[j] = (XT)(p[j] * sj);
         if (j >= ins0)
             t[j] = 0.0;
         acc[0] = fma(sj, sj, acc[0]);
@@ -390,15 +391,16 @@ k_cg_vec1(const double *__restrict__ p, const double *__restrict__ t, double *__
 }
 
 // d = s + beta d, xp32 = fl32(p o d); clears the instrumental/global part of t
+template <typename XT>
 __global__ void k_cg_vec2(const double *__restrict__ p, const double *__restrict__ s,
-                          double *__restrict__ d, float *__restrict__ xp32, double *__restrict__ t,
+                          double *__restrict__ d, XT *__restrict__ xp32, double *__restrict__ t,
                           int64_t n, int64_t ins0, const CgState *cg)
 {
     const double beta = cg->beta;
     for (int64_t j = gtid32(); j < n; j += gstride32()) {
         const double dj = fma(beta, d[j], s[j]);
         d[j] = dj;
-        xp32[j] = __double2float_rn(p[j] * dj);
+        xp32[j] = (XT)(p[j] * dj);
         if (j >= ins0)
             t[j] = 0.0;
     }
@@ -507,7 +509,7 @@ static cudaError_t cg_prologue(const gsr_handle_t *h, cudaStream_t s, cudaGraphC
                                int in_graph)
 {
     const SysView &A = h->sys;
-    k_cg_init<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_c, h->d_s, h->d_d, h->d_zc, h->d_x32,
+    k_cg_init<float><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_c, h->d_s, h->d_d, h->d_zc, h->d_x32,
                                                 h->d_t, A.n, A.ins0, h->d_cg, h->d_cgargs,
                                                 h->d_partial + kRedBnorm * kPartialsPerKind,
                                                 h->d_counter + kRedBnorm, loop, in_graph);
@@ -526,7 +528,7 @@ static cudaError_t cg_iteration(const gsr_handle_t *h, cudaStream_t s, cudaGraph
     k_cg_vec1<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc, A.n, h->d_cg,
                                                 h->d_cgargs, h->d_partial + kRedV * kPartialsPerKind,
                                                 h->d_counter + kRedV, loop, in_graph);
-    k_cg_vec2<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_s, h->d_d, h->d_x32, h->d_t, A.n, A.ins0,
+    k_cg_vec2<float><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_s, h->d_d, h->d_x32, h->d_t, A.n, A.ins0,
                                                 h->d_cg);
     return cudaGetLastError();
 }
@@ -664,6 +666,118 @@ int aprod2_f32_grid(const gsr_handle_t *h)
         return -1;
     int64_t g = (int64_t)h->nsm * occ;
     return (int)(g > kMaxPartials ? kMaxPartials : g);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 conjugate gradients on the preconditioned normal equations
+// (diag(p) A^T A diag(p)) z = diag(p) c, q = p o z: the same recurrences as
+// the inner solve above with the FP64 products of gsr_kernels.cu (used for
+// the adjoint of the least-squares solution)
+// ---------------------------------------------------------------------------
+static cudaError_t cg64_prologue(const gsr_handle_t *h, cudaStream_t s,
+                                 cudaGraphConditionalHandle loop, int in_graph)
+{
+    const SysView &A = h->sys;
+    k_cg_init<double><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_c, h->d_s, h->d_d, h->d_zc,
+                                                        h->d_xp64, h->d_t, A.n, A.ins0, h->d_cg,
+                                                        h->d_cgargs,
+                                                        h->d_partial + kRedBnorm * kPartialsPerKind,
+                                                        h->d_counter + kRedBnorm, loop, in_graph);
+    return cudaGetLastError();
+}
+
+static cudaError_t cg64_iteration(const gsr_handle_t *h, cudaStream_t s,
+                                  cudaGraphConditionalHandle loop, int in_graph)
+{
+    const SysView &A = h->sys;
+    cudaError_t e = launch_aprod1_cg(h, h->d_xp64, h->d_q64, s);
+    if (e == cudaSuccess)
+        e = launch_aprod2(h, h->d_q64, h->d_t, kA2Overwrite, s);
+    if (e != cudaSuccess)
+        return e;
+    k_cg_vec1<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc, A.n, h->d_cg,
+                                                h->d_cgargs, h->d_partial + kRedV * kPartialsPerKind,
+                                                h->d_counter + kRedV, loop, in_graph);
+    k_cg_vec2<double><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_s, h->d_d, h->d_xp64, h->d_t,
+                                                        A.n, A.ins0, h->d_cg);
+    return cudaGetLastError();
+}
+
+cudaError_t build_cg64_graph(gsr_handle_t *h)
+{
+    cudaError_t err = cudaSuccess;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle loop;
+    cudaGraphNode_t pre_leaf, wnode;
+    cudaGraphNodeParams cp = {};
+    cudaGraph_t body;
+    cudaStream_t s = h->cap_stream;
+    CG_TRY(cudaGraphCreate(&g, 0));
+    CG_TRY(cudaGraphConditionalHandleCreate(&loop, g, 1u, cudaGraphCondAssignDefault));
+    CG_TRY(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cg64_prologue(h, s, loop, 1);
+    CG_TRY(cudaStreamEndCapture(s, &g));
+    CG_TRY(find_graph_leaf(g, &pre_leaf));
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CG_TRY(cudaGraphAddNode(&wnode, g, &pre_leaf, nullptr, 1, &cp));
+    body = cp.conditional.phGraph_out[0];
+    CG_TRY(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cg64_iteration(h, s, loop, 1);
+    CG_TRY(cudaStreamEndCapture(s, &body));
+    CG_TRY(cudaStreamBeginCaptureToGraph(s, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    k_axpy_p<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_zc, h->d_xm, h->sys.n);
+    CG_TRY(cudaStreamEndCapture(s, &g));
+    CG_TRY(cudaGraphInstantiate(&h->cg64_exec, g, 0));
+    cudaGraphDestroy(g);
+    return cudaSuccess;
+fail:
+    {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(s, &junk);
+            if (junk && junk != g)
+                cudaGraphDestroy(junk);
+        }
+    }
+    if (g)
+        cudaGraphDestroy(g);
+    cudaGetLastError();
+    return err;
+}
+
+cudaError_t run_cg64(gsr_handle_t *h, cudaStream_t st, int max_iter)
+{
+    if (!h->cfg.eager)
+        return cudaGraphLaunch(h->cg64_exec, st);
+    cudaError_t e = cg64_prologue(h, st, 0, 0);
+    for (int it = 0; e == cudaSuccess && it < max_iter; it++) {
+        e = cudaMemcpyAsync(h->h_cg, h->d_cg, sizeof(CgState), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess || h->h_cg->done)
+            break;
+        e = cg64_iteration(h, st, 0, 0);
+    }
+    if (e == cudaSuccess) {
+        k_axpy_p<<<h->grid_vec, kThreads, 0, st>>>(h->d_p, h->d_zc, h->d_xm, h->sys.n);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// binary32 copies of plane k after it changed
+cudaError_t launch_f32_plane(const gsr_handle_t *h, int k, cudaStream_t st)
+{
+    const int64_t mp = h->sys.mp;
+    k_to_f32<<<h->nsm * 8, kThreads, 0, st>>>(h->d_val + k * mp, h->d_val32 + k * mp, h->sys.m);
+    if (k >= kNAstro && k < kNAstro + kNAtt)
+        k_to_f32<<<h->nsm * 8, kThreads, 0, st>>>(h->d_tval + (k - kNAstro) * mp,
+                                                   h->d_tval32 + (k - kNAstro) * mp, h->sys.m);
+    return cudaGetLastError();
 }
 
 }  // namespace gsr

@@ -11,7 +11,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import Config, Dims, MixedResult, Result, check, lib
+from ._lib import CgResult, Config, Dims, MixedResult, Result, check, lib
 
 
 def _torch():
@@ -154,6 +154,38 @@ class Solver:
                                     float(inner_tol), float(atol), _ptr(x)[0], ctypes.byref(res),
                                     _stream(stream)), "gsr_mixed_solve")
         return x, res.as_dict()
+
+    def set_values(self, k, values, stream=None):
+        """Replace nonzero k (0..23; 23 = global column) of every row."""
+        _check_vec(values, self.m, "values")
+        check(lib().gsr_set_values(self._h, int(k), _ptr(values)[0], _stream(stream)),
+              "gsr_set_values")
+
+    def normal_solve(self, g, max_iter=1000, tol=1e-13, q=None, stream=None):
+        """q = (A^T A)^{-1} g by FP64 conjugate gradients; returns (q, info)."""
+        _check_vec(g, self.n, "g")
+        if q is None:
+            q = np.empty(self.n) if isinstance(g, np.ndarray) else _torch().empty_like(g)
+        res = CgResult()
+        check(lib().gsr_normal_solve(self._h, _ptr(g)[0], int(max_iter), float(tol), _ptr(q)[0],
+                                     ctypes.byref(res), _stream(stream)), "gsr_normal_solve")
+        return q, res.as_dict()
+
+    def lsq_backward(self, b, x, gx, max_iter=1000, tol=1e-13, want_glob=True, stream=None):
+        """(dL/db, dL/dA(:, global), info) for the least-squares solution x of b."""
+        _check_vec(b, self.m, "b")
+        _check_vec(x, self.n, "x")
+        _check_vec(gx, self.n, "gx")
+        host = isinstance(b, np.ndarray)
+        mk = (lambda: np.empty(self.m)) if host else (
+            lambda: _torch().empty(self.m, dtype=b.dtype, device=b.device))
+        gb = mk()
+        gg = mk() if want_glob else None
+        res = CgResult()
+        check(lib().gsr_lsq_backward(self._h, _ptr(b)[0], _ptr(x)[0], _ptr(gx)[0], int(max_iter),
+                                     float(tol), _ptr(gb)[0], _ptr(gg)[0] if gg is not None else None,
+                                     ctypes.byref(res), _stream(stream)), "gsr_lsq_backward")
+        return gb, gg, res.as_dict()
 
     def precondition(self, p, stream=None):
         """p = 1/||A(:,j)|| (1 for an empty column); returns p."""
