@@ -261,6 +261,32 @@ int gsr_lsq_backward(void *h, const double *b, const double *x, const double *gx
                      int max_iter, double tol, double *grad_b, double *grad_glob,
                      gsr_cg_result *out, void *stream);
 
+/*
+ * Batched mixed-precision solve of k <= 32 right-hand sides (for example the
+ * Monte-Carlo perturbations of b used to estimate errors): the
+ * gsr_mixed_solve refinement for every column, with the inner
+ * conjugate-gradient iterations of all columns sharing each pass over the
+ * binary32 matrix (sparse times skinny-dense products over column tiles).
+ * B[m*k] and X[n*k] are column-major (column c starts at c*m, c*n); out[k]
+ * receives one result per column.  Handles created with GSR_PREC_MIXED
+ * only.  Column tile and lanes per star: gsr_set_batch_tiling.
+ */
+int gsr_batched_solve(void *h, int k, const double *B, int max_outer,
+                      int max_inner, double inner_tol, double atol, double *X,
+                      gsr_mixed_result *out, void *stream);
+
+/*
+ * The batched inner products on k <= 32 columns, for tests and tuning:
+ * Q[m*k] = A32 X[n*k] and T[n*k] = A32^T Y[m*k] (column-major, device
+ * pointers), with the binary32-product rule of gsr_aprod1_f32.
+ */
+int gsr_batched_products(void *h, int k, const double *X, const double *Y,
+                         double *Q, double *T, void *stream);
+
+/* Column tile kt (1, 2, 4, 8) and lanes per star (8, 16, 32) of the batched
+ * kernels; the next batched call rebuilds its graph.  Defaults 8 and 16. */
+int gsr_set_batch_tiling(void *h, int kt, int lanes);
+
 /* Text of the last CUDA failure seen by this host thread ("" if none). */
 const char *gsr_last_error(void);
 

@@ -29,7 +29,8 @@ EXPORTS = (
     "gsr_config_default", "gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
     "gsr_precondition", "gsr_lsqr_solve", "gsr_last_error", "gsr_info", "gsr_strerror",
     "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32", "gsr_mixed_solve",
-    "gsr_set_values", "gsr_normal_solve", "gsr_lsq_backward",
+    "gsr_set_values", "gsr_normal_solve", "gsr_lsq_backward", "gsr_batched_solve",
+    "gsr_batched_products", "gsr_set_batch_tiling",
 )
 
 
@@ -117,6 +118,9 @@ def lib():
             L.gsr_set_values.argtypes = [P, I, P, P]
             L.gsr_normal_solve.argtypes = [P, P, I, D, P, ctypes.POINTER(CgResult), P]
             L.gsr_lsq_backward.argtypes = [P, P, P, P, I, D, P, P, ctypes.POINTER(CgResult), P]
+            L.gsr_batched_solve.argtypes = [P, I, P, I, I, D, D, P, ctypes.POINTER(MixedResult), P]
+            L.gsr_batched_products.argtypes = [P, I, P, P, P, P, P]
+            L.gsr_set_batch_tiling.argtypes = [P, I, I]
             L.gsr_last_error.restype = ctypes.c_char_p
             L.gsr_strerror.argtypes = [I]
             L.gsr_strerror.restype = ctypes.c_char_p
@@ -125,7 +129,8 @@ def lib():
                          "gsr_precondition", "gsr_lsqr_solve", "gsr_info",
                          "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32",
                          "gsr_mixed_solve", "gsr_set_values", "gsr_normal_solve",
-                         "gsr_lsq_backward"):
+                         "gsr_lsq_backward", "gsr_batched_solve", "gsr_batched_products",
+                         "gsr_set_batch_tiling"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib

@@ -113,6 +113,14 @@ static void release(gsr_handle_t *h)
         cudaGraphExecDestroy(h->cg_exec);
     if (h->cg64_exec)
         cudaGraphExecDestroy(h->cg64_exec);
+    if (h->b_exec)
+        cudaGraphExecDestroy(h->b_exec);
+    if (h->h_bs)
+        cudaFreeHost(h->h_bs);
+    if (h->h_bargs)
+        cudaFreeHost(h->h_bargs);
+    if (h->h_bnorms)
+        cudaFreeHost(h->h_bnorms);
     if (h->h_cg)
         cudaFreeHost(h->h_cg);
     if (h->h_cgargs)
@@ -127,7 +135,10 @@ static void release(gsr_handle_t *h)
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err,
                    h->d_val32, h->d_tval32, h->d_x32, h->d_q32, h->d_c, h->d_s, h->d_d, h->d_t,
                    h->d_zc, h->d_xm, h->d_r, h->d_xneg, h->d_onorm, h->d_cg, h->d_cgargs,
-                   h->d_xp64, h->d_q64};
+                   h->d_xp64, h->d_q64, h->d_biseg, h->d_birow, h->d_bival, h->d_bX32, h->d_bQ32,
+                   h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT, h->d_bS, h->d_bXcm, h->d_bRcm,
+                   h->d_bCcm, h->d_bB, h->d_bnorms, h->d_bpartial, h->d_bcounter, h->d_bs,
+                   h->d_bargs};
     for (void *p : dev)
         if (p)
             cudaFree(p);
@@ -155,6 +166,50 @@ static int create_mixed(gsr_handle_t *h, cudaStream_t st)
     CK(launch_to_f32(h, h->d_tval, h->d_tval32, kNAtt * mp, st));
     A.val32 = h->d_val32;
     A.tval32 = h->d_tval32;
+    // instrument-sorted copy of the whole matrix (batched solve): a stable
+    // counting sort of the 6 m instrumental entries by instrument
+    {
+        std::vector<uint4> rec((size_t)m);
+        CK(cudaMemcpy(rec.data(), h->d_rec, m * sizeof(uint4), cudaMemcpyDeviceToHost));
+        std::vector<uint16_t> ins_host((size_t)(kNInstr * m));
+        for (int64_t i = 0; i < m; i++) {
+            const uint32_t w[3] = {rec[i].y, rec[i].z, rec[i].w};
+            for (int j = 0; j < kNInstr; j++)
+                ins_host[kNInstr * i + j] = (uint16_t)((j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu));
+        }
+        std::vector<uint32_t> code((size_t)m * kNInstr);
+        const int64_t I = A.I;
+        std::vector<uint32_t> seg((size_t)I + 1, 0), irow((size_t)(kNInstr * m));
+        for (int64_t e = 0; e < kNInstr * m; e++)
+            seg[ins_host[e] + 1]++;
+        for (int64_t f = 0; f < I; f++)
+            seg[f + 1] += seg[f];
+        std::vector<uint32_t> pos(seg.begin(), seg.end() - 1);
+        for (int64_t e = 0; e < kNInstr * m; e++) {
+            const uint32_t p = pos[ins_host[e]]++;
+            irow[p] = (uint32_t)(e / kNInstr);
+            code[p] = (uint32_t)e;
+        }
+        TRY(dalloc(h, &h->d_biseg, I + 1));
+        TRY(dalloc(h, &h->d_birow, kNInstr * m));
+        TRY(dalloc(h, &h->d_bival, kNInstr * m));
+        CK(cudaMemcpy(h->d_biseg, seg.data(), (I + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->d_birow, irow.data(), kNInstr * m * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        uint32_t *d_code = nullptr;
+        if (cudaMalloc(&d_code, kNInstr * m * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return GSR_ERR_OOM;
+        }
+        cudaError_t e = cudaMemcpy(d_code, code.data(), kNInstr * m * sizeof(uint32_t),
+                                   cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = launch_gather_instr32(h, d_code, h->d_bival, st);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+        cudaFree(d_code);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "instrument-sorted layout");
+    }
     // ||A diag(p)||_F^2 = number of nonempty columns (column sums of squares > 0)
     CK(cudaMemsetAsync(h->d_s, 0, n * sizeof(double), st));
     CK(launch_aprod2(h, nullptr, h->d_s, kA2Squares, st));
@@ -744,5 +799,194 @@ extern "C" int gsr_lsq_backward(void *hv, const double *b, const double *x, cons
     if (dgb != grad_b)
         CK(cudaMemcpyAsync(grad_b, dgb, A.m * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    return GSR_OK;
+}
+
+// buffers of the batched solve for k columns (leading dimension rounded up
+// to 8 so that the column-tile loads are aligned) and its inner graph
+static int ensure_batched(gsr_handle_t *h, int k)
+{
+    const SysView &A = h->sys;
+    const int ldk = (k + 7) / 8 * 8;
+    if (ldk > h->bk) {
+        void *old[] = {h->d_bX32, h->d_bQ32, h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT};
+        for (void *p : old)
+            if (p)
+                cudaFree(p);
+        h->d_bX32 = nullptr; h->d_bQ32 = nullptr; h->d_bC = nullptr; h->d_bS_ = nullptr;
+        h->d_bD = nullptr; h->d_bZ = nullptr; h->d_bT = nullptr;
+        TRY(dalloc(h, &h->d_bX32, A.n * ldk));
+        TRY(dalloc(h, &h->d_bQ32, A.m * ldk));
+        TRY(dalloc(h, &h->d_bC, A.n * ldk));
+        TRY(dalloc(h, &h->d_bS_, A.n * ldk));
+        TRY(dalloc(h, &h->d_bD, A.n * ldk));
+        TRY(dalloc(h, &h->d_bZ, A.n * ldk));
+        TRY(dalloc(h, &h->d_bT, A.n * ldk));
+        h->bk = ldk;
+    }
+    if (!h->d_bS) {
+        TRY(dalloc(h, &h->d_bS, A.nseg * kNAtt * 8));
+        TRY(dalloc(h, &h->d_bpartial, (int64_t)8 * kMaxPartials));
+        TRY(dalloc(h, &h->d_bcounter, 1));
+        TRY(dalloc(h, &h->d_bs, 1));
+        TRY(dalloc(h, &h->d_bargs, 1));
+        TRY(dalloc(h, &h->d_bnorms, 2 * kMaxBatch));
+        CK(cudaMemset(h->d_bcounter, 0, sizeof(unsigned)));
+        CK(cudaMallocHost((void **)&h->h_bs, sizeof(BatchState)));
+        CK(cudaMallocHost((void **)&h->h_bargs, sizeof(BatchArgs)));
+        CK(cudaMallocHost((void **)&h->h_bnorms, 2 * kMaxBatch * sizeof(double)));
+        h->grid_b1 = batched_grid_rows(h);
+        h->grid_b2 = batched_grid_stars(h);
+        if (h->grid_b1 <= 0 || h->grid_b2 <= 0)
+            return cuda_fail(cudaGetLastError(), "batched occupancy");
+    }
+    if (!h->b_exec || h->b_graph_k != h->bk || h->b_graph_kt != h->b_kt ||
+        h->b_graph_lanes != h->b_lanes) {
+        cudaError_t e = build_batched_graph(h, h->bk);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "build_batched_graph");
+    }
+    return GSR_OK;
+}
+
+static int cm_buffers(gsr_handle_t *h, int k)
+{
+    const SysView &A = h->sys;
+    if (h->d_bXcm && h->bkcm == k)
+        return GSR_OK;
+    void *old[] = {h->d_bXcm, h->d_bRcm, h->d_bCcm, h->d_bB};
+    for (void *p : old)
+        if (p)
+            cudaFree(p);
+    h->d_bXcm = h->d_bRcm = h->d_bCcm = h->d_bB = nullptr;
+    TRY(dalloc(h, &h->d_bXcm, A.n * k));
+    TRY(dalloc(h, &h->d_bRcm, A.m * k));
+    TRY(dalloc(h, &h->d_bCcm, A.n * k));
+    TRY(dalloc(h, &h->d_bB, A.m * k));
+    h->bkcm = k;
+    return GSR_OK;
+}
+
+extern "C" int gsr_set_batch_tiling(void *hv, int kt, int lanes)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || (kt != 1 && kt != 2 && kt != 4 && kt != 8) || (lanes != 8 && lanes != 16 && lanes != 32))
+        return GSR_ERR_ARG;
+    h->b_kt = kt;
+    h->b_lanes = lanes;
+    return GSR_OK;
+}
+
+extern "C" int gsr_batched_products(void *hv, int k, const double *X, const double *Y, double *Q,
+                                    double *T, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !X || !Y || !Q || !T || k < 1 || k > kMaxBatch)
+        return GSR_ERR_ARG;
+    if (h->cfg.precision != GSR_PREC_MIXED)
+        return GSR_ERR_UNSUPPORTED;
+    if (!on_device(X) || !on_device(Y) || !on_device(Q) || !on_device(T))
+        return GSR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const SysView &A = h->sys;
+    TRY(ensure_batched(h, k));
+    CK(cudaMemsetAsync(h->d_bX32, 0, A.n * h->bk * sizeof(float), st));
+    CK(cudaMemsetAsync(h->d_bQ32, 0, A.m * h->bk * sizeof(float), st));
+    CK(launch_b_layout(h, 1, X, h->d_bX32, 1, A.n, k, st));
+    // Y goes into the binary32 m-block; Q32 is produced into d_bX32's partner
+    float *Y32 = h->d_bQ32;
+    CK(launch_b_layout(h, 1, Y, Y32, 1, A.m, k, st));
+    // T = A32^T Y needs Y32 intact while Q = A32 X is formed: use d_bC as the
+    // row-major FP64 T, and a second binary32 m-block for Q
+    float *Q32 = nullptr;
+    if (cudaMalloc(&Q32, A.m * h->bk * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return GSR_ERR_OOM;
+    }
+    cudaError_t e = cudaMemsetAsync(h->d_bC, 0, A.n * h->bk * sizeof(double), st);
+    if (e == cudaSuccess)
+        e = launch_b_products(h, h->bk, h->d_bX32, Q32, Y32, h->d_bC, st);
+    if (e == cudaSuccess)
+        e = launch_b_layout(h, 0, (const double *)Q32, Q, 2, A.m, k, st);
+    if (e == cudaSuccess)
+        e = launch_b_layout(h, 0, h->d_bC, T, 0, A.n, k, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    cudaFree(Q32);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "gsr_batched_products");
+    return GSR_OK;
+}
+
+extern "C" int gsr_batched_solve(void *hv, int k, const double *B, int max_outer, int max_inner,
+                                 double inner_tol, double atol, double *X, gsr_mixed_result *out,
+                                 void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !B || !X || k < 1 || k > kMaxBatch || max_outer < 0 || max_inner < 1 ||
+        !(inner_tol >= 0.0) || !(atol >= 0.0))
+        return GSR_ERR_ARG;
+    if (h->cfg.precision != GSR_PREC_MIXED)
+        return GSR_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const SysView &A = h->sys;
+    TRY(ensure_batched(h, k));
+    TRY(cm_buffers(h, k));
+    CK(cudaMemcpyAsync(h->d_bB, B, A.m * k * sizeof(double), cudaMemcpyDefault, st));
+    CK(enqueue_precondition(h, h->d_p, st));
+    CK(cudaMemsetAsync(h->d_bXcm, 0, A.n * k * sizeof(double), st));
+    CK(cudaMemcpyAsync(h->d_bRcm, h->d_bB, A.m * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    h->h_bargs->max_inner = max_inner;
+    h->h_bargs->tol = inner_tol;
+    CK(cudaMemcpyAsync(h->d_bargs, h->h_bargs, sizeof(BatchArgs), cudaMemcpyHostToDevice, st));
+    const double anorm = sqrt(h->n_nonempty);
+    std::vector<gsr_mixed_result> res((size_t)k);
+    for (int c = 0; c < k; c++)
+        res[c].anorm = anorm;
+    for (int it = 0;; it++) {
+        // FP64 normal residuals, one column at a time
+        CK(cudaMemsetAsync(h->d_bCcm, 0, A.n * k * sizeof(double), st));
+        for (int c = 0; c < k; c++)
+            CK(launch_aprod2(h, h->d_bRcm + (int64_t)c * A.m, h->d_bCcm + (int64_t)c * A.n,
+                             kA2Accumulate, st));
+        CK(launch_b_norms(h, h->d_bCcm, h->d_bRcm, k, h->d_bnorms, st));
+        CK(cudaMemcpyAsync(h->h_bnorms, h->d_bnorms, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int all = 1;
+        for (int c = 0; c < k; c++) {
+            res[c].arnorm = sqrt(h->h_bnorms[2 * c]);
+            res[c].rnorm = sqrt(h->h_bnorms[2 * c + 1]);
+            if (!isfinite(res[c].arnorm) || !isfinite(res[c].rnorm))
+                return GSR_ERR_NONFINITE;
+            res[c].converged = res[c].arnorm <= atol * anorm * res[c].rnorm;
+            all &= res[c].converged;
+        }
+        if (all || it >= max_outer)
+            break;
+        // inner solve of all columns (converged ones have a tiny right-hand side)
+        CK(cudaMemsetAsync(h->d_bC, 0, A.n * h->bk * sizeof(double), st));
+        CK(launch_b_layout(h, 1, h->d_bCcm, h->d_bC, 0, A.n, k, st));
+        CK(run_batched_inner(h, h->bk, max_inner, st));
+        CK(launch_b_update_x(h, h->d_bXcm, k, st));
+        CK(cudaMemcpyAsync(h->h_bs, h->d_bs, sizeof(BatchState), cudaMemcpyDeviceToHost, st));
+        // FP64 residuals r_c = b_c - A x_c
+        CK(cudaMemcpyAsync(h->d_bRcm, h->d_bB, A.m * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        for (int c = 0; c < k; c++) {
+            CK(launch_neg(h, h->d_bXcm + (int64_t)c * A.n, h->d_xneg, A.n, st));
+            CK(launch_aprod1(h, h->d_xneg, h->d_bRcm + (int64_t)c * A.m, 0, st));
+        }
+        CK(cudaStreamSynchronize(st));
+        if (h->h_bs->nonfinite)
+            return GSR_ERR_NONFINITE;
+        for (int c = 0; c < k; c++) {
+            res[c].outer = it + 1;
+            res[c].inner += h->h_bs->it[c];
+        }
+    }
+    CK(cudaMemcpyAsync(X, h->d_bXcm, A.n * k * sizeof(double), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    if (out)
+        for (int c = 0; c < k; c++)
+            out[c] = res[c];
     return GSR_OK;
 }

@@ -1,0 +1,782 @@
+// Batched k right-hand-side solve: the mixed-precision refinement of
+// gsr_mixed.cu for k right-hand sides at once.  The inner products become
+// skinny sparse-times-dense products: every row's binary32 values are read
+// once per column tile and applied to KT columns (KT = 1, 2, 4 or 8), so the
+// matrix traffic of k solves is paid ceil(k/KT) times instead of k times.
+//
+// Dense vectors of the inner solve are row-major with leading dimension k:
+// entry (j, c) of an n x k block is at j*k + c, so the gather of unknown j
+// fetches KT consecutive values (one 32-byte sector for KT = 8 binary32).
+//
+// Column sections:
+//   aprod 1: row-parallel, one row per lane (as the single form)
+//   aprod 2: astrometric + global: star-parallel, G lanes per star;
+//            attitude: offset-sorted copy, one warp per offset, one axis at a
+//            time (4 taps x KT columns of double-float sums per lane);
+//            instrumental: instrument-sorted copy of the whole matrix, one
+//            warp per instrument.  No atomics except the global column.
+// CG: k independent Hestenes-Stiefel recurrences with per-column scalars.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gsr_df.cuh"
+#include "gsr_internal.cuh"
+#include "gsr_reduce.cuh"
+
+namespace gsr {
+
+__device__ __forceinline__ uint32_t instr_b(const uint4 &rc, int j)
+{
+    const uint32_t w = (j < 2) ? rc.y : ((j < 4) ? rc.z : rc.w);
+    return (j & 1) ? (w >> 16) : (w & 0xffffu);
+}
+
+template <int KT>
+__device__ __forceinline__ void load_cols(const float *__restrict__ p, float (&v)[KT])
+{
+    if constexpr (KT == 8) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else if constexpr (KT == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if constexpr (KT == 2) {
+        const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = a.x; v[1] = a.y;
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+
+// grid reduction of KT per-column sums into bs->sums[c0 .. c0+KT)
+template <int KT>
+__device__ __forceinline__ bool grid_reduce_cols(double (&v)[KT], double *partial, unsigned *counter)
+{
+    return grid_reduce<KT>(v, partial, counter);
+}
+
+// ---------------------------------------------------------------------------
+// aprod 1 on KT columns: Q32[:, c0+c] = fl32(A32 X32[:, c0+c]), with
+// |Q[:, c]|^2 and alpha_c = gamma_c / |Q[:, c]|^2 (0 for a finished column)
+// ---------------------------------------------------------------------------
+template <int KT>
+__global__ void __launch_bounds__(kThreads)
+k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ldk, int c0,
+           BatchState *bs, double *partial, unsigned *counter)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t ntiles = (A.m + 31) >> 5;
+    const int64_t mp = A.mp;
+    double nrm[KT];
+#pragma unroll
+    for (int c = 0; c < KT; c++)
+        nrm[c] = 0.0;
+    for (int64_t t = warp; t < ntiles; t += nwarps) {
+        const int64_t r = (t << 5) + lane;
+        if (r >= A.m)
+            continue;
+        uint32_t s = A.tile_star[t];
+        while ((int64_t)A.star_ptr[s + 1] <= r)
+            ++s;
+        const uint4 rc = __ldcs(A.rec + r);
+        float h[KT], l[KT];
+#pragma unroll
+        for (int c = 0; c < KT; c++)
+            h[c] = l[c] = 0.f;
+        const float *v = A.val32 + r;
+#pragma unroll
+        for (int k = 0; k < kNPar; k++) {
+            int64_t col;
+            if (k < kNAstro)
+                col = (int64_t)kNAstro * s + k;
+            else if (k < kNAstro + kNAtt)
+                col = A.att0 + ((k - kNAstro) >> 2) * A.D + rc.x + ((k - kNAstro) & 3);
+            else if (k < kNPar - 1)
+                col = A.ins0 + instr_b(rc, k - kNAstro - kNAtt);
+            else
+                col = A.glb0;
+            const float a = __ldcs(v + k * mp);
+            float xv[KT];
+            load_cols<KT>(X + col * ldk + c0, xv);
+#pragma unroll
+            for (int c = 0; c < KT; c++)
+                df_acc(h[c], l[c], __fmul_rn(a, xv[c]));
+        }
+        float *q = Q + r * ldk + c0;
+#pragma unroll
+        for (int c = 0; c < KT; c++) {
+            const float qv = __fadd_rn(h[c], l[c]);
+            q[c] = qv;
+            const double qd = f2d(qv);
+            nrm[c] = fma(qd, qd, nrm[c]);
+        }
+    }
+    if (grid_reduce_cols<KT>(nrm, partial, counter) && threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < KT; c++) {
+            const int cc = c0 + c;
+            bs->xi[cc] = nrm[c];
+            bs->alpha[cc] = (!bs->done[cc] && nrm[c] > 0.0) ? bs->gamma[cc] / nrm[c] : 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// aprod 2, astrometric and global nonzeros on KT columns (star-parallel):
+// T[astro rows] written, T[global] accumulated into zeroed memory
+// ---------------------------------------------------------------------------
+template <int KT, int G>
+__global__ void __launch_bounds__(kThreads)
+k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ldk, int c0)
+{
+    __shared__ double s_g[kThreads / 32][KT];
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & (G - 1);
+    const int gw = (threadIdx.x & 31) / G;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t mp = A.mp;
+    float gh[KT], gl[KT];
+#pragma unroll
+    for (int c = 0; c < KT; c++)
+        gh[c] = gl[c] = 0.f;
+    for (int64_t s0 = warp * GPW; s0 < A.S; s0 += nwarps * GPW) {
+        const int64_t s = s0 + gw;
+        uint32_t r0 = 0, r1 = 0;
+        if (s < A.S) {
+            r0 = A.star_ptr[s];
+            r1 = A.star_ptr[s + 1];
+        }
+        float ah[kNAstro][KT], al[kNAstro][KT];
+#pragma unroll
+        for (int k = 0; k < kNAstro; k++)
+#pragma unroll
+            for (int c = 0; c < KT; c++)
+                ah[k][c] = al[k][c] = 0.f;
+        for (uint32_t r = r0 + lane; r < r1; r += G) {
+            const float *v = A.val32 + r;
+            float yv[KT];
+            load_cols<KT>(Y + (int64_t)r * ldk + c0, yv);
+#pragma unroll
+            for (int k = 0; k < kNAstro; k++) {
+                const float a = __ldcs(v + k * mp);
+#pragma unroll
+                for (int c = 0; c < KT; c++)
+                    df_acc(ah[k][c], al[k][c], __fmul_rn(a, yv[c]));
+            }
+            const float ag = __ldcs(v + 23 * mp);
+#pragma unroll
+            for (int c = 0; c < KT; c++)
+                df_acc(gh[c], gl[c], __fmul_rn(ag, yv[c]));
+        }
+#pragma unroll
+        for (int k = 0; k < kNAstro; k++) {
+#pragma unroll
+            for (int c = 0; c < KT; c++) {
+                double t = df_to_d(ah[k][c], al[k][c]);
+#pragma unroll
+                for (int off = G / 2; off > 0; off >>= 1)
+                    t += __shfl_xor_sync(0xffffffffu, t, off);
+                if (lane == 0 && s < A.S)
+                    T[((int64_t)kNAstro * s + k) * ldk + c0 + c] = t;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < KT; c++) {
+        const double g = warp_sum(df_to_d(gh[c], gl[c]));
+        if ((threadIdx.x & 31) == 0)
+            s_g[threadIdx.x >> 5][c] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x < KT) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; w++)
+            t += s_g[w][threadIdx.x];
+        atomicAdd(T + A.glb0 * ldk + c0 + threadIdx.x, t);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// aprod 2, attitude nonzeros on KT columns: one warp per offset o and axis a
+// sums tap j of column c into S[((o * 3 + a) * 4 + j) * KT + c]
+// ---------------------------------------------------------------------------
+template <int KT>
+__global__ void __launch_bounds__(kThreads)
+k_b_att(SysView A, const float *__restrict__ Y, double *__restrict__ S, int ldk, int c0)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t mp = A.mp;
+    constexpr int NV = 4 * KT;  // sums per (offset, axis)
+    for (int64_t oa = warp; oa < A.nseg * 3; oa += nwarps) {
+        const int64_t o = oa / 3;
+        const int a = (int)(oa - o * 3);
+        const uint32_t e0 = A.seg[o], e1 = A.seg[o + 1];
+        float h[NV], l[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++)
+            h[k] = l[k] = 0.f;
+        for (uint32_t e = e0 + lane; e < e1; e += 32) {
+            float yv[KT];
+            load_cols<KT>(Y + (int64_t)__ldcs(A.perm + e) * ldk + c0, yv);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const float v = __ldcs(A.tval32 + (4 * a + j) * mp + e);
+#pragma unroll
+                for (int c = 0; c < KT; c++)
+                    df_acc(h[j * KT + c], l[j * KT + c], __fmul_rn(v, yv[c]));
+            }
+        }
+        // reduce-scatter of NV sums over the warp (NV is a power of two <= 32)
+        double r[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++)
+            r[k] = df_to_d(h[k], l[k]);
+#pragma unroll
+        for (int half = NV / 2, off = 16; half >= 1; half >>= 1, off >>= 1) {
+            const bool upper = (lane & off) != 0;
+#pragma unroll
+            for (int k = 0; k < half; k++) {
+                const double send = upper ? r[k] : r[k + half];
+                const double keep = upper ? r[k + half] : r[k];
+                r[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+        // the first log2(NV) exchanges used offsets 16, 8, ...; lanes that
+        // differ only in the lower bits hold partial sums of the same index
+        constexpr int LOGNV = (NV >= 32) ? 5 : (NV >= 16) ? 4 : (NV >= 8) ? 3 : (NV >= 4) ? 2 : 1;
+        constexpr int REST = 32 >> LOGNV;
+        double tot = r[0];
+#pragma unroll
+        for (int off = REST / 2; off > 0; off >>= 1)
+            tot += __shfl_xor_sync(0xffffffffu, tot, off);
+        // index held by this lane: bits 4 .. 5-LOGNV of the lane, high first
+        const int idx = lane / REST;
+        if ((lane % REST) == 0)
+            S[(o * 3 + a) * NV + idx] = tot;
+    }
+}
+
+// attitude columns of T from S; ldk-strided, column tile c0
+template <int KT>
+__global__ void k_b_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ T,
+                                int ldk, int c0)
+{
+    const int64_t total = 3 * A.D * KT;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % KT);
+        const int64_t colrow = i / KT;  // a * D + k
+        const int64_t a = colrow / A.D, k = colrow - a * A.D;
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int64_t o = k - j;
+            if (o >= 0 && o < A.nseg)
+                t += S[((o * 3 + a) * 4 + j) * KT + c];
+        }
+        T[(A.att0 + colrow) * ldk + c0 + c] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// aprod 2, instrumental nonzeros on KT columns: one warp per instrument f
+// over its entries (row ibrow[e], value ibval32[e]) in the instrument-sorted
+// copy of the whole matrix
+// ---------------------------------------------------------------------------
+template <int KT>
+__global__ void __launch_bounds__(kThreads)
+k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restrict__ irow,
+          const float *__restrict__ ival, const float *__restrict__ Y, double *__restrict__ T,
+          int ldk, int c0)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t f = warp; f < A.I; f += nwarps) {
+        const uint32_t e0 = iseg[f], e1 = iseg[f + 1];
+        float h[KT], l[KT];
+#pragma unroll
+        for (int c = 0; c < KT; c++)
+            h[c] = l[c] = 0.f;
+        for (uint32_t e = e0 + lane; e < e1; e += 32) {
+            float yv[KT];
+            load_cols<KT>(Y + (int64_t)__ldcs(irow + e) * ldk + c0, yv);
+            const float v = __ldcs(ival + e);
+#pragma unroll
+            for (int c = 0; c < KT; c++)
+                df_acc(h[c], l[c], __fmul_rn(v, yv[c]));
+        }
+#pragma unroll
+        for (int c = 0; c < KT; c++) {
+            const double t = warp_sum(df_to_d(h[c], l[c]));
+            if (lane == 0)
+                T[(A.ins0 + f) * ldk + c0 + c] = t;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batched CG vector kernels: n x k row-major FP64 blocks, per-column scalars
+// ---------------------------------------------------------------------------
+// S = p o C, Dd = S, Z = 0, X32 = fl32(p o Dd), gamma_c = |S_c|^2; zeroes the
+// global row of T.  One launch per column tile (c0, KT).
+template <int KT>
+__global__ void __launch_bounds__(kThreads)
+k_b_init(const double *__restrict__ p, const double *__restrict__ C, double *__restrict__ Sv,
+         double *__restrict__ Dd, double *__restrict__ Z, float *__restrict__ X32,
+         double *__restrict__ T, int64_t n, int64_t glb0, int ldk, int c0, BatchState *bs,
+         const BatchArgs *args, double *partial, unsigned *counter)
+{
+    double acc[KT];
+#pragma unroll
+    for (int c = 0; c < KT; c++)
+        acc[c] = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double pj = p[j];
+#pragma unroll
+        for (int c = 0; c < KT; c++) {
+            const int64_t i = j * ldk + c0 + c;
+            const double sj = pj * C[i];
+            Sv[i] = sj;
+            Dd[i] = sj;
+            Z[i] = 0.0;
+            X32[i] = (float)(pj * sj);
+            acc[c] = fma(sj, sj, acc[c]);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < KT)
+        T[glb0 * ldk + c0 + threadIdx.x] = 0.0;
+    if (grid_reduce<KT>(acc, partial, counter) && threadIdx.x == 0) {
+        if (c0 == 0) {
+            bs->nonfinite = 0;
+            bs->all_done = 0;
+        }
+#pragma unroll
+        for (int c = 0; c < KT; c++) {
+            const int cc = c0 + c;
+            bs->gamma[cc] = acc[c];
+            bs->gamma0[cc] = acc[c];
+            bs->beta[cc] = 0.0;
+            bs->done[cc] = (acc[c] > 0.0) ? 0 : 1;
+            bs->it[cc] = 0;
+        }
+    }
+}
+
+// S_c -= alpha_c p o T_c, Z_c += alpha_c Dd_c, gamma'_c = |S_c|^2
+template <int KT>
+__global__ void __launch_bounds__(kThreads)
+k_b_vec1(const double *__restrict__ p, const double *__restrict__ T, double *__restrict__ Sv,
+         const double *__restrict__ Dd, double *__restrict__ Z, int64_t n, int ldk, int c0,
+         BatchState *bs, const BatchArgs *args, double *partial, unsigned *counter)
+{
+    double al[KT], acc[KT];
+#pragma unroll
+    for (int c = 0; c < KT; c++) {
+        al[c] = bs->alpha[c0 + c];
+        acc[c] = 0.0;
+    }
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double pj = p[j];
+#pragma unroll
+        for (int c = 0; c < KT; c++) {
+            const int64_t i = j * ldk + c0 + c;
+            const double sj = fma(-al[c], pj * T[i], Sv[i]);
+            Sv[i] = sj;
+            Z[i] = fma(al[c], Dd[i], Z[i]);
+            acc[c] = fma(sj, sj, acc[c]);
+        }
+    }
+    if (grid_reduce<KT>(acc, partial, counter) && threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < KT; c++) {
+            const int cc = c0 + c;
+            if (bs->done[cc]) {
+                bs->beta[cc] = 0.0;
+                continue;
+            }
+            const double gnew = acc[c];
+            bs->beta[cc] = gnew / bs->gamma[cc];
+            bs->gamma[cc] = gnew;
+            bs->it[cc] += 1;
+            if (!isfinite(gnew))
+                bs->nonfinite = 1;
+            if (!isfinite(gnew) || gnew <= args->tol * args->tol * bs->gamma0[cc] ||
+                bs->it[cc] >= args->max_inner)
+                bs->done[cc] = 1;
+        }
+    }
+}
+
+// Dd = S + beta_c Dd, X32 = fl32(p o Dd); zeroes the global row of T
+template <int KT>
+__global__ void k_b_vec2(const double *__restrict__ p, const double *__restrict__ Sv,
+                         double *__restrict__ Dd, float *__restrict__ X32, double *__restrict__ T,
+                         int64_t n, int64_t glb0, int ldk, int c0, const BatchState *bs)
+{
+    double be[KT];
+#pragma unroll
+    for (int c = 0; c < KT; c++)
+        be[c] = bs->beta[c0 + c];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double pj = p[j];
+#pragma unroll
+        for (int c = 0; c < KT; c++) {
+            const int64_t i = j * ldk + c0 + c;
+            const double dj = fma(be[c], Dd[i], Sv[i]);
+            Dd[i] = dj;
+            X32[i] = (float)(pj * dj);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < KT)
+        T[glb0 * ldk + c0 + threadIdx.x] = 0.0;
+}
+
+// loop flag: clear when every column is done
+__global__ void k_b_flag(BatchState *bs, int k, cudaGraphConditionalHandle loop, int in_graph)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int all = 1;
+        for (int c = 0; c < k; c++)
+            all &= bs->done[c];
+        bs->all_done = all;
+        if (all && in_graph)
+            cudaGraphSetConditional(loop, 0u);
+    }
+}
+
+// generic layout change with optional binary32 output: to_rm = 1 maps a
+// column-major (rows x k) block to row-major, 0 the reverse
+__global__ void k_b_layout(int to_rm, const double *__restrict__ src, double *__restrict__ dst64,
+                           float *__restrict__ dst32, int64_t rows, int k, int ldk)
+{
+    const int64_t total = rows * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / rows;
+        const int64_t r = i - c * rows;
+        const int64_t rm = r * ldk + c, cm = i;
+        const double v = to_rm ? src[cm] : src[rm];
+        const int64_t to = to_rm ? rm : cm;
+        if (dst32)
+            dst32[to] = (float)v;
+        else
+            dst64[to] = v;
+    }
+}
+
+// row-major binary32 (rows x ldk) -> column-major FP64 (rows x k)
+__global__ void k_b_rm32_to_cm(const float *__restrict__ src, double *__restrict__ dst, int64_t rows,
+                               int k, int ldk)
+{
+    const int64_t total = rows * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / rows;
+        const int64_t r = i - c * rows;
+        dst[i] = (double)src[r * ldk + c];
+    }
+}
+
+// dst_f32: 0 FP64 out, 1 binary32 out, 2 binary32 row-major source -> FP64
+// column-major out.  The row-major side has leading dimension h->bk.
+cudaError_t launch_b_layout(const gsr_handle_t *h, int to_rm, const double *src, void *dst,
+                            int dst_f32, int64_t rows, int k, cudaStream_t st)
+{
+    if (dst_f32 == 2)
+        k_b_rm32_to_cm<<<h->nsm * 8, kThreads, 0, st>>>((const float *)src, (double *)dst, rows, k,
+                                                         h->bk);
+    else
+        k_b_layout<<<h->nsm * 8, kThreads, 0, st>>>(to_rm, src, dst_f32 ? nullptr : (double *)dst,
+                                                     dst_f32 ? (float *)dst : nullptr, rows, k, h->bk);
+    return cudaGetLastError();
+}
+
+// X[:, c] += p o Z[:, c] (X column-major n x k, Z row-major with leading
+// dimension ldk)
+__global__ void k_b_update_x(const double *__restrict__ p, const double *__restrict__ Z,
+                             double *__restrict__ X, int64_t n, int k, int ldk)
+{
+    const int64_t total = n * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / n);
+        const int64_t j = i - c * n;
+        X[i] = fma(p[j], Z[j * ldk + c], X[i]);
+    }
+}
+
+// per-column |p o C_c|^2 and |R_c|^2 (column-major blocks), one block per
+// column pair entry; deterministic per-column tree sums
+__global__ void __launch_bounds__(kThreads)
+k_b_norms(const double *__restrict__ p, const double *__restrict__ C, const double *__restrict__ R,
+          int64_t n, int64_t m, double *out)
+{
+    const int c = blockIdx.x;  // one block per column
+    double acc[2] = {0.0, 0.0};
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const double v = p[j] * C[c * n + j];
+        acc[0] = fma(v, v, acc[0]);
+    }
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+        const double v = R[c * m + i];
+        acc[1] = fma(v, v, acc[1]);
+    }
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        out[2 * c] = acc[0];
+        out[2 * c + 1] = acc[1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int KT>
+static cudaError_t b_aprod1(const gsr_handle_t *h, const float *X, float *Q, int ldk, int c0,
+                            cudaStream_t st)
+{
+    k_b_aprod1<KT><<<h->grid_b1, kThreads, 0, st>>>(h->sys, X, Q, ldk, c0, h->d_bs,
+                                                    h->d_bpartial, h->d_bcounter);
+    return cudaGetLastError();
+}
+
+template <int KT>
+static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, int ldk, int c0,
+                            cudaStream_t st)
+{
+    switch (h->b_lanes) {
+    case 8: k_b_stars<KT, 8><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, c0); break;
+    case 32: k_b_stars<KT, 32><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, c0); break;
+    default: k_b_stars<KT, 16><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, c0); break;
+    }
+    k_b_att<KT><<<h->grid_att, kThreads, 0, st>>>(h->sys, Y, h->d_bS, ldk, c0);
+    k_b_att_combine<KT><<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_bS, T, ldk, c0);
+    k_b_instr<KT><<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_biseg, h->d_birow, h->d_bival, Y, T,
+                                                  ldk, c0);
+    return cudaGetLastError();
+}
+
+template <int KT>
+static cudaError_t b_prologue_tile(const gsr_handle_t *h, int ldk, int c0, cudaStream_t s)
+{
+    k_b_init<KT><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_bC, h->d_bS_, h->d_bD, h->d_bZ,
+                                                   h->d_bX32, h->d_bT, h->sys.n, h->sys.glb0, ldk,
+                                                   c0, h->d_bs, h->d_bargs, h->d_bpartial,
+                                                   h->d_bcounter);
+    return cudaGetLastError();
+}
+
+template <int KT>
+static cudaError_t b_iteration_tile_a(const gsr_handle_t *h, int ldk, int c0, cudaStream_t s)
+{
+    cudaError_t e = b_aprod1<KT>(h, h->d_bX32, h->d_bQ32, ldk, c0, s);
+    if (e == cudaSuccess)
+        e = b_aprod2<KT>(h, h->d_bQ32, h->d_bT, ldk, c0, s);
+    if (e != cudaSuccess)
+        return e;
+    k_b_vec1<KT><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_bT, h->d_bS_, h->d_bD, h->d_bZ,
+                                                   h->sys.n, ldk, c0, h->d_bs, h->d_bargs,
+                                                   h->d_bpartial, h->d_bcounter);
+    k_b_vec2<KT><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_bS_, h->d_bD, h->d_bX32, h->d_bT,
+                                                   h->sys.n, h->sys.glb0, ldk, c0, h->d_bs);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_dispatch(const gsr_handle_t *h, int kt, int which, int ldk, int c0,
+                              cudaStream_t s)
+{
+    switch (kt) {
+    case 1: return which ? b_iteration_tile_a<1>(h, ldk, c0, s) : b_prologue_tile<1>(h, ldk, c0, s);
+    case 2: return which ? b_iteration_tile_a<2>(h, ldk, c0, s) : b_prologue_tile<2>(h, ldk, c0, s);
+    case 4: return which ? b_iteration_tile_a<4>(h, ldk, c0, s) : b_prologue_tile<4>(h, ldk, c0, s);
+    default: return which ? b_iteration_tile_a<8>(h, ldk, c0, s) : b_prologue_tile<8>(h, ldk, c0, s);
+    }
+}
+
+// the inner solve of the k columns: prologue, then iterations until every
+// column is done (graph with a conditional loop, or host-driven in eager mode)
+static cudaError_t b_prologue(const gsr_handle_t *h, int k, cudaStream_t s,
+                              cudaGraphConditionalHandle loop, int in_graph)
+{
+    for (int c0 = 0; c0 < k; c0 += h->b_kt) {
+        cudaError_t e = b_dispatch(h, h->b_kt, 0, k, c0, s);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k_b_flag<<<1, 32, 0, s>>>(h->d_bs, k, loop, in_graph);
+    return cudaGetLastError();
+}
+
+static cudaError_t b_iteration(const gsr_handle_t *h, int k, cudaStream_t s,
+                               cudaGraphConditionalHandle loop, int in_graph)
+{
+    for (int c0 = 0; c0 < k; c0 += h->b_kt) {
+        cudaError_t e = b_dispatch(h, h->b_kt, 1, k, c0, s);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k_b_flag<<<1, 32, 0, s>>>(h->d_bs, k, loop, in_graph);
+    return cudaGetLastError();
+}
+
+#define B_TRY(x)                        \
+    do {                                \
+        cudaError_t e_ = (x);           \
+        if (e_ != cudaSuccess) {        \
+            err = e_;                   \
+            goto fail;                  \
+        }                               \
+    } while (0)
+
+cudaError_t find_graph_leaf(cudaGraph_t g, cudaGraphNode_t *leaf);
+
+cudaError_t build_batched_graph(gsr_handle_t *h, int k)
+{
+    cudaError_t err = cudaSuccess;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle loop;
+    cudaGraphNode_t pre_leaf, wnode;
+    cudaGraphNodeParams cp = {};
+    cudaGraph_t body;
+    cudaStream_t s = h->cap_stream;
+    if (h->b_exec) {
+        cudaGraphExecDestroy(h->b_exec);
+        h->b_exec = nullptr;
+    }
+    B_TRY(cudaGraphCreate(&g, 0));
+    B_TRY(cudaGraphConditionalHandleCreate(&loop, g, 1u, cudaGraphCondAssignDefault));
+    B_TRY(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    b_prologue(h, k, s, loop, 1);
+    B_TRY(cudaStreamEndCapture(s, &g));
+    B_TRY(find_graph_leaf(g, &pre_leaf));
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    B_TRY(cudaGraphAddNode(&wnode, g, &pre_leaf, nullptr, 1, &cp));
+    body = cp.conditional.phGraph_out[0];
+    B_TRY(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    b_iteration(h, k, s, loop, 1);
+    B_TRY(cudaStreamEndCapture(s, &body));
+    B_TRY(cudaGraphInstantiate(&h->b_exec, g, 0));
+    cudaGraphDestroy(g);
+    h->b_graph_k = k;
+    h->b_graph_kt = h->b_kt;
+    h->b_graph_lanes = h->b_lanes;
+    return cudaSuccess;
+fail:
+    {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(s, &junk);
+            if (junk && junk != g)
+                cudaGraphDestroy(junk);
+        }
+    }
+    if (g)
+        cudaGraphDestroy(g);
+    cudaGetLastError();
+    return err;
+}
+
+cudaError_t run_batched_inner(gsr_handle_t *h, int k, int max_inner, cudaStream_t st)
+{
+    if (!h->cfg.eager)
+        return cudaGraphLaunch(h->b_exec, st);
+    cudaError_t e = b_prologue(h, k, st, 0, 0);
+    for (int it = 0; e == cudaSuccess && it < max_inner + 1; it++) {
+        e = cudaMemcpyAsync(h->h_bs, h->d_bs, sizeof(BatchState), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess || h->h_bs->all_done)
+            break;
+        e = b_iteration(h, k, st, 0, 0);
+    }
+    return e;
+}
+
+cudaError_t launch_b_update_x(const gsr_handle_t *h, double *X, int k, cudaStream_t st)
+{
+    k_b_update_x<<<h->nsm * 8, kThreads, 0, st>>>(h->d_p, h->d_bZ, X, h->sys.n, k, h->bk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_norms(const gsr_handle_t *h, const double *C, const double *R, int k,
+                           double *out, cudaStream_t st)
+{
+    k_b_norms<<<k, kThreads, 0, st>>>(h->d_p, C, R, h->sys.n, h->sys.m, out);
+    return cudaGetLastError();
+}
+
+// single products on the binary32 copy for k columns (row-major blocks),
+// for the parity tests and the tuner: Q = A32 X and T = A32^T Y
+cudaError_t launch_b_products(const gsr_handle_t *h, int k, const float *X, float *Q, const float *Y,
+                              double *T, cudaStream_t st)
+{
+    for (int c0 = 0; c0 < k; c0 += h->b_kt) {
+        cudaError_t e;
+        switch (h->b_kt) {
+        case 1: e = b_aprod1<1>(h, X, Q, k, c0, st); if (e == cudaSuccess) e = b_aprod2<1>(h, Y, T, k, c0, st); break;
+        case 2: e = b_aprod1<2>(h, X, Q, k, c0, st); if (e == cudaSuccess) e = b_aprod2<2>(h, Y, T, k, c0, st); break;
+        case 4: e = b_aprod1<4>(h, X, Q, k, c0, st); if (e == cudaSuccess) e = b_aprod2<4>(h, Y, T, k, c0, st); break;
+        default: e = b_aprod1<8>(h, X, Q, k, c0, st); if (e == cudaSuccess) e = b_aprod2<8>(h, Y, T, k, c0, st); break;
+        }
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+// ival32[e] = fl32(val[17 + code % 6][code / 6]) for the entry code 6 row + slot
+__global__ void k_gather_instr32(SysView A, const uint32_t *__restrict__ code, float *__restrict__ out)
+{
+    const int64_t ne = kNInstr * A.m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = code[e];
+        out[e] = (float)A.val[(17 + g % kNInstr) * A.mp + g / kNInstr];
+    }
+}
+
+cudaError_t launch_gather_instr32(const gsr_handle_t *h, const uint32_t *code, float *out,
+                                  cudaStream_t st)
+{
+    k_gather_instr32<<<h->nsm * 8, kThreads, 0, st>>>(h->sys, code, out);
+    return cudaGetLastError();
+}
+
+int batched_grid_rows(const gsr_handle_t *h)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_b_aprod1<8>, kThreads, 0) != cudaSuccess ||
+        occ <= 0)
+        return -1;
+    int64_t g = (int64_t)h->nsm * occ;
+    return (int)(g > kMaxPartials ? kMaxPartials : g);
+}
+
+int batched_grid_stars(const gsr_handle_t *h)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_b_stars<8, 16>, kThreads, 0) !=
+            cudaSuccess ||
+        occ <= 0)
+        return -1;
+    int64_t g = (int64_t)h->nsm * occ;
+    return (int)(g > kMaxPartials ? kMaxPartials : g);
+}
+
+}  // namespace gsr

@@ -69,6 +69,18 @@ struct CgArgs {
     double tol;
 };
 
+// Per-column state of the batched inner solve (at most kMaxBatch columns).
+constexpr int kMaxBatch = 32;
+struct BatchState {
+    double gamma[kMaxBatch], gamma0[kMaxBatch], xi[kMaxBatch], alpha[kMaxBatch], beta[kMaxBatch];
+    int it[kMaxBatch], done[kMaxBatch];
+    int all_done, nonfinite;
+};
+struct BatchArgs {
+    int max_inner;
+    double tol;
+};
+
 // Per-solve arguments, read by the graph's kernels from device memory so one
 // instantiated graph serves every call.
 struct SolveArgs {
@@ -119,6 +131,23 @@ struct gsr_handle_t {
     double *h_onorm = nullptr;
     cudaGraphExec_t cg_exec = nullptr;
     cudaGraphExec_t cg64_exec = nullptr;   // FP64 normal-equation CG
+    // batched k-RHS solve
+    uint32_t *d_biseg = nullptr, *d_birow = nullptr;  // instrument-sorted copy of A
+    float *d_bival = nullptr;
+    int bk = 0;                                       // columns the buffers hold
+    int bkcm = 0;                                     // columns of the column-major buffers
+    float *d_bX32 = nullptr, *d_bQ32 = nullptr;
+    double *d_bC = nullptr, *d_bS_ = nullptr, *d_bD = nullptr, *d_bZ = nullptr, *d_bT = nullptr;
+    double *d_bS = nullptr;                           // attitude sums of one column tile
+    double *d_bXcm = nullptr, *d_bRcm = nullptr, *d_bCcm = nullptr, *d_bB = nullptr;
+    double *d_bnorms = nullptr, *h_bnorms = nullptr;
+    double *d_bpartial = nullptr;
+    unsigned *d_bcounter = nullptr;
+    gsr::BatchState *d_bs = nullptr, *h_bs = nullptr;
+    gsr::BatchArgs *d_bargs = nullptr, *h_bargs = nullptr;
+    cudaGraphExec_t b_exec = nullptr;
+    int b_kt = 8, b_lanes = 16, b_graph_k = 0, b_graph_kt = 0, b_graph_lanes = 0;
+    int grid_b1 = 0, grid_b2 = 0;
     double *d_xp64 = nullptr, *d_q64 = nullptr;
     int grid_rows32 = 0, grid_rows2_32 = 0;
     double n_nonempty = 0.0;
@@ -153,6 +182,20 @@ cudaError_t launch_grad_global(const gsr_handle_t *h, const double *r, const dou
 cudaError_t build_cg64_graph(gsr_handle_t *h);
 cudaError_t run_cg64(gsr_handle_t *h, cudaStream_t st, int max_iter);
 cudaError_t launch_f32_plane(const gsr_handle_t *h, int k, cudaStream_t st);
+// batched (gsr_batched.cu)
+cudaError_t build_batched_graph(gsr_handle_t *h, int k);
+cudaError_t run_batched_inner(gsr_handle_t *h, int k, int max_inner, cudaStream_t st);
+cudaError_t launch_b_update_x(const gsr_handle_t *h, double *X, int k, cudaStream_t st);
+cudaError_t launch_b_norms(const gsr_handle_t *h, const double *C, const double *R, int k,
+                           double *out, cudaStream_t st);
+cudaError_t launch_b_products(const gsr_handle_t *h, int k, const float *X, float *Q, const float *Y,
+                              double *T, cudaStream_t st);
+cudaError_t launch_b_layout(const gsr_handle_t *h, int to_rm, const double *src, void *dst,
+                            int dst_f32, int64_t rows, int k, cudaStream_t st);
+int batched_grid_rows(const gsr_handle_t *h);
+cudaError_t launch_gather_instr32(const gsr_handle_t *h, const uint32_t *code, float *out,
+                                  cudaStream_t st);
+int batched_grid_stars(const gsr_handle_t *h);
 cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out,
                           int mode, cudaStream_t st);
 cudaError_t launch_validate(const gsr_handle_t *h, cudaStream_t st);

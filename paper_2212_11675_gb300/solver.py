@@ -187,6 +187,41 @@ class Solver:
                                      ctypes.byref(res), _stream(stream)), "gsr_lsq_backward")
         return gb, gg, res.as_dict()
 
+    def set_batch_tiling(self, kt, lanes):
+        """Column tile (1, 2, 4, 8) and lanes per star (8, 16, 32) of the batched kernels."""
+        check(lib().gsr_set_batch_tiling(self._h, int(kt), int(lanes)), "gsr_set_batch_tiling")
+
+    def batched_products(self, X, Y, stream=None):
+        """(A32 X, A32^T Y) for X (k, n) and Y (k, m) CUDA tensors (rows are columns)."""
+        torch = _torch()
+        k = X.shape[0]
+        if X.shape != (k, self.n) or Y.shape != (k, self.m):
+            raise ValueError("X must be (k, n) and Y (k, m)")
+        Q = torch.empty((k, self.m), dtype=torch.float64, device=X.device)
+        T = torch.empty((k, self.n), dtype=torch.float64, device=X.device)
+        check(lib().gsr_batched_products(self._h, k, _ptr(X)[0], _ptr(Y)[0], _ptr(Q)[0], _ptr(T)[0],
+                                         _stream(stream)), "gsr_batched_products")
+        return Q, T
+
+    def batched_solve(self, B, max_outer=10, max_inner=100, inner_tol=1e-4, atol=1e-12,
+                      stream=None):
+        """Mixed-precision least squares for k right-hand sides B (k, m); returns
+        (X (k, n), list of k result dicts)."""
+        k = B.shape[0]
+        if B.shape != (k, self.m):
+            raise ValueError("B must be (k, m)")
+        if isinstance(B, np.ndarray):
+            B = np.ascontiguousarray(B, dtype=np.float64)
+            X = np.empty((k, self.n))
+        else:
+            B = B.contiguous()
+            X = _torch().empty((k, self.n), dtype=B.dtype, device=B.device)
+        res = (MixedResult * k)()
+        check(lib().gsr_batched_solve(self._h, k, _ptr(B)[0], int(max_outer), int(max_inner),
+                                      float(inner_tol), float(atol), _ptr(X)[0], res,
+                                      _stream(stream)), "gsr_batched_solve")
+        return X, [r.as_dict() for r in res]
+
     def precondition(self, p, stream=None):
         """p = 1/||A(:,j)|| (1 for an empty column); returns p."""
         _check_vec(p, self.n, "p")
