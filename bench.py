@@ -210,6 +210,67 @@ def time_to_solution(sys_, b, torch, stream, target=1e-9, reps=3):
     return res
 
 
+def batched_vs_sequential(sys_, seed, torch, stream, ks=(8, 32), target=1e-9):
+    """Time for the batched k-RHS solve to bring every column within `target`
+    of its FP64 least-squares solution, against k sequential FP64 PC-LSQR
+    solves with the tolerance that reaches the same accuracy."""
+    from paper_2212_11675_gb300 import _lib, autotune
+    from paper_2212_11675_gb300.solver import Solver
+    out = {"target_rel_err": target}
+    with Solver(sys_, conlim=0.0, precision=_lib.GSR_PREC_MIXED) as s:
+        xt = torch.tensor(gen.x_true(sys_, seed), device="cuda")
+        ax = torch.zeros(sys_.m, dtype=torch.float64, device="cuda")
+        s.aprod1(xt, ax, stream=stream)
+        for k in ks:
+            B = torch.stack([ax + torch.tensor(gen.noise(sys_, seed + 1000 * (j + 1)), device="cuda")
+                             for j in range(k)])
+            refs = [s.lsqr_solve(B[j], 20000, 1e-15, 1e-15, stream=stream, want_se=False)[0]
+                    for j in range(k)]
+            kt, lanes, tune = autotune.tune(s, k)
+            # sequential FP64: the loosest tolerance meeting the target on every column
+            seq = None
+            for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                xs = [s.lsqr_solve(B[j], 20000, tol, tol, stream=stream, want_se=False)[0]
+                      for j in range(k)]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                err = max(float(torch.linalg.norm(xs[j] - refs[j]) / torch.linalg.norm(refs[j]))
+                          for j in range(k))
+                if err <= target:
+                    seq = {"ms": e0.elapsed_time(e1), "atol": tol, "max_rel_err": err}
+                    break
+            bat = None
+            for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
+                for itol in (1e-3, 1e-4):
+                    s.batched_solve(B, max_outer=30, max_inner=500, inner_tol=itol, atol=tol,
+                                    stream=stream)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    X, res = s.batched_solve(B, max_outer=30, max_inner=500, inner_tol=itol,
+                                             atol=tol, stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    err = max(float(torch.linalg.norm(X[j] - refs[j]) / torch.linalg.norm(refs[j]))
+                              for j in range(k))
+                    ms = e0.elapsed_time(e1)
+                    if err <= target and (bat is None or ms < bat["ms"]):
+                        bat = {"ms": ms, "atol": tol, "inner_tol": itol, "max_rel_err": err,
+                               "outer": max(r["outer"] for r in res),
+                               "inner": max(r["inner"] for r in res)}
+                if bat is not None:
+                    break
+            out["k%d" % k] = {"sequential_fp64": seq, "batched": bat,
+                              "tiling": {"kt": kt, "lanes": lanes},
+                              "speedup": (seq["ms"] / bat["ms"]) if (seq and bat) else None}
+    return out
+
+
 def cpu_baseline(sys_, seed, seconds):
     """The oracle timed on a bounded sample: LSQR iterations of the same system."""
     import oracle
@@ -244,6 +305,8 @@ def main():
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision vs FP64 time-to-solution comparison")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched k-RHS vs sequential FP64 comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -362,6 +425,9 @@ def main():
     mixed = None
     if not args.no_mixed and rank == 0:
         mixed = time_to_solution(sys_, b, torch, stream)
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = batched_vs_sequential(sys_, seed, torch, stream)
 
     # per solve: 12 prologue launches (preconditioner 5, init 7), 6 per LSQR
     # iteration (aprod 1, aprod 2 as 3 kernels, 2 vector passes), 1 epilogue
@@ -378,6 +444,8 @@ def main():
             "gpu_launches": launches_per_step * args.steps}
     if mixed is not None:
         line["mixed_vs_fp64"] = mixed
+    if batched is not None:
+        line["batched_vs_sequential_fp64"] = batched
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sys_, seed, args.cpu_seconds)
     if rank == 0:

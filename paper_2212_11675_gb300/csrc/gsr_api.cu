@@ -138,6 +138,7 @@ static void release(gsr_handle_t *h)
                    h->d_xp64, h->d_q64, h->d_biseg, h->d_birow, h->d_bival, h->d_bX32, h->d_bQ32,
                    h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT, h->d_bS, h->d_bXcm, h->d_bRcm,
                    h->d_bCcm, h->d_bB, h->d_bnorms, h->d_bpartial, h->d_bcounter, h->d_bs,
+                   h->d_bipart,
                    h->d_bargs};
     for (void *p : dev)
         if (p)
@@ -826,6 +827,7 @@ static int ensure_batched(gsr_handle_t *h, int k)
     }
     if (!h->d_bS) {
         TRY(dalloc(h, &h->d_bS, A.nseg * kNAtt * 8));
+        TRY(dalloc(h, &h->d_bipart, A.I * 4 * 8));
         TRY(dalloc(h, &h->d_bpartial, (int64_t)8 * kMaxPartials));
         TRY(dalloc(h, &h->d_bcounter, 1));
         TRY(dalloc(h, &h->d_bs, 1));

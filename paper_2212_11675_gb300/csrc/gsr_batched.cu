@@ -26,6 +26,8 @@
 
 namespace gsr {
 
+constexpr int kInstrSplit = 4;  // warps per instrument in the batched instrumental pass
+
 __device__ __forceinline__ uint32_t instr_b(const uint4 &rc, int j)
 {
     const uint32_t w = (j < 2) ? rc.y : ((j < 4) ? rc.z : rc.w);
@@ -63,7 +65,7 @@ __device__ __forceinline__ bool grid_reduce_cols(double (&v)[KT], double *partia
 // |Q[:, c]|^2 and alpha_c = gamma_c / |Q[:, c]|^2 (0 for a finished column)
 // ---------------------------------------------------------------------------
 template <int KT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ldk, int c0,
            BatchState *bs, double *partial, unsigned *counter)
 {
@@ -294,19 +296,39 @@ __global__ void k_b_att_combine(SysView A, const double *__restrict__ S, double 
 template <int KT>
 __global__ void __launch_bounds__(kThreads)
 k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restrict__ irow,
-          const float *__restrict__ ival, const float *__restrict__ Y, double *__restrict__ T,
+          const float *__restrict__ ival, const float *__restrict__ Y, double *__restrict__ part,
           int ldk, int c0)
 {
+    // warp w takes chunk (w % kInstrSplit) of instrument w / kInstrSplit; two
+    // entries per lane are in flight to hide the dependent row -> Y gathers
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t f = warp; f < A.I; f += nwarps) {
-        const uint32_t e0 = iseg[f], e1 = iseg[f + 1];
+    for (int64_t wi = warp; wi < A.I * kInstrSplit; wi += nwarps) {
+        const int64_t f = wi / kInstrSplit;
+        const int q = (int)(wi - f * kInstrSplit);
+        const uint32_t s0 = iseg[f], s1 = iseg[f + 1];
+        const uint32_t len = s1 - s0;
+        const uint32_t e0 = s0 + (uint32_t)(((uint64_t)len * q) / kInstrSplit);
+        const uint32_t e1 = s0 + (uint32_t)(((uint64_t)len * (q + 1)) / kInstrSplit);
         float h[KT], l[KT];
 #pragma unroll
         for (int c = 0; c < KT; c++)
             h[c] = l[c] = 0.f;
-        for (uint32_t e = e0 + lane; e < e1; e += 32) {
+        uint32_t e = e0 + lane;
+        for (; e + 32 < e1; e += 64) {
+            const uint32_t ra = __ldcs(irow + e), rb = __ldcs(irow + e + 32);
+            const float va = __ldcs(ival + e), vb = __ldcs(ival + e + 32);
+            float ya[KT], yb[KT];
+            load_cols<KT>(Y + (int64_t)ra * ldk + c0, ya);
+            load_cols<KT>(Y + (int64_t)rb * ldk + c0, yb);
+#pragma unroll
+            for (int c = 0; c < KT; c++) {
+                df_acc(h[c], l[c], __fmul_rn(va, ya[c]));
+                df_acc(h[c], l[c], __fmul_rn(vb, yb[c]));
+            }
+        }
+        if (e < e1) {
             float yv[KT];
             load_cols<KT>(Y + (int64_t)__ldcs(irow + e) * ldk + c0, yv);
             const float v = __ldcs(ival + e);
@@ -318,8 +340,26 @@ k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restri
         for (int c = 0; c < KT; c++) {
             const double t = warp_sum(df_to_d(h[c], l[c]));
             if (lane == 0)
-                T[(A.ins0 + f) * ldk + c0 + c] = t;
+                part[(f * kInstrSplit + q) * KT + c] = t;
         }
+    }
+}
+
+// instrumental rows of T from the per-chunk partials (fixed order)
+template <int KT>
+__global__ void k_b_instr_combine(SysView A, const double *__restrict__ part, double *__restrict__ T,
+                                  int ldk, int c0)
+{
+    const int64_t total = A.I * KT;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = i / KT;
+        const int c = (int)(i - f * KT);
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kInstrSplit; q++)
+            t += part[(f * kInstrSplit + q) * KT + c];
+        T[(A.ins0 + f) * ldk + c0 + c] = t;
     }
 }
 
@@ -556,15 +596,21 @@ template <int KT>
 static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, int ldk, int c0,
                             cudaStream_t st)
 {
-    switch (h->b_lanes) {
-    case 8: k_b_stars<KT, 8><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, c0); break;
-    case 32: k_b_stars<KT, 32><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, c0); break;
-    default: k_b_stars<KT, 16><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, c0); break;
+    // the star and attitude passes keep at most 4 columns per lane (register
+    // pressure); wider tiles are split
+    constexpr int KS = (KT > 4) ? 4 : KT;
+    for (int cs = c0; cs < c0 + KT; cs += KS) {
+        switch (h->b_lanes) {
+        case 8: k_b_stars<KS, 8><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
+        case 32: k_b_stars<KS, 32><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
+        default: k_b_stars<KS, 16><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
+        }
+        k_b_att<KS><<<h->grid_att, kThreads, 0, st>>>(h->sys, Y, h->d_bS, ldk, cs);
+        k_b_att_combine<KS><<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_bS, T, ldk, cs);
     }
-    k_b_att<KT><<<h->grid_att, kThreads, 0, st>>>(h->sys, Y, h->d_bS, ldk, c0);
-    k_b_att_combine<KT><<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_bS, T, ldk, c0);
-    k_b_instr<KT><<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_biseg, h->d_birow, h->d_bival, Y, T,
-                                                  ldk, c0);
+    k_b_instr<KT><<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_biseg, h->d_birow, h->d_bival, Y,
+                                                  h->d_bipart, ldk, c0);
+    k_b_instr_combine<KT><<<h->nsm * 2, kThreads, 0, st>>>(h->sys, h->d_bipart, T, ldk, c0);
     return cudaGetLastError();
 }
 

@@ -139,6 +139,7 @@ struct gsr_handle_t {
     float *d_bX32 = nullptr, *d_bQ32 = nullptr;
     double *d_bC = nullptr, *d_bS_ = nullptr, *d_bD = nullptr, *d_bZ = nullptr, *d_bT = nullptr;
     double *d_bS = nullptr;                           // attitude sums of one column tile
+    double *d_bipart = nullptr;                       // [I][4][8] instrumental partials
     double *d_bXcm = nullptr, *d_bRcm = nullptr, *d_bCcm = nullptr, *d_bB = nullptr;
     double *d_bnorms = nullptr, *h_bnorms = nullptr;
     double *d_bpartial = nullptr;
