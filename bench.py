@@ -157,13 +157,12 @@ def time_kernel(fn, stream, reps, torch):
     return e0.elapsed_time(e1) / reps * 1e-3
 
 
-def time_to_solution(sys_, b, torch, stream, target=1e-9, reps=3):
+def time_to_solution(s, b, torch, stream, target=1e-9, reps=3):
     """Time for the FP64 PC-LSQR and for the mixed-precision solve to reach a
     solution within `target` (relative) of the FP64 least-squares solution,
-    on the same GPU.  Each form is run with a ladder of tolerances; the
-    fastest setting that meets the target is reported."""
-    from paper_2212_11675_gb300 import _lib
-    from paper_2212_11675_gb300.solver import Solver
+    on the same GPU and the same mixed-precision solver `s` (which holds both
+    the FP64 and the binary32 matrix).  Each form is run with a ladder of
+    tolerances; the fastest setting that meets the target is reported."""
 
     def timed(fn):
         best = None
@@ -181,94 +180,141 @@ def time_to_solution(sys_, b, torch, stream, target=1e-9, reps=3):
         return best, out
 
     res = {"target_rel_err": target}
-    with Solver(sys_, conlim=0.0, precision=_lib.GSR_PREC_MIXED) as s:
-        xr, _, rr = s.lsqr_solve(b, 20000, 1e-15, 1e-15, stream=stream, want_se=False)
-        nref = float(torch.linalg.norm(xr))
-        res["reference"] = {"itn": rr["itn"], "istop": rr["istop"]}
-        best = None
-        for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13, 1e-14):
-            ms, out = timed(lambda: s.lsqr_solve(b, 20000, tol, tol, stream=stream, want_se=False))
+    xr, _, rr = s.lsqr_solve(b, 20000, 1e-15, 1e-15, stream=stream, want_se=False)
+    nref = float(torch.linalg.norm(xr))
+    res["reference"] = {"itn": rr["itn"], "istop": rr["istop"]}
+    best = None
+    for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13, 1e-14):
+        ms, out = timed(lambda: s.lsqr_solve(b, 20000, tol, tol, stream=stream, want_se=False))
+        err = float(torch.linalg.norm(out[0] - xr)) / nref
+        if err <= target:
+            best = {"ms": ms, "itn": out[2]["itn"], "atol": tol, "rel_err": err}
+            break
+    res["fp64"] = best
+    bestm = None
+    for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
+        for itol in (1e-2, 1e-3, 1e-4):
+            ms, out = timed(lambda: s.mixed_solve(b, max_outer=30, max_inner=500,
+                                                  inner_tol=itol, atol=tol, stream=stream))
             err = float(torch.linalg.norm(out[0] - xr)) / nref
-            if err <= target:
-                best = {"ms": ms, "itn": out[2]["itn"], "atol": tol, "rel_err": err}
-                break
-        res["fp64"] = best
-        bestm = None
-        for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
-            for itol in (1e-2, 1e-3, 1e-4):
-                ms, out = timed(lambda: s.mixed_solve(b, max_outer=30, max_inner=500,
-                                                      inner_tol=itol, atol=tol, stream=stream))
-                err = float(torch.linalg.norm(out[0] - xr)) / nref
-                if err <= target and (bestm is None or ms < bestm["ms"]):
-                    bestm = {"ms": ms, "outer": out[1]["outer"], "inner": out[1]["inner"],
-                             "atol": tol, "inner_tol": itol, "rel_err": err}
-            if bestm is not None:
-                break
-        res["mixed"] = bestm
-        if best and bestm:
-            res["speedup"] = best["ms"] / bestm["ms"]
+            if err <= target and (bestm is None or ms < bestm["ms"]):
+                bestm = {"ms": ms, "outer": out[1]["outer"], "inner": out[1]["inner"],
+                         "atol": tol, "inner_tol": itol, "rel_err": err}
+        if bestm is not None:
+            break
+    res["mixed"] = bestm
+    if best and bestm:
+        res["speedup"] = best["ms"] / bestm["ms"]
     return res
 
 
-def batched_vs_sequential(sys_, seed, torch, stream, ks=(8, 32), target=1e-9):
+def batched_vs_sequential(s, xt, noise, torch, stream, ks=(8, 32), target=1e-9):
     """Time for the batched k-RHS solve to bring every column within `target`
     of its FP64 least-squares solution, against k sequential FP64 PC-LSQR
-    solves with the tolerance that reaches the same accuracy."""
-    from paper_2212_11675_gb300 import _lib, autotune
-    from paper_2212_11675_gb300.solver import Solver
+    solves with the tolerance that reaches the same accuracy.  Right-hand side
+    j is A xt + noise(j) (independent noise streams)."""
+    from paper_2212_11675_gb300 import autotune
     out = {"target_rel_err": target}
-    with Solver(sys_, conlim=0.0, precision=_lib.GSR_PREC_MIXED) as s:
-        xt = torch.tensor(gen.x_true(sys_, seed), device="cuda")
-        ax = torch.zeros(sys_.m, dtype=torch.float64, device="cuda")
-        s.aprod1(xt, ax, stream=stream)
-        for k in ks:
-            B = torch.stack([ax + torch.tensor(gen.noise(sys_, seed + 1000 * (j + 1)), device="cuda")
-                             for j in range(k)])
-            refs = [s.lsqr_solve(B[j], 20000, 1e-15, 1e-15, stream=stream, want_se=False)[0]
-                    for j in range(k)]
-            kt, lanes, tune = autotune.tune(s, k)
-            # sequential FP64: the loosest tolerance meeting the target on every column
-            seq = None
-            for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
+    ax = torch.zeros(s.m, dtype=torch.float64, device="cuda")
+    s.aprod1(xt, ax, stream=stream)
+    torch.cuda.synchronize()
+    for k in ks:
+        torch.cuda.empty_cache()
+        B = torch.empty((k, s.m), dtype=torch.float64, device="cuda")
+        for j in range(k):
+            torch.add(ax, noise(j), out=B[j])
+        refs = [s.lsqr_solve(B[j], 20000, 1e-15, 1e-15, stream=stream, want_se=False)[0]
+                for j in range(k)]
+        kt, lanes, tune = autotune.tune(s, k)
+        # sequential FP64: the loosest tolerance meeting the target on every column
+        seq = None
+        for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            xs = [s.lsqr_solve(B[j], 20000, tol, tol, stream=stream, want_se=False)[0]
+                  for j in range(k)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            err = max(float(torch.linalg.norm(xs[j] - refs[j]) / torch.linalg.norm(refs[j]))
+                      for j in range(k))
+            if err <= target:
+                seq = {"ms": e0.elapsed_time(e1), "atol": tol, "max_rel_err": err}
+                break
+        bat = None
+        for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
+            for itol in (1e-3, 1e-4):
+                s.batched_solve(B, max_outer=30, max_inner=500, inner_tol=itol, atol=tol,
+                                stream=stream)
                 torch.cuda.synchronize()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                xs = [s.lsqr_solve(B[j], 20000, tol, tol, stream=stream, want_se=False)[0]
-                      for j in range(k)]
+                X, res = s.batched_solve(B, max_outer=30, max_inner=500, inner_tol=itol,
+                                         atol=tol, stream=stream)
                 e1.record(stream)
                 torch.cuda.synchronize()
-                err = max(float(torch.linalg.norm(xs[j] - refs[j]) / torch.linalg.norm(refs[j]))
+                err = max(float(torch.linalg.norm(X[j] - refs[j]) / torch.linalg.norm(refs[j]))
                           for j in range(k))
-                if err <= target:
-                    seq = {"ms": e0.elapsed_time(e1), "atol": tol, "max_rel_err": err}
-                    break
-            bat = None
-            for tol in (1e-9, 1e-10, 1e-11, 1e-12, 1e-13):
-                for itol in (1e-3, 1e-4):
-                    s.batched_solve(B, max_outer=30, max_inner=500, inner_tol=itol, atol=tol,
-                                    stream=stream)
-                    torch.cuda.synchronize()
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    X, res = s.batched_solve(B, max_outer=30, max_inner=500, inner_tol=itol,
-                                             atol=tol, stream=stream)
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    err = max(float(torch.linalg.norm(X[j] - refs[j]) / torch.linalg.norm(refs[j]))
-                              for j in range(k))
-                    ms = e0.elapsed_time(e1)
-                    if err <= target and (bat is None or ms < bat["ms"]):
-                        bat = {"ms": ms, "atol": tol, "inner_tol": itol, "max_rel_err": err,
-                               "outer": max(r["outer"] for r in res),
-                               "inner": max(r["inner"] for r in res)}
-                if bat is not None:
-                    break
-            out["k%d" % k] = {"sequential_fp64": seq, "batched": bat,
-                              "tiling": {"kt": kt, "lanes": lanes},
-                              "speedup": (seq["ms"] / bat["ms"]) if (seq and bat) else None}
+                ms = e0.elapsed_time(e1)
+                if err <= target and (bat is None or ms < bat["ms"]):
+                    bat = {"ms": ms, "atol": tol, "inner_tol": itol, "max_rel_err": err,
+                           "outer": max(r["outer"] for r in res),
+                           "inner": max(r["inner"] for r in res)}
+            if bat is not None:
+                break
+        out["k%d" % k] = {"sequential_fp64": seq, "batched": bat,
+                          "tiling": {"kt": kt, "lanes": lanes},
+                          "speedup": (seq["ms"] / bat["ms"]) if (seq and bat) else None}
     return out
+
+
+def tts_main(args):
+    """Time to solution on the large workloads, generated on the device: the
+    mixed-precision solve against FP64 PC-LSQR (1,000,000 stars), or the
+    batched k-RHS solve against k sequential FP64 solves (2,000,000 stars)."""
+    import torch
+    from paper_2212_11675_gb300 import _lib
+    from paper_2212_11675_gb300.solver import Solver
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    name = args.tts
+    seed = gen.SEEDS[name]
+    t0 = time.perf_counter()
+    sys_ = gen.make_t(name, dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    m, n = sys_.m, sys_.n
+    cfg = {"workload": name, "stars": sys_.n_stars, "m": m, "n": n, "n_dfa": sys_.n_dfa,
+           "n_instr": sys_.n_instr, "nnz": 24 * m, "generated_on": "device"}
+    t0 = time.perf_counter()
+    s = Solver(sys_, conlim=0.0, precision=_lib.GSR_PREC_MIXED)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    sys_.values = None
+    sys_.instr = sys_.attoff = None
+    torch.cuda.empty_cache()
+    xt = gen.x_true_t(sys_, seed, dev)
+    line = {"metric": "time to 1e-9 relative error vs the FP64 least-squares solution",
+            "unit": "ms", "higher_is_better": False, "dtype": "f32 storage, f64 accumulation",
+            "data": "synthetic", "config": cfg, "generate_s": t_gen, "create_s": t_create,
+            "device_bytes": s.device_bytes}
+    with Clocks(0) as clk:
+        if name == "large":
+            b = gen.noise_t(sys_, seed + 1, dev)
+            s.aprod1(xt, b, stream=stream)
+            torch.cuda.synchronize()
+            line["mixed_vs_fp64"] = time_to_solution(s, b, torch, stream, reps=2)
+        else:
+            line["batched_vs_sequential_fp64"] = batched_vs_sequential(
+                s, xt, lambda j: gen.noise_t(sys_, seed + 1000 * (j + 1), dev), torch, stream,
+                ks=tuple(args.tts_k))
+    line["clocks"] = clk.summary()
+    s.close()
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def cpu_baseline(sys_, seed, seconds):
@@ -307,11 +353,17 @@ def main():
                     help="skip the mixed-precision vs FP64 time-to-solution comparison")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched k-RHS vs sequential FP64 comparison")
+    ap.add_argument("--tts", choices=["large", "xlarge"], default=None,
+                    help="only the time-to-solution comparison on a large workload generated "
+                         "on the device (large: mixed vs FP64; xlarge: batched vs sequential)")
+    ap.add_argument("--tts-k", type=int, nargs="+", default=[8, 32])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.tts:
+        return tts_main(args)
 
     import torch
     ws, rank, local = dist_env()
@@ -423,11 +475,15 @@ def main():
                  "aprod_GB/s": (bytes_a1 + bytes_a2) / (t_a1 + t_a2) / 1e9})
 
     mixed = None
-    if not args.no_mixed and rank == 0:
-        mixed = time_to_solution(sys_, b, torch, stream)
     batched = None
-    if not args.no_batched and rank == 0:
-        batched = batched_vs_sequential(sys_, seed, torch, stream)
+    if (not args.no_mixed or not args.no_batched) and rank == 0:
+        with Solver(sys_, conlim=0.0, precision=_lib.GSR_PREC_MIXED) as sm:
+            if not args.no_mixed:
+                mixed = time_to_solution(sm, b, torch, stream)
+            if not args.no_batched:
+                batched = batched_vs_sequential(
+                    sm, xt, lambda j: torch.tensor(gen.noise(sys_, seed + 1000 * (j + 1)), device=dev),
+                    torch, stream)
 
     # per solve: 12 prologue launches (preconditioner 5, init 7), 6 per LSQR
     # iteration (aprod 1, aprod 2 as 3 kernels, 2 vector passes), 1 epilogue

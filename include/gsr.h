@@ -269,7 +269,11 @@ int gsr_lsq_backward(void *h, const double *b, const double *x, const double *gx
  * binary32 matrix (sparse times skinny-dense products over column tiles).
  * B[m*k] and X[n*k] are column-major (column c starts at c*m, c*n); out[k]
  * receives one result per column.  Handles created with GSR_PREC_MIXED
- * only.  Column tile and lanes per star: gsr_set_batch_tiling.
+ * only.  Column tile and lanes per star: gsr_set_batch_tiling.  A device B
+ * is read in place and must not change during the call; a host B is staged
+ * in a device block of m*k doubles that the handle keeps.  The FP64
+ * residuals are formed one column at a time in one m-vector, so the
+ * workspace beyond the binary32 m-by-k block is O(n k + m).
  */
 int gsr_batched_solve(void *h, int k, const double *B, int max_outer,
                       int max_inner, double inner_tol, double atol, double *X,

@@ -136,7 +136,7 @@ static void release(gsr_handle_t *h)
                    h->d_val32, h->d_tval32, h->d_x32, h->d_q32, h->d_c, h->d_s, h->d_d, h->d_t,
                    h->d_zc, h->d_xm, h->d_r, h->d_xneg, h->d_onorm, h->d_cg, h->d_cgargs,
                    h->d_xp64, h->d_q64, h->d_biseg, h->d_birow, h->d_bival, h->d_bX32, h->d_bQ32,
-                   h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT, h->d_bS, h->d_bXcm, h->d_bRcm,
+                   h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT, h->d_bS, h->d_bXcm,
                    h->d_bCcm, h->d_bB, h->d_bnorms, h->d_bpartial, h->d_bcounter, h->d_bs,
                    h->d_bipart,
                    h->d_bargs};
@@ -856,15 +856,13 @@ static int cm_buffers(gsr_handle_t *h, int k)
     const SysView &A = h->sys;
     if (h->d_bXcm && h->bkcm == k)
         return GSR_OK;
-    void *old[] = {h->d_bXcm, h->d_bRcm, h->d_bCcm, h->d_bB};
+    void *old[] = {h->d_bXcm, h->d_bCcm};
     for (void *p : old)
         if (p)
             cudaFree(p);
-    h->d_bXcm = h->d_bRcm = h->d_bCcm = h->d_bB = nullptr;
+    h->d_bXcm = h->d_bCcm = nullptr;
     TRY(dalloc(h, &h->d_bXcm, A.n * k));
-    TRY(dalloc(h, &h->d_bRcm, A.m * k));
     TRY(dalloc(h, &h->d_bCcm, A.n * k));
-    TRY(dalloc(h, &h->d_bB, A.m * k));
     h->bkcm = k;
     return GSR_OK;
 }
@@ -934,10 +932,22 @@ extern "C" int gsr_batched_solve(void *hv, int k, const double *B, int max_outer
     const SysView &A = h->sys;
     TRY(ensure_batched(h, k));
     TRY(cm_buffers(h, k));
-    CK(cudaMemcpyAsync(h->d_bB, B, A.m * k * sizeof(double), cudaMemcpyDefault, st));
+    // right-hand sides: the caller's device block in place, or a staged copy
+    const double *dB = B;
+    if (!on_device(B)) {
+        if (h->bkB < k) {
+            if (h->d_bB)
+                cudaFree(h->d_bB);
+            h->d_bB = nullptr;
+            h->bkB = 0;
+            TRY(dalloc(h, &h->d_bB, A.m * k));
+            h->bkB = k;
+        }
+        CK(cudaMemcpyAsync(h->d_bB, B, A.m * k * sizeof(double), cudaMemcpyHostToDevice, st));
+        dB = h->d_bB;
+    }
     CK(enqueue_precondition(h, h->d_p, st));
     CK(cudaMemsetAsync(h->d_bXcm, 0, A.n * k * sizeof(double), st));
-    CK(cudaMemcpyAsync(h->d_bRcm, h->d_bB, A.m * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
     h->h_bargs->max_inner = max_inner;
     h->h_bargs->tol = inner_tol;
     CK(cudaMemcpyAsync(h->d_bargs, h->h_bargs, sizeof(BatchArgs), cudaMemcpyHostToDevice, st));
@@ -946,14 +956,25 @@ extern "C" int gsr_batched_solve(void *hv, int k, const double *B, int max_outer
     for (int c = 0; c < k; c++)
         res[c].anorm = anorm;
     for (int it = 0;; it++) {
-        // FP64 normal residuals, one column at a time
+        // FP64 residual r_c = b_c - A x_c and normal residual c_c = A^T r_c,
+        // one column at a time through one m-vector
         CK(cudaMemsetAsync(h->d_bCcm, 0, A.n * k * sizeof(double), st));
-        for (int c = 0; c < k; c++)
-            CK(launch_aprod2(h, h->d_bRcm + (int64_t)c * A.m, h->d_bCcm + (int64_t)c * A.n,
-                             kA2Accumulate, st));
-        CK(launch_b_norms(h, h->d_bCcm, h->d_bRcm, k, h->d_bnorms, st));
+        for (int c = 0; c < k; c++) {
+            const double *bc = dB + (int64_t)c * A.m;
+            const double *r = bc;  // x = 0 on the first pass
+            if (it > 0) {
+                CK(cudaMemcpyAsync(h->d_r, bc, A.m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                CK(launch_neg(h, h->d_bXcm + (int64_t)c * A.n, h->d_xneg, A.n, st));
+                CK(launch_aprod1(h, h->d_xneg, h->d_r, 0, st));
+                r = h->d_r;
+            }
+            CK(launch_aprod2(h, r, h->d_bCcm + (int64_t)c * A.n, kA2Accumulate, st));
+            CK(launch_norms2(h, h->d_bCcm + (int64_t)c * A.n, r, h->d_bnorms + 2 * c, st));
+        }
         CK(cudaMemcpyAsync(h->h_bnorms, h->d_bnorms, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        if (it > 0 && h->h_bs->nonfinite)
+            return GSR_ERR_NONFINITE;
         int all = 1;
         for (int c = 0; c < k; c++) {
             res[c].arnorm = sqrt(h->h_bnorms[2 * c]);
@@ -971,15 +992,7 @@ extern "C" int gsr_batched_solve(void *hv, int k, const double *B, int max_outer
         CK(run_batched_inner(h, h->bk, max_inner, st));
         CK(launch_b_update_x(h, h->d_bXcm, k, st));
         CK(cudaMemcpyAsync(h->h_bs, h->d_bs, sizeof(BatchState), cudaMemcpyDeviceToHost, st));
-        // FP64 residuals r_c = b_c - A x_c
-        CK(cudaMemcpyAsync(h->d_bRcm, h->d_bB, A.m * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        for (int c = 0; c < k; c++) {
-            CK(launch_neg(h, h->d_bXcm + (int64_t)c * A.n, h->d_xneg, A.n, st));
-            CK(launch_aprod1(h, h->d_xneg, h->d_bRcm + (int64_t)c * A.m, 0, st));
-        }
         CK(cudaStreamSynchronize(st));
-        if (h->h_bs->nonfinite)
-            return GSR_ERR_NONFINITE;
         for (int c = 0; c < k; c++) {
             res[c].outer = it + 1;
             res[c].inner += h->h_bs->it[c];

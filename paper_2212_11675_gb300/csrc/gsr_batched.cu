@@ -557,29 +557,6 @@ __global__ void k_b_update_x(const double *__restrict__ p, const double *__restr
     }
 }
 
-// per-column |p o C_c|^2 and |R_c|^2 (column-major blocks), one block per
-// column pair entry; deterministic per-column tree sums
-__global__ void __launch_bounds__(kThreads)
-k_b_norms(const double *__restrict__ p, const double *__restrict__ C, const double *__restrict__ R,
-          int64_t n, int64_t m, double *out)
-{
-    const int c = blockIdx.x;  // one block per column
-    double acc[2] = {0.0, 0.0};
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const double v = p[j] * C[c * n + j];
-        acc[0] = fma(v, v, acc[0]);
-    }
-    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-        const double v = R[c * m + i];
-        acc[1] = fma(v, v, acc[1]);
-    }
-    block_sum<2>(acc);
-    if (threadIdx.x == 0) {
-        out[2 * c] = acc[0];
-        out[2 * c + 1] = acc[1];
-    }
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -757,13 +734,6 @@ cudaError_t run_batched_inner(gsr_handle_t *h, int k, int max_inner, cudaStream_
 cudaError_t launch_b_update_x(const gsr_handle_t *h, double *X, int k, cudaStream_t st)
 {
     k_b_update_x<<<h->nsm * 8, kThreads, 0, st>>>(h->d_p, h->d_bZ, X, h->sys.n, k, h->bk);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_b_norms(const gsr_handle_t *h, const double *C, const double *R, int k,
-                           double *out, cudaStream_t st)
-{
-    k_b_norms<<<k, kThreads, 0, st>>>(h->d_p, C, R, h->sys.n, h->sys.m, out);
     return cudaGetLastError();
 }
 

@@ -136,11 +136,12 @@ struct gsr_handle_t {
     float *d_bival = nullptr;
     int bk = 0;                                       // columns the buffers hold
     int bkcm = 0;                                     // columns of the column-major buffers
+    int bkB = 0;                                      // columns of the staged right-hand sides
     float *d_bX32 = nullptr, *d_bQ32 = nullptr;
     double *d_bC = nullptr, *d_bS_ = nullptr, *d_bD = nullptr, *d_bZ = nullptr, *d_bT = nullptr;
     double *d_bS = nullptr;                           // attitude sums of one column tile
     double *d_bipart = nullptr;                       // [I][4][8] instrumental partials
-    double *d_bXcm = nullptr, *d_bRcm = nullptr, *d_bCcm = nullptr, *d_bB = nullptr;
+    double *d_bXcm = nullptr, *d_bCcm = nullptr, *d_bB = nullptr;
     double *d_bnorms = nullptr, *h_bnorms = nullptr;
     double *d_bpartial = nullptr;
     unsigned *d_bcounter = nullptr;
@@ -187,8 +188,6 @@ cudaError_t launch_f32_plane(const gsr_handle_t *h, int k, cudaStream_t st);
 cudaError_t build_batched_graph(gsr_handle_t *h, int k);
 cudaError_t run_batched_inner(gsr_handle_t *h, int k, int max_inner, cudaStream_t st);
 cudaError_t launch_b_update_x(const gsr_handle_t *h, double *X, int k, cudaStream_t st);
-cudaError_t launch_b_norms(const gsr_handle_t *h, const double *C, const double *R, int k,
-                           double *out, cudaStream_t st);
 cudaError_t launch_b_products(const gsr_handle_t *h, int k, const float *X, float *Q, const float *Y,
                               double *T, cudaStream_t st);
 cudaError_t launch_b_layout(const gsr_handle_t *h, int to_rm, const double *src, void *dst,
@@ -217,6 +216,9 @@ cudaError_t launch_aprod2_f32_api(const gsr_handle_t *h, const double *y, double
 cudaError_t build_cg_graph(gsr_handle_t *h);
 cudaError_t run_cg(gsr_handle_t *h, cudaStream_t st, int max_inner);
 cudaError_t launch_outer_norms(const gsr_handle_t *h, const double *r, cudaStream_t st);
+// out2 = (||p o c||^2, ||r||^2) for one n-vector c and one m-vector r
+cudaError_t launch_norms2(const gsr_handle_t *h, const double *c, const double *r, double *out2,
+                          cudaStream_t st);
 cudaError_t launch_neg(const gsr_handle_t *h, const double *a, double *b, int64_t n, cudaStream_t st);
 cudaError_t launch_count_pos(const gsr_handle_t *h, const double *a, double *out, cudaStream_t st);
 cudaError_t launch_to_f32(const gsr_handle_t *h, const double *a, float *b, int64_t n, cudaStream_t st);

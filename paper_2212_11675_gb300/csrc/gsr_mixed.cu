@@ -585,6 +585,15 @@ cudaError_t launch_outer_norms(const gsr_handle_t *h, const double *r, cudaStrea
     return cudaGetLastError();
 }
 
+cudaError_t launch_norms2(const gsr_handle_t *h, const double *c, const double *r, double *out2,
+                          cudaStream_t st)
+{
+    k_outer_norms<<<h->grid_vec, kThreads, 0, st>>>(h->d_p, c, h->sys.n, r, h->sys.m, out2,
+                                                     h->d_partial + kRedU * kPartialsPerKind,
+                                                     h->d_counter + kRedU);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_neg(const gsr_handle_t *h, const double *a, double *b, int64_t n, cudaStream_t st)
 {
     k_neg<<<h->grid_vec, kThreads, 0, st>>>(a, b, n);

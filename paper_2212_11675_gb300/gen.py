@@ -197,3 +197,116 @@ def noise(sys: GaiaSystem, seed: int, sigma: float = 1e-3) -> np.ndarray:
 
 def make(name: str) -> GaiaSystem:
     return generate(SHAPES[name], SEEDS[name])
+
+
+# ---------------------------------------------------------------------------
+# The same streams and recipe drawn with PyTorch on any device, for workloads
+# too large to generate on the host in reasonable time.  Integer draws,
+# uniforms, counts, orders, offsets and instrument indices are bit-identical
+# to the NumPy functions above; normals agree to the last bits of the
+# platform's log1p/cos.  uint64 arithmetic is carried in int64 tensors
+# (two's-complement wrap-around), with right shifts masked to be logical.
+
+def _s64(v: int) -> int:
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+_T_GOLDEN, _T_M1, _T_M2 = _s64(int(GOLDEN)), _s64(int(_M1)), _s64(int(_M2))
+
+
+def _t_shr(z, k: int):
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def _t_mix64(z):
+    z = (z ^ _t_shr(z, 30)) * _T_M1
+    z = (z ^ _t_shr(z, 27)) * _T_M2
+    return z ^ _t_shr(z, 31)
+
+
+def u64_t(seed: int, tag: int, start: int, count: int, device):
+    """u64() as an int64 tensor holding the same 64 bits."""
+    import torch
+    key = _s64(int(stream_key(seed, tag)))
+    ctr = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    return _t_mix64(ctr * _T_GOLDEN + key)
+
+
+def uniform_t(seed: int, tag: int, start: int, count: int, device):
+    import torch
+    return _t_shr(u64_t(seed, tag, start, count, device), 11).to(torch.float64) * (2.0 ** -53)
+
+
+def normal_t(seed: int, tag: int, start: int, count: int, device, chunk: int = 1 << 24):
+    import torch
+    out = torch.empty(count, dtype=torch.float64, device=device)
+    for c0 in range(0, count, chunk):
+        c = min(chunk, count - c0)
+        uu = uniform_t(seed, tag, 2 * (start + c0), 2 * c, device)
+        u1, u2 = uu[0::2], uu[1::2]
+        out[c0:c0 + c] = torch.sqrt(-2.0 * torch.log1p(-u1)) * torch.cos(2.0 * math.pi * u2)
+        del uu, u1, u2
+    return out
+
+
+def generate_t(shape: Shape, seed: int, device, with_values: bool = True) -> GaiaSystem:
+    """generate() with PyTorch tensors on `device` (same recipe, same streams)."""
+    import torch
+    S, D, I = shape.n_stars, shape.n_dfa, shape.n_instr
+    if D < N_PARAXIS:
+        raise ValueError("need at least 4 attitude knots per axis")
+    if I < N_INSTR:
+        raise ValueError("need at least 6 instrument unknowns")
+    i64 = torch.int64
+    if shape.obs_per_star is not None:
+        cnt = torch.full((S,), shape.obs_per_star, dtype=i64, device=device)
+    else:
+        lam, clip = shape.lam, shape.clip
+        kmax = int(lam + 40 * math.sqrt(lam) + 40)
+        pmf = np.empty(kmax + 1)
+        pmf[0] = math.exp(-lam)
+        for k in range(1, kmax + 1):
+            pmf[k] = pmf[k - 1] * lam / k
+        cdf = torch.tensor(np.cumsum(pmf), device=device)
+        u = uniform_t(seed, TAG_COUNT, 0, S, device)
+        cnt = torch.searchsorted(cdf, u, right=True).clamp(max=kmax).clamp(min=clip).to(i64)
+    star_ptr = torch.zeros(S + 1, dtype=i64, device=device)
+    torch.cumsum(cnt, 0, out=star_ptr[1:])
+    m = int(star_ptr[-1])
+    if m >= 2 ** 32:
+        raise ValueError("too many rows for 32-bit row indices")
+    t = uniform_t(seed, TAG_TIME, 0, m, device)
+    star_of_row = torch.repeat_interleave(torch.arange(S, dtype=i64, device=device), cnt)
+    order = torch.argsort(t, stable=True)                               # time minor
+    order = order[torch.argsort(star_of_row[order], stable=True)]      # star major
+    del star_of_row
+    t = t[order]
+    del order
+    attoff = torch.floor(t * (D - 3)).to(i64).clamp(max=D - 4).to(torch.uint32)
+    del t
+    instr = torch.empty((m, N_INSTR), dtype=i64, device=device)
+    u = uniform_t(seed, TAG_INSTR, 0, N_INSTR * m, device).view(m, N_INSTR)
+    for j in range(N_INSTR):
+        top = I - N_INSTR + j
+        tj = (u[:, j] * (top + 1)).to(i64).clamp(max=top)
+        if j:
+            taken = (instr[:, :j] == tj[:, None]).any(dim=1)
+            tj = torch.where(taken, torch.full_like(tj, top), tj)
+        instr[:, j] = tj
+    del u
+    instr = instr.to(torch.uint16)
+    values = normal_t(seed, TAG_VALUE, 0, N_PAR * m, device).view(m, N_PAR) if with_values else None
+    return GaiaSystem(S, D, I, star_ptr.to(torch.uint32), attoff, instr, values)
+
+
+def make_t(name: str, device) -> GaiaSystem:
+    return generate_t(SHAPES[name], SEEDS[name], device)
+
+
+def x_true_t(sys: GaiaSystem, seed: int, device):
+    return normal_t(seed, TAG_XTRUE, 0, sys.n, device)
+
+
+def noise_t(sys: GaiaSystem, seed: int, device, sigma: float = 1e-3):
+    return sigma * normal_t(seed, TAG_NOISE, 0, sys.m, device)
