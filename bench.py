@@ -317,6 +317,45 @@ def tts_main(args):
     return 0
 
 
+def profile_main(args):
+    """A short run of the mixed-precision or batched path on the medium
+    workload with host-launched kernels (eager), for ncu: ncu does not profile
+    kernel nodes inside graphs with conditional nodes."""
+    import torch
+    from paper_2212_11675_gb300 import _lib
+    from paper_2212_11675_gb300.solver import Solver
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    sys_, seed = make_system(args.workload, 0)
+    out = {"profile": args.profile, "workload": args.workload}
+    with Solver(sys_, conlim=0.0, precision=_lib.GSR_PREC_MIXED, eager=True) as s:
+        xt = torch.tensor(gen.x_true(sys_, seed), device=dev)
+        b = torch.tensor(gen.noise(sys_, seed + 1), device=dev)
+        s.aprod1(xt, b, stream=stream)
+        torch.cuda.synchronize()
+        if args.profile == "mixed":
+            for _ in range(2):
+                _, r = s.mixed_solve(b, max_outer=1, max_inner=10, inner_tol=0.0, atol=0.0,
+                                     stream=stream)
+            out["result"] = r
+        else:
+            k = args.profile_k
+            g = torch.Generator(device=dev).manual_seed(1)
+            X = torch.randn((k, s.n), dtype=torch.float64, device=dev, generator=g)
+            Y = torch.randn((k, s.m), dtype=torch.float64, device=dev, generator=g)
+            s.set_batch_tiling(args.profile_kt, args.profile_lanes)
+            for _ in range(2):
+                s.batched_products(X, Y, stream=stream)
+            B = b.repeat(k, 1)
+            _, r = s.batched_solve(B, max_outer=1, max_inner=10, inner_tol=0.0, atol=0.0,
+                                   stream=stream)
+            out["result"] = r[0]
+        torch.cuda.synchronize()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def cpu_baseline(sys_, seed, seconds):
     """The oracle timed on a bounded sample: LSQR iterations of the same system."""
     import oracle
@@ -357,6 +396,11 @@ def main():
                     help="only the time-to-solution comparison on a large workload generated "
                          "on the device (large: mixed vs FP64; xlarge: batched vs sequential)")
     ap.add_argument("--tts-k", type=int, nargs="+", default=[8, 32])
+    ap.add_argument("--profile", choices=["mixed", "batched"], default=None,
+                    help="a short host-launched run of the mixed or batched path (for ncu)")
+    ap.add_argument("--profile-k", type=int, default=8)
+    ap.add_argument("--profile-kt", type=int, default=8)
+    ap.add_argument("--profile-lanes", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -364,6 +408,8 @@ def main():
         return run_reference(args)
     if args.tts:
         return tts_main(args)
+    if args.profile:
+        return profile_main(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -53,9 +53,11 @@ extern "C" {
 #define GSR_ERR_UNSUPPORTED (-7) /* configuration not supported by this build */
 
 /* Accumulation of the instrumental columns in aprod 2. */
-#define GSR_INSTR_AUTO 0     /* shared memory per block when I <= 6144, else replicas */
-#define GSR_INSTR_SMEM 1     /* shared memory per block (needs I <= 6144) */
+#define GSR_INSTR_AUTO 0     /* GSR_INSTR_SORTED */
+#define GSR_INSTR_SMEM 1     /* shared memory per block (needs I <= 6144, else replicas) */
 #define GSR_INSTR_REPLICAS 2 /* one replica per SM in device memory, L2 reductions */
+#define GSR_INSTR_SORTED 3   /* instrument-sorted copy of the instrumental values:
+                                per-instrument segment sums, no atomics, deterministic */
 
 /* Storage and arithmetic of the matrix values. */
 #define GSR_PREC_FP64 0  /* IEEE double values, native FP64 arithmetic */
@@ -290,6 +292,20 @@ int gsr_batched_products(void *h, int k, const double *X, const double *Y,
 /* Column tile kt (1, 2, 4, 8) and lanes per star (8, 16, 32) of the batched
  * kernels; the next batched call rebuilds its graph.  Defaults 8 and 16. */
 int gsr_set_batch_tiling(void *h, int kt, int lanes);
+
+/*
+ * Schedule of the FP64 aprod 2 (Alg. 2) on the sorted instrumental path
+ * (GSR_INSTR_SORTED, the default).  fused = 1 (default): the star-group
+ * sums, the attitude segment sums and the instrumental segment sums run in
+ * one launch whose warps take units of all three kinds from one work queue,
+ * so the FP64-bound and the gather-bound parts share every SM.  fused = 0:
+ * three separate launches.  Only the schedule changes: the astrometric,
+ * attitude and instrumental sums keep their order; the global column's
+ * per-block grouping follows the schedule.  The handle's solve graphs are
+ * captured again.  Errors: GSR_ERR_ARG, GSR_ERR_UNSUPPORTED (another
+ * instrumental path), GSR_ERR_CUDA.
+ */
+int gsr_set_aprod2_fused(void *h, int fused);
 
 /* Text of the last CUDA failure seen by this host thread ("" if none). */
 const char *gsr_last_error(void);

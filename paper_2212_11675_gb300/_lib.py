@@ -23,14 +23,14 @@ GSR_ERR_UNSUPPORTED = -7
 
 GSR_PREC_FP64 = 0
 GSR_PREC_MIXED = 1
-GSR_INSTR_AUTO, GSR_INSTR_SMEM, GSR_INSTR_REPLICAS = 0, 1, 2
+GSR_INSTR_AUTO, GSR_INSTR_SMEM, GSR_INSTR_REPLICAS, GSR_INSTR_SORTED = 0, 1, 2, 3
 
 EXPORTS = (
     "gsr_config_default", "gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
     "gsr_precondition", "gsr_lsqr_solve", "gsr_last_error", "gsr_info", "gsr_strerror",
     "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32", "gsr_mixed_solve",
     "gsr_set_values", "gsr_normal_solve", "gsr_lsq_backward", "gsr_batched_solve",
-    "gsr_batched_products", "gsr_set_batch_tiling",
+    "gsr_batched_products", "gsr_set_batch_tiling", "gsr_set_aprod2_fused",
 )
 
 
@@ -121,6 +121,7 @@ def lib():
             L.gsr_batched_solve.argtypes = [P, I, P, I, I, D, D, P, ctypes.POINTER(MixedResult), P]
             L.gsr_batched_products.argtypes = [P, I, P, P, P, P, P]
             L.gsr_set_batch_tiling.argtypes = [P, I, I]
+            L.gsr_set_aprod2_fused.argtypes = [P, I]
             L.gsr_last_error.restype = ctypes.c_char_p
             L.gsr_strerror.argtypes = [I]
             L.gsr_strerror.restype = ctypes.c_char_p
@@ -130,7 +131,7 @@ def lib():
                          "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32",
                          "gsr_mixed_solve", "gsr_set_values", "gsr_normal_solve",
                          "gsr_lsq_backward", "gsr_batched_solve", "gsr_batched_products",
-                         "gsr_set_batch_tiling"):
+                         "gsr_set_batch_tiling", "gsr_set_aprod2_fused"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib

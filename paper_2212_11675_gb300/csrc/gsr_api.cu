@@ -15,6 +15,7 @@
 namespace gsr {
 cudaError_t enqueue_precondition(const gsr_handle_t *h, double *p, cudaStream_t st);
 int aprod2_grid(const gsr_handle_t *h);
+int aprod2_fused_grid(const gsr_handle_t *h);
 }  // namespace gsr
 
 using namespace gsr;
@@ -65,6 +66,13 @@ extern "C" void gsr_config_default(gsr_config *c)
     c->conlim = 1e8;
     c->lanes_per_star = 0;
     c->validate = 1;
+}
+
+// instrument index j (0..5) of a packed row record
+static inline uint32_t instr_of(const uint4 &r, int j)
+{
+    const uint32_t w = j < 2 ? r.y : (j < 4 ? r.z : r.w);
+    return (j & 1) ? (w >> 16) : (w & 0xffffu);
 }
 
 static bool on_device(const void *p)
@@ -135,7 +143,7 @@ static void release(gsr_handle_t *h)
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err,
                    h->d_val32, h->d_tval32, h->d_x32, h->d_q32, h->d_c, h->d_s, h->d_d, h->d_t,
                    h->d_zc, h->d_xm, h->d_r, h->d_xneg, h->d_onorm, h->d_cg, h->d_cgargs,
-                   h->d_xp64, h->d_q64, h->d_biseg, h->d_birow, h->d_bival, h->d_bX32, h->d_bQ32,
+                   h->d_xp64, h->d_q64, h->d_iseg, h->d_irow, h->d_ival32, h->d_ival, h->d_ipart, h->d_gpart, h->d_a2ctr, h->d_bX32, h->d_bQ32,
                    h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT, h->d_bS, h->d_bXcm,
                    h->d_bCcm, h->d_bB, h->d_bnorms, h->d_bpartial, h->d_bcounter, h->d_bs,
                    h->d_bipart,
@@ -155,62 +163,73 @@ static void release(gsr_handle_t *h)
 
 // binary32 copies of the value planes and of the offset-sorted attitude
 // values, the mixed-precision workspace and the inner CG graph
+// Instrument-sorted copy of the instrumental nonzeros: a stable counting
+// sort of the 6 m entries (row, slot) by instrument on the host, so the
+// entries of every instrument keep ascending row order and their sums a
+// fixed order; the FP64 values are then gathered on the device.
+static int build_instr_sorted(gsr_handle_t *h, cudaStream_t st)
+{
+    SysView &A = h->sys;
+    const int64_t m = A.m, I = A.I, E = kNInstr * m;
+    std::vector<uint4> rec((size_t)m);
+    CK(cudaMemcpy(rec.data(), h->d_rec, m * sizeof(uint4), cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> seg((size_t)I + 1, 0);
+    for (int64_t i = 0; i < m; i++)
+        for (int j = 0; j < kNInstr; j++)
+            seg[instr_of(rec[i], j) + 1]++;
+    for (int64_t f = 0; f < I; f++)
+        seg[f + 1] += seg[f];
+    std::vector<uint32_t> pos(seg.begin(), seg.end() - 1), irow((size_t)E), code((size_t)E);
+    for (int64_t i = 0; i < m; i++)
+        for (int j = 0; j < kNInstr; j++) {
+            const uint32_t p = pos[instr_of(rec[i], j)]++;
+            irow[p] = (uint32_t)i;
+            code[p] = (uint32_t)(kNInstr * i + j);
+        }
+    std::vector<uint4>().swap(rec);
+    TRY(dalloc(h, &h->d_iseg, I + 1));
+    TRY(dalloc(h, &h->d_irow, E));
+    TRY(dalloc(h, &h->d_ival, E));
+    CK(cudaMemcpy(h->d_iseg, seg.data(), (I + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_irow, irow.data(), E * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    uint32_t *d_code = nullptr;
+    if (cudaMalloc(&d_code, E * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return GSR_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpy(d_code, code.data(), E * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_gather_instr64(h, d_code, h->d_ival, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    cudaFree(d_code);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "instrument-sorted layout");
+    // chunks per instrument: about 64 warps' worth of units per SM
+    const int64_t want = ((int64_t)h->nsm * 64 + I - 1) / I;
+    h->isplit = (int)(want < 1 ? 1 : (want > 64 ? 64 : want));
+    TRY(dalloc(h, &h->d_ipart, (int64_t)h->isplit * I));
+    CK(cudaMemset(h->d_ipart, 0, (size_t)h->isplit * I * sizeof(double)));
+    const int64_t units_blocks = (I * h->isplit + kThreads / 32 - 1) / (kThreads / 32);
+    const int64_t cap = (int64_t)h->nsm * 16;
+    h->grid_ins = (int)(units_blocks < cap ? units_blocks : cap);
+    return GSR_OK;
+}
+
 static int create_mixed(gsr_handle_t *h, cudaStream_t st)
 {
     SysView &A = h->sys;
     const int64_t m = A.m, n = A.n, mp = A.mp;
     TRY(dalloc(h, &h->d_val32, kNPar * mp));
     TRY(dalloc(h, &h->d_tval32, (int64_t)kNAtt * mp));
+    TRY(dalloc(h, &h->d_ival32, kNInstr * m));
     TRY(dalloc(h, &h->d_x32, n));
     TRY(dalloc(h, &h->d_q32, m));
     CK(launch_to_f32(h, h->d_val, h->d_val32, kNPar * mp, st));
     CK(launch_to_f32(h, h->d_tval, h->d_tval32, kNAtt * mp, st));
     A.val32 = h->d_val32;
     A.tval32 = h->d_tval32;
-    // instrument-sorted copy of the whole matrix (batched solve): a stable
-    // counting sort of the 6 m instrumental entries by instrument
-    {
-        std::vector<uint4> rec((size_t)m);
-        CK(cudaMemcpy(rec.data(), h->d_rec, m * sizeof(uint4), cudaMemcpyDeviceToHost));
-        std::vector<uint16_t> ins_host((size_t)(kNInstr * m));
-        for (int64_t i = 0; i < m; i++) {
-            const uint32_t w[3] = {rec[i].y, rec[i].z, rec[i].w};
-            for (int j = 0; j < kNInstr; j++)
-                ins_host[kNInstr * i + j] = (uint16_t)((j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu));
-        }
-        std::vector<uint32_t> code((size_t)m * kNInstr);
-        const int64_t I = A.I;
-        std::vector<uint32_t> seg((size_t)I + 1, 0), irow((size_t)(kNInstr * m));
-        for (int64_t e = 0; e < kNInstr * m; e++)
-            seg[ins_host[e] + 1]++;
-        for (int64_t f = 0; f < I; f++)
-            seg[f + 1] += seg[f];
-        std::vector<uint32_t> pos(seg.begin(), seg.end() - 1);
-        for (int64_t e = 0; e < kNInstr * m; e++) {
-            const uint32_t p = pos[ins_host[e]]++;
-            irow[p] = (uint32_t)(e / kNInstr);
-            code[p] = (uint32_t)e;
-        }
-        TRY(dalloc(h, &h->d_biseg, I + 1));
-        TRY(dalloc(h, &h->d_birow, kNInstr * m));
-        TRY(dalloc(h, &h->d_bival, kNInstr * m));
-        CK(cudaMemcpy(h->d_biseg, seg.data(), (I + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(h->d_birow, irow.data(), kNInstr * m * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        uint32_t *d_code = nullptr;
-        if (cudaMalloc(&d_code, kNInstr * m * sizeof(uint32_t)) != cudaSuccess) {
-            cudaGetLastError();
-            return GSR_ERR_OOM;
-        }
-        cudaError_t e = cudaMemcpy(d_code, code.data(), kNInstr * m * sizeof(uint32_t),
-                                   cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = launch_gather_instr32(h, d_code, h->d_bival, st);
-        if (e == cudaSuccess)
-            e = cudaStreamSynchronize(st);
-        cudaFree(d_code);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "instrument-sorted layout");
-    }
+    CK(launch_to_f32(h, h->d_ival, h->d_ival32, kNInstr * m, st));
     // ||A diag(p)||_F^2 = number of nonempty columns (column sums of squares > 0)
     CK(cudaMemsetAsync(h->d_s, 0, n * sizeof(double), st));
     CK(launch_aprod2(h, nullptr, h->d_s, kA2Squares, st));
@@ -376,10 +395,15 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     CK(launch_tile_star(h, st));
     CK(cudaStreamSynchronize(st));
 
+    // instrumental part of aprod 2 and its layout
+    h->ipath = instr_path(h->cfg, I);
+    if (h->ipath == kIpSorted || h->cfg.precision == GSR_PREC_MIXED)
+        TRY(build_instr_sorted(h, st));
+
     // launch geometry
     // measured at the medium size: 8 lanes per star with shared-memory
-    // instrument sums, 32 with replicas
-    h->lanes = h->cfg.lanes_per_star ? h->cfg.lanes_per_star : (instr_in_smem(h) ? 8 : 32);
+    // instrument sums or the sorted pass, 32 with replicas
+    h->lanes = h->cfg.lanes_per_star ? h->cfg.lanes_per_star : (h->ipath == kIpReplicas ? 32 : 8);
     h->grid_rows = aprod1_grid(h);
     if (h->grid_rows <= 0)
         return cuda_fail(cudaGetLastError(), "aprod1 occupancy");
@@ -390,7 +414,7 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     if (gv > (int64_t)h->nsm * 2) gv = (int64_t)h->nsm * 2;
     if (gv > kMaxPartials) gv = kMaxPartials;
     h->grid_vec = (int)(gv < 1 ? 1 : gv);
-    if (!instr_in_smem(h) || h->cfg.precision == GSR_PREC_MIXED) {
+    if (h->ipath == kIpReplicas || (h->cfg.precision == GSR_PREC_MIXED && !instr_in_smem(h))) {
         h->nrep = h->nsm;
         TRY(dalloc(h, &h->d_irep, (int64_t)h->nrep * I));
         CK(cudaMemset(h->d_irep, 0, (size_t)h->nrep * I * sizeof(double)));
@@ -398,6 +422,22 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     h->grid_rows2 = aprod2_grid(h);
     if (h->grid_rows2 <= 0)
         return cuda_fail(cudaGetLastError(), "aprod2 occupancy");
+    int ngp = h->grid_rows2;
+    if (h->ipath == kIpSorted) {
+        h->grid_fused = aprod2_fused_grid(h);
+        if (h->grid_fused <= 0)
+            return cuda_fail(cudaGetLastError(), "fused aprod2 occupancy");
+        const int64_t nsu = (h->sys.S + 32 / h->lanes - 1) / (32 / h->lanes);  // star units
+        if (nsu > ((int64_t)1 << 30))
+            h->a2_fused = 0;  // one global partial per star unit: keep the buffer bounded
+        else if (nsu > ngp)
+            ngp = (int)nsu;
+        TRY(dalloc(h, &h->d_a2ctr, 1));
+        CK(cudaMemset(h->d_a2ctr, 0, sizeof(unsigned long long)));
+    } else {
+        h->a2_fused = 0;
+    }
+    TRY(dalloc(h, &h->d_gpart, ngp));
 
     cudaError_t e = build_solve_graph(h);
     if (e != cudaSuccess)
@@ -449,7 +489,7 @@ extern "C" int gsr_create(void **out, const gsr_dims *d, const uint32_t *star_pt
         return GSR_ERR_ARG;
     if (!(c.conlim >= 0.0))
         return GSR_ERR_ARG;
-    if (c.instr_mode < GSR_INSTR_AUTO || c.instr_mode > GSR_INSTR_REPLICAS)
+    if (c.instr_mode < GSR_INSTR_AUTO || c.instr_mode > GSR_INSTR_SORTED)
         return GSR_ERR_ARG;
     if (c.instr_mode == GSR_INSTR_SMEM && d->n_instr > 6144)
         return GSR_ERR_UNSUPPORTED;
@@ -864,6 +904,33 @@ static int cm_buffers(gsr_handle_t *h, int k)
     TRY(dalloc(h, &h->d_bXcm, A.n * k));
     TRY(dalloc(h, &h->d_bCcm, A.n * k));
     h->bkcm = k;
+    return GSR_OK;
+}
+
+extern "C" int gsr_set_aprod2_fused(void *hv, int fused)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || (fused != 0 && fused != 1))
+        return GSR_ERR_ARG;
+    if (h->ipath != kIpSorted)
+        return GSR_ERR_UNSUPPORTED;
+    if (h->a2_fused == fused)
+        return GSR_OK;
+    h->a2_fused = fused;
+    // the captured graphs hold the old launches: capture them again
+    if (h->solve_exec) {
+        cudaGraphExecDestroy(h->solve_exec);
+        h->solve_exec = nullptr;
+    }
+    if (h->cg64_exec) {
+        cudaGraphExecDestroy(h->cg64_exec);
+        h->cg64_exec = nullptr;
+    }
+    cudaError_t e = build_solve_graph(h);
+    if (e == cudaSuccess)
+        e = build_cg64_graph(h);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "gsr_set_aprod2_fused");
     return GSR_OK;
 }
 

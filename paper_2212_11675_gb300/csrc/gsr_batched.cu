@@ -585,7 +585,7 @@ static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, in
         k_b_att<KS><<<h->grid_att, kThreads, 0, st>>>(h->sys, Y, h->d_bS, ldk, cs);
         k_b_att_combine<KS><<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_bS, T, ldk, cs);
     }
-    k_b_instr<KT><<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_biseg, h->d_birow, h->d_bival, Y,
+    k_b_instr<KT><<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_iseg, h->d_irow, h->d_ival32, Y,
                                                   h->d_bipart, ldk, c0);
     k_b_instr_combine<KT><<<h->nsm * 2, kThreads, 0, st>>>(h->sys, h->d_bipart, T, ldk, c0);
     return cudaGetLastError();
@@ -754,24 +754,6 @@ cudaError_t launch_b_products(const gsr_handle_t *h, int k, const float *X, floa
             return e;
     }
     return cudaSuccess;
-}
-
-// ival32[e] = fl32(val[17 + code % 6][code / 6]) for the entry code 6 row + slot
-__global__ void k_gather_instr32(SysView A, const uint32_t *__restrict__ code, float *__restrict__ out)
-{
-    const int64_t ne = kNInstr * A.m;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t g = code[e];
-        out[e] = (float)A.val[(17 + g % kNInstr) * A.mp + g / kNInstr];
-    }
-}
-
-cudaError_t launch_gather_instr32(const gsr_handle_t *h, const uint32_t *code, float *out,
-                                  cudaStream_t st)
-{
-    k_gather_instr32<<<h->nsm * 8, kThreads, 0, st>>>(h->sys, code, out);
-    return cudaGetLastError();
 }
 
 int batched_grid_rows(const gsr_handle_t *h)

@@ -100,6 +100,9 @@ struct ReduceSlots {
     unsigned *counter;   // [kReduceKinds]
 };
 enum ReduceKind { kRedBnorm = 0, kRedU = 1, kRedV = 2, kRedCount = 3 };
+// instrumental part of the FP64 aprod 2: L2 replicas, shared memory per
+// block, or segment sums over the instrument-sorted copy
+enum InstrPath { kIpReplicas = 0, kIpSmem = 1, kIpSorted = 2 };
 constexpr int kPartialsPerKind = 4 * kMaxPartials;  // up to 4 sums per block
 
 }  // namespace gsr
@@ -121,6 +124,18 @@ struct gsr_handle_t {
     double *d_attS = nullptr;           // [nseg][12] attitude segment sums
     double *d_irep = nullptr;           // [nrep][I] instrumental replicas
     int nrep = 0;
+    int ipath = 0;                      // instrumental part of the FP64 aprod 2 (kIp*)
+    // instrument-sorted copy of the instrumental nonzeros: entries of
+    // instrument f are iseg[f] .. iseg[f+1]-1, ascending row irow[e]
+    uint32_t *d_iseg = nullptr, *d_irow = nullptr;
+    double *d_ival = nullptr;           // FP64 values of the sorted entries
+    float *d_ival32 = nullptr;          // binary32 copy (mixed precision)
+    double *d_ipart = nullptr;          // [isplit][I] per-chunk instrumental sums
+    int isplit = 1;                     // chunks per instrument segment
+    double *d_gpart = nullptr;          // per-block partials of the global column (star pass)
+    int a2_fused = 1;                   // aprod 2 in one launch (sorted path), else separate passes
+    unsigned long long *d_a2ctr = nullptr;  // work counter of the single-launch aprod 2
+    int grid_fused = 0;
     // mixed precision
     float *d_val32 = nullptr, *d_tval32 = nullptr;
     float *d_x32 = nullptr, *d_q32 = nullptr;
@@ -132,8 +147,6 @@ struct gsr_handle_t {
     cudaGraphExec_t cg_exec = nullptr;
     cudaGraphExec_t cg64_exec = nullptr;   // FP64 normal-equation CG
     // batched k-RHS solve
-    uint32_t *d_biseg = nullptr, *d_birow = nullptr;  // instrument-sorted copy of A
-    float *d_bival = nullptr;
     int bk = 0;                                       // columns the buffers hold
     int bkcm = 0;                                     // columns of the column-major buffers
     int bkB = 0;                                      // columns of the staged right-hand sides
@@ -169,7 +182,7 @@ struct gsr_handle_t {
     // CUDA graph of one whole solve
     cudaGraphExec_t solve_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
-    int grid_rows = 0, grid_rows2 = 0, grid_vec = 0, grid_att = 0;
+    int grid_rows = 0, grid_rows2 = 0, grid_vec = 0, grid_att = 0, grid_ins = 0;
 };
 
 namespace gsr {
@@ -193,8 +206,6 @@ cudaError_t launch_b_products(const gsr_handle_t *h, int k, const float *X, floa
 cudaError_t launch_b_layout(const gsr_handle_t *h, int to_rm, const double *src, void *dst,
                             int dst_f32, int64_t rows, int k, cudaStream_t st);
 int batched_grid_rows(const gsr_handle_t *h);
-cudaError_t launch_gather_instr32(const gsr_handle_t *h, const uint32_t *code, float *out,
-                                  cudaStream_t st);
 int batched_grid_stars(const gsr_handle_t *h);
 cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out,
                           int mode, cudaStream_t st);
@@ -209,7 +220,11 @@ cudaError_t launch_gather_att(const gsr_handle_t *h, cudaStream_t st);
 int aprod1_grid(const gsr_handle_t *h);
 bool instr_in_smem(const gsr_handle_t *h);
 cudaError_t launch_att_combine(const gsr_handle_t *h, double *out, int nb_att, int nb_ins,
-                               bool accumulate, cudaStream_t st);
+                               double *rep, int nrep, const double *gpart, int ngpart,
+                               bool accumulate, cudaStream_t st, unsigned long long *ctr = nullptr);
+int instr_path(const gsr_config &cfg, int64_t I);
+cudaError_t launch_gather_instr64(const gsr_handle_t *h, const uint32_t *code, double *out,
+                                  cudaStream_t st);
 // mixed precision (gsr_mixed.cu)
 cudaError_t launch_aprod1_f32_api(const gsr_handle_t *h, const double *x, double *y, cudaStream_t st);
 cudaError_t launch_aprod2_f32_api(const gsr_handle_t *h, const double *y, double *x, cudaStream_t st);

@@ -156,26 +156,20 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
 // part overwritten, instrumental/global accumulated into zeroed memory.
 // kA2Squares: as kA2Overwrite with A_ik^2 in place of A_ik y_i.
 // ---------------------------------------------------------------------------
-template <int G, int MODE, bool SMEM_INSTR>
-__global__ void __launch_bounds__(kThreads)
-k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out,
-               double *__restrict__ rep, int nrep)
+// Star-group part of warp `warp` of `nwarps`: astrometric sums of G lanes
+// per star (rows are star-grouped), the instrumental products unless the
+// sorted path (IP == kIpSorted) takes them, and this thread's share of the
+// global column, which is returned.
+template <int G, int MODE, int IP>
+__device__ __forceinline__ double stars_body(const SysView &A, const double *__restrict__ y,
+                                             double *__restrict__ out, double *__restrict__ rep,
+                                             int nrep, double *s_ins, int64_t warp, int64_t nwarps)
 {
-    extern __shared__ double s_ins[];
-    __shared__ double s_red[kThreads / 32];
     constexpr int GPW = 32 / G;
     const int lane = threadIdx.x & (G - 1);
     const int gw = (threadIdx.x & 31) / G;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t mp = A.mp;
-    if (SMEM_INSTR) {
-        for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x)
-            s_ins[f] = 0.0;
-        __syncthreads();
-    }
     double gacc = 0.0;
-
     for (int64_t s0 = warp * GPW; s0 < A.S; s0 += nwarps * GPW) {
         const int64_t s = s0 + gw;
         uint32_t r0 = 0, r1 = 0;
@@ -185,7 +179,9 @@ k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out
         }
         double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
         for (uint32_t r = r0 + lane; r < r1; r += G) {
-            const uint4 rc = __ldcs(A.rec + r);
+            // the sorted path leaves the instrumental nonzeros to its own pass
+            constexpr bool INS = IP != kIpSorted;
+            const uint4 rc = INS ? __ldcs(A.rec + r) : make_uint4(0, 0, 0, 0);
             const double *v = A.val + r;
             double va[kNAstro], vi[kNInstr], vg;
 #pragma unroll
@@ -193,7 +189,7 @@ k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out
                 va[k] = __ldcs(v + k * mp);
 #pragma unroll
             for (int j = 0; j < kNInstr; j++)
-                vi[j] = __ldcs(v + (17 + j) * mp);
+                vi[j] = INS ? __ldcs(v + (17 + j) * mp) : 0.0;
             vg = __ldcs(v + 23 * mp);
             double yi;
             if (MODE == kA2Squares) {
@@ -216,9 +212,9 @@ k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out
 #pragma unroll
             for (int j = 0; j < kNInstr; j++) {
                 const uint32_t f = instr_at(rc, j);
-                if (SMEM_INSTR)
+                if (IP == kIpSmem)
                     atomicAdd(&s_ins[f], vi[j] * yi);
-                else  // reduction in L2 into this block's replica
+                else if (IP == kIpReplicas)  // reduction in L2 into this block's replica
                     atomicAdd(rep + (blockIdx.x % nrep) * A.I + f, vi[j] * yi);
             }
             gacc = fma(vg, yi, gacc);
@@ -270,8 +266,15 @@ k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out
             }
         }
     }
-    // global column: one reduction per block
-    double g = warp_sum(gacc);
+    return gacc;
+}
+
+// global column: one partial per block, added in block order by the combine
+// kernel
+__device__ __forceinline__ void global_partial(double gacc, double *__restrict__ gpart)
+{
+    __shared__ double s_red[kThreads / 32];
+    const double g = warp_sum(gacc);
     if ((threadIdx.x & 31) == 0)
         s_red[threadIdx.x >> 5] = g;
     __syncthreads();
@@ -279,9 +282,26 @@ k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out
         double t = 0.0;
         for (int w = 0; w < kThreads / 32; w++)
             t += s_red[w];
-        atomicAdd(out + A.glb0, t);
+        gpart[blockIdx.x] = t;
     }
-    if (SMEM_INSTR) {
+}
+
+template <int G, int MODE, int IP>
+__global__ void __launch_bounds__(kThreads)
+k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out,
+               double *__restrict__ rep, int nrep, double *__restrict__ gpart)
+{
+    extern __shared__ double s_ins[];
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (IP == kIpSmem) {
+        for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x)
+            s_ins[f] = 0.0;
+        __syncthreads();
+    }
+    const double gacc = stars_body<G, MODE, IP>(A, y, out, rep, nrep, s_ins, warp, nwarps);
+    global_partial(gacc, gpart);
+    if (IP == kIpSmem) {
         for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x) {
             const double t = s_ins[f];
             if (t != 0.0)
@@ -291,17 +311,105 @@ k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out
 }
 
 // ---------------------------------------------------------------------------
+// aprod 2, instrumental part over the instrument-sorted copy (column f of
+// Alg. 2's instrumental block is the sum over its entries of value * y_row).
+// Unit w covers chunk q = w % nsplit of instrument f = w / nsplit; a warp
+// sums its chunk with four independent FMA chains (four gathers of y in
+// flight per lane) and writes the chunk's total to part[q * I + f].  The
+// combine kernel adds the nsplit chunk totals of each instrument in a fixed
+// order: no atomics, deterministic.  SQ: squares of the values.
+// ---------------------------------------------------------------------------
+template <bool SQ>
+__device__ __forceinline__ void instr_body(const SysView &A, const uint32_t *__restrict__ iseg,
+                                           const uint32_t *__restrict__ irow,
+                                           const double *__restrict__ ival,
+                                           const double *__restrict__ y, double *__restrict__ part,
+                                           int nsplit, int64_t warp, int64_t nwarps)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t w = warp; w < A.I * nsplit; w += nwarps) {
+        const int64_t f = w / nsplit;
+        const int q = (int)(w - f * nsplit);
+        const uint32_t s0 = iseg[f];
+        const uint64_t len = iseg[f + 1] - s0;
+        const uint32_t e1 = s0 + (uint32_t)(len * (q + 1) / nsplit);
+        uint32_t e = s0 + (uint32_t)(len * q / nsplit) + lane;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        // four entries per lane in flight: the row indices first, then the
+        // four independent gathers of y
+        for (; e + 96 < e1; e += 128) {
+            double v[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                v[u] = __ldcs(ival + e + 32 * u);
+            if (SQ) {
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    yv[u] = v[u];
+            } else {
+                uint32_t r[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    r[u] = __ldcs(irow + e + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    yv[u] = __ldg(y + r[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                acc[u] = fma(v[u], yv[u], acc[u]);
+        }
+        for (int u = 0; e < e1; e += 32, u++) {
+            const double v = __ldcs(ival + e);
+            acc[u & 3] = fma(v, SQ ? v : __ldg(y + __ldcs(irow + e)), acc[u & 3]);
+        }
+        const double t = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        if (lane == 0)
+            part[(int64_t)q * A.I + f] = t;
+    }
+}
+
+template <bool SQ>
+__global__ void __launch_bounds__(kThreads)
+k_instr_segments(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restrict__ irow,
+                 const double *__restrict__ ival, const double *__restrict__ y,
+                 double *__restrict__ part, int nsplit)
+{
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    instr_body<SQ>(A, iseg, irow, ival, y, part, nsplit, warp, nwarps);
+}
+
+// ival[e] = val[17 + code % 6][code / 6] for the entry code 6 row + slot
+__global__ void k_gather_instr64(SysView A, const uint32_t *__restrict__ code,
+                                 double *__restrict__ out)
+{
+    const int64_t total = kNInstr * A.m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = code[e];
+        const uint32_t row = c / kNInstr, slot = c - row * kNInstr;
+        out[e] = A.val[(int64_t)(kNAstro + kNAtt + slot) * A.mp + row];
+    }
+}
+
+cudaError_t launch_gather_instr64(const gsr_handle_t *h, const uint32_t *code, double *out,
+                                  cudaStream_t st)
+{
+    k_gather_instr64<<<h->nsm * 8, kThreads, 0, st>>>(h->sys, code, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // aprod 2, attitude part.  Pass 1: one warp per attitude offset o sums the
 // products of the rows with that offset into S[o][4a + j].  SQ: squares of
 // the values (preconditioner) instead of products with y.
 // ---------------------------------------------------------------------------
 template <bool SQ>
-__global__ void __launch_bounds__(kThreads)
-k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
+__device__ __forceinline__ void att_body(const SysView &A, const double *__restrict__ y,
+                                         double *__restrict__ S, int64_t warp, int64_t nwarps)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t mp = A.mp;
     for (int64_t o = warp; o < A.nseg; o += nwarps) {
         const uint32_t e0 = A.seg[o], e1 = A.seg[o + 1];
@@ -342,16 +450,104 @@ k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
     }
 }
 
+template <bool SQ>
+__global__ void __launch_bounds__(kThreads)
+k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
+{
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    att_body<SQ>(A, y, S, warp, nwarps);
+}
+
+// ---------------------------------------------------------------------------
+// aprod 2 in one launch (sorted instrumental path): the three passes above
+// run side by side, so the FP64-bound star and attitude sums share every SM
+// with the gather-bound instrumental sums.  The work is a queue of units --
+// star groups (GPW stars per warp), attitude segments (one offset) and
+// instrument chunks -- interleaved by a repeating pattern of L = ns + na + ni
+// slots (ns star, na attitude, ni instrument units per period, in
+// proportion to their counts).  A warp takes the next unit index from a
+// device counter, so the roles balance themselves; the combine kernel
+// resets the counter.  Which warp computes a unit does not change its sums:
+// the global column gets one partial per star unit, gpart[unit].
+// ---------------------------------------------------------------------------
+struct A2Queue {
+    unsigned long long *ctr;  // next unit index (zero on entry)
+    int ns, na, ni;           // slots per period of each unit type
+    int64_t nstar_units;      // ceil(S / GPW)
+    int64_t ninstr_units;     // I * nsplit
+    int64_t total;            // periods * (ns + na + ni)
+};
+
+template <int G, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out,
+               double *__restrict__ S, const uint32_t *__restrict__ iseg,
+               const uint32_t *__restrict__ irow, const double *__restrict__ ival,
+               double *__restrict__ part, int nsplit, double *__restrict__ gpart, A2Queue q)
+{
+    constexpr bool SQ = MODE == kA2Squares;
+    const int lane = threadIdx.x & 31;
+    const int L = q.ns + q.na + q.ni;
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0)
+            u = atomicAdd(q.ctr, 1ull);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if ((int64_t)u >= q.total)
+            break;
+        const int64_t c = (int64_t)u / L;
+        const int slot = (int)((int64_t)u - c * L);
+        if (slot < q.ns) {
+            const int64_t i = c * q.ns + slot;
+            if (i < q.nstar_units) {
+                // the unit's global-column partial, summed in unit order by
+                // the combine kernel (independent of which warp took it)
+                const double g = warp_sum(stars_body<G, MODE, kIpSorted>(
+                    A, y, out, nullptr, 1, nullptr, i, q.nstar_units));
+                if (lane == 0)
+                    gpart[i] = g;
+            }
+        } else if (slot < q.ns + q.na) {
+            const int64_t i = c * q.na + (slot - q.ns);
+            if (i < A.nseg)
+                att_body<SQ>(A, y, S, i, A.nseg);
+        } else {
+            const int64_t i = c * q.ni + (slot - q.ns - q.na);
+            if (i < q.ninstr_units)
+                instr_body<SQ>(A, iseg, irow, ival, y, part, nsplit, i, q.ninstr_units);
+        }
+    }
+}
+
 // Pass 2, fused with the instrumental replicas.  Blocks [0, nb_att) combine
 // the attitude columns: column a*D + k receives sum_{j=0..3} S[k-j][4a+j]
-// (0 <= k-j < nseg).  The remaining blocks (when rep != null) take 8
-// instrument columns each, one warp per column, summing the replicas in a
-// fixed order and clearing them for the next call.
+// (0 <= k-j < nseg).  The next blocks (when rep != null) take 8
+// instrument columns each, one warp per column, summing the replicas (or the
+// chunk totals of the sorted pass) in a fixed order and clearing them for
+// the next call.  With gpart, one last block adds the ngpart per-block
+// partials of the global column in block order (and clears ctr).
 template <bool ACC>
 __global__ void __launch_bounds__(kThreads)
 k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out,
-              double *__restrict__ rep, int nrep, int nb_att)
+              double *__restrict__ rep, int nrep, int nb_att, const double *__restrict__ gpart,
+              int ngpart, unsigned long long *ctr)
 {
+    if (gpart && blockIdx.x == gridDim.x - 1) {
+        // the global column from the star pass's partials (per block, or per
+        // star unit of the single-launch aprod 2, whose work counter is reset
+        // here for the next launch)
+        double t[1] = {0.0};
+        for (int b = threadIdx.x; b < ngpart; b += blockDim.x)
+            t[0] += gpart[b];
+        block_sum<1>(t);
+        if (threadIdx.x == 0) {
+            out[A.glb0] += t[0];
+            if (ctr)
+                *ctr = 0ull;
+        }
+        return;
+    }
     if ((int)blockIdx.x < nb_att) {
         const int64_t total = 3 * A.D;
         for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
@@ -432,6 +628,7 @@ cudaError_t launch_aprod1_with_slots(const gsr_handle_t *h, const double *x, dou
     return a1_launch<1>(h, x, y, st_slot, partial, counter, st);
 }
 
+// shared-memory instrument sums of the binary32 star pass
 bool instr_in_smem(const gsr_handle_t *h)
 {
     if (h->cfg.instr_mode == GSR_INSTR_REPLICAS)
@@ -439,19 +636,34 @@ bool instr_in_smem(const gsr_handle_t *h)
     return h->sys.I <= kSmemInstrMax;
 }
 
+int instr_path(const gsr_config &cfg, int64_t I)
+{
+    switch (cfg.instr_mode) {
+    case GSR_INSTR_SMEM: return I <= kSmemInstrMax ? kIpSmem : kIpReplicas;
+    case GSR_INSTR_REPLICAS: return kIpReplicas;
+    default: return kIpSorted;
+    }
+}
+
 template <int G, int MODE>
 static cudaError_t a2_stars(const gsr_handle_t *h, const double *y, double *out, cudaStream_t st)
 {
-    if (instr_in_smem(h)) {
-        const size_t shm = (size_t)h->sys.I * sizeof(double);
-        k_aprod2_stars<G, MODE, true><<<h->grid_rows2, kThreads, shm, st>>>(h->sys, y, out,
-                                                                             nullptr, 1);
-        return cudaGetLastError();
+    switch (h->ipath) {
+    case kIpSmem:
+        k_aprod2_stars<G, MODE, kIpSmem><<<h->grid_rows2, kThreads, (size_t)h->sys.I * sizeof(double),
+                                           st>>>(h->sys, y, out, nullptr, 1, h->d_gpart);
+        break;
+    case kIpReplicas:
+        // the replicas are zero on entry (cleared at creation and by every
+        // combine that reads them)
+        k_aprod2_stars<G, MODE, kIpReplicas><<<h->grid_rows2, kThreads, 0, st>>>(
+            h->sys, y, out, h->d_irep, h->nrep, h->d_gpart);
+        break;
+    default:
+        k_aprod2_stars<G, MODE, kIpSorted><<<h->grid_rows2, kThreads, 0, st>>>(
+            h->sys, y, out, nullptr, 1, h->d_gpart);
+        break;
     }
-    // the replicas are zero on entry (cleared at creation and by every
-    // combine that reads them)
-    k_aprod2_stars<G, MODE, false><<<h->grid_rows2, kThreads, 0, st>>>(h->sys, y, out, h->d_irep,
-                                                                        h->nrep);
     return cudaGetLastError();
 }
 
@@ -466,8 +678,23 @@ static cudaError_t a2_stars_g(const gsr_handle_t *h, const double *y, double *ou
     }
 }
 
-cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out, int mode,
-                          cudaStream_t st)
+static int att_combine_blocks(const gsr_handle_t *h)
+{
+    const int64_t nb = (3 * h->sys.D + kThreads - 1) / kThreads;
+    return (int)(nb < 4 * h->nsm ? nb : 4 * h->nsm);
+}
+
+static int instr_combine_blocks(const gsr_handle_t *h)
+{
+    return (int)((h->sys.I + kThreads / 32 - 1) / (kThreads / 32));
+}
+
+static cudaError_t a2_rest(const gsr_handle_t *h, const double *y, double *out, int mode,
+                           int ngpart, cudaStream_t st);
+
+// aprod 2 as separate star, attitude (and instrumental) passes
+static cudaError_t launch_aprod2_split(const gsr_handle_t *h, const double *y, double *out,
+                                       int mode, cudaStream_t st)
 {
     cudaError_t e;
     switch (mode) {
@@ -481,22 +708,106 @@ cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out, i
         k_att_segments<true><<<h->grid_att, kThreads, 0, st>>>(h->sys, y, h->d_attS);
     else
         k_att_segments<false><<<h->grid_att, kThreads, 0, st>>>(h->sys, y, h->d_attS);
-    const int nb_att = (int)((3 * h->sys.D + kThreads - 1) / kThreads < 4 * h->nsm
-                                 ? (3 * h->sys.D + kThreads - 1) / kThreads
-                                 : 4 * h->nsm);
-    const int nb_ins = instr_in_smem(h) ? 0 : (int)((h->sys.I + kThreads / 32 - 1) / (kThreads / 32));
-    return launch_att_combine(h, out, nb_att, nb_ins, mode == kA2Accumulate, st);
+    return a2_rest(h, y, out, mode, h->grid_rows2, st);
+}
+
+// the unit queue of the single-launch aprod 2 for G lanes per star
+A2Queue a2_queue(const gsr_handle_t *h, int G)
+{
+    A2Queue q;
+    q.ctr = h->d_a2ctr;
+    q.nstar_units = (h->sys.S + 32 / G - 1) / (32 / G);
+    q.ninstr_units = h->sys.I * h->isplit;
+    const int64_t n[3] = {q.nstar_units, h->sys.nseg, q.ninstr_units};
+    const int64_t tot = n[0] + n[1] + n[2];
+    int sl[3];
+    for (int t = 0; t < 3; t++) {
+        sl[t] = (int)((16 * n[t] + tot / 2) / tot);
+        if (sl[t] < 1 && n[t] > 0)
+            sl[t] = 1;
+    }
+    q.ns = sl[0];
+    q.na = sl[1];
+    q.ni = sl[2];
+    int64_t periods = 0;
+    for (int t = 0; t < 3; t++)
+        if (sl[t] > 0) {
+            const int64_t p = (n[t] + sl[t] - 1) / sl[t];
+            if (p > periods)
+                periods = p;
+        }
+    q.total = periods * (q.ns + q.na + q.ni);
+    return q;
+}
+
+template <int G, int MODE>
+static void fused_launch(const gsr_handle_t *h, const double *y, double *out, cudaStream_t st)
+{
+    k_aprod2_fused<G, MODE><<<h->grid_fused, kThreads, 0, st>>>(
+        h->sys, y, out, h->d_attS, h->d_iseg, h->d_irow, h->d_ival, h->d_ipart, h->isplit,
+        h->d_gpart, a2_queue(h, G));
+}
+
+template <int MODE>
+static void fused_launch_g(const gsr_handle_t *h, const double *y, double *out, cudaStream_t st)
+{
+    switch (h->lanes) {
+    case 4: fused_launch<4, MODE>(h, y, out, st); break;
+    case 8: fused_launch<8, MODE>(h, y, out, st); break;
+    case 32: fused_launch<32, MODE>(h, y, out, st); break;
+    default: fused_launch<16, MODE>(h, y, out, st); break;
+    }
+}
+
+cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out, int mode,
+                          cudaStream_t st)
+{
+    if (h->ipath == kIpSorted && h->a2_fused) {
+        switch (mode) {
+        case kA2Accumulate: fused_launch_g<kA2Accumulate>(h, y, out, st); break;
+        case kA2Overwrite: fused_launch_g<kA2Overwrite>(h, y, out, st); break;
+        default: fused_launch_g<kA2Squares>(h, y, out, st); break;
+        }
+        const int nb_att = att_combine_blocks(h);
+        return launch_att_combine(h, out, nb_att, instr_combine_blocks(h), h->d_ipart, h->isplit,
+                                  h->d_gpart, (int)a2_queue(h, h->lanes).nstar_units,
+                                  mode == kA2Accumulate, st, h->d_a2ctr);
+    }
+    return launch_aprod2_split(h, y, out, mode, st);
+}
+
+// the instrumental pass (sorted path) and the combine after the star and
+// attitude passes; ngpart star-pass blocks wrote global partials
+static cudaError_t a2_rest(const gsr_handle_t *h, const double *y, double *out, int mode,
+                           int ngpart, cudaStream_t st)
+{
+    const int nb_att = att_combine_blocks(h);
+    if (h->ipath == kIpSorted) {
+        if (mode == kA2Squares)
+            k_instr_segments<true><<<h->grid_ins, kThreads, 0, st>>>(
+                h->sys, h->d_iseg, h->d_irow, h->d_ival, y, h->d_ipart, h->isplit);
+        else
+            k_instr_segments<false><<<h->grid_ins, kThreads, 0, st>>>(
+                h->sys, h->d_iseg, h->d_irow, h->d_ival, y, h->d_ipart, h->isplit);
+        return launch_att_combine(h, out, nb_att, instr_combine_blocks(h), h->d_ipart, h->isplit,
+                                  h->d_gpart, ngpart, mode == kA2Accumulate, st);
+    }
+    const int nb_ins = h->ipath == kIpSmem ? 0 : instr_combine_blocks(h);
+    return launch_att_combine(h, out, nb_att, nb_ins, h->d_irep, h->nrep, h->d_gpart, ngpart,
+                              mode == kA2Accumulate, st);
 }
 
 cudaError_t launch_att_combine(const gsr_handle_t *h, double *out, int nb_att, int nb_ins,
-                               bool accumulate, cudaStream_t st)
+                               double *rep, int nrep, const double *gpart, int ngpart,
+                               bool accumulate, cudaStream_t st, unsigned long long *ctr)
 {
+    const int nb = nb_att + nb_ins + (gpart ? 1 : 0);
     if (accumulate)
-        k_att_combine<true><<<nb_att + nb_ins, kThreads, 0, st>>>(h->sys, h->d_attS, out,
-                                                                   h->d_irep, h->nrep, nb_att);
+        k_att_combine<true><<<nb, kThreads, 0, st>>>(h->sys, h->d_attS, out, rep, nrep, nb_att,
+                                                      gpart, ngpart, ctr);
     else
-        k_att_combine<false><<<nb_att + nb_ins, kThreads, 0, st>>>(h->sys, h->d_attS, out,
-                                                                    h->d_irep, h->nrep, nb_att);
+        k_att_combine<false><<<nb, kThreads, 0, st>>>(h->sys, h->d_attS, out, rep, nrep, nb_att,
+                                                       gpart, ngpart, ctr);
     return cudaGetLastError();
 }
 
@@ -702,14 +1013,42 @@ int aprod1_grid(const gsr_handle_t *h)
 template <int G>
 static int a2_occupancy(const gsr_handle_t *h)
 {
-    const bool smem = instr_in_smem(h);
-    const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
     int occ = 0;
-    cudaError_t e = smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &occ, k_aprod2_stars<G, kA2Overwrite, true>, kThreads, shm)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &occ, k_aprod2_stars<G, kA2Overwrite, false>, kThreads, 0);
+    cudaError_t e;
+    switch (h->ipath) {
+    case kIpSmem:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod2_stars<G, kA2Overwrite, kIpSmem>,
+                                                          kThreads, (size_t)h->sys.I * sizeof(double));
+        break;
+    case kIpReplicas:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, k_aprod2_stars<G, kA2Overwrite, kIpReplicas>, kThreads, 0);
+        break;
+    default:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, k_aprod2_stars<G, kA2Overwrite, kIpSorted>, kThreads, 0);
+        break;
+    }
     return e == cudaSuccess ? occ : -1;
+}
+
+// blocks of the fused aprod 2: all resident blocks, a multiple of 8
+int aprod2_fused_grid(const gsr_handle_t *h)
+{
+    int occ = 0;
+    cudaError_t e;
+    switch (h->lanes) {
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod2_fused<4, kA2Overwrite>, kThreads, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod2_fused<8, kA2Overwrite>, kThreads, 0); break;
+    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod2_fused<32, kA2Overwrite>, kThreads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod2_fused<16, kA2Overwrite>, kThreads, 0); break;
+    }
+    if (e != cudaSuccess || occ <= 0)
+        return -1;
+    int64_t g = (int64_t)h->nsm * occ / 8 * 8;
+    if (g > kMaxPartials)
+        g = kMaxPartials;
+    return (int)(g < 8 ? 8 : g);
 }
 
 int aprod2_grid(const gsr_handle_t *h)

@@ -453,7 +453,8 @@ static cudaError_t a2f_launch(const gsr_handle_t *h, const float *y32, double *o
                                  ? (3 * h->sys.D + kThreads - 1) / kThreads
                                  : 4 * h->nsm);
     const int nb_ins = smem ? 0 : (int)((h->sys.I + kThreads / 32 - 1) / (kThreads / 32));
-    launch_att_combine(h, out, nb_att, nb_ins, MODE == kA2Accumulate, st);
+    launch_att_combine(h, out, nb_att, nb_ins, h->d_irep, h->nrep, nullptr, 0, MODE == kA2Accumulate,
+                       st);
     return cudaGetLastError();
 }
 

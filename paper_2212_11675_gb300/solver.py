@@ -187,6 +187,11 @@ class Solver:
                                      ctypes.byref(res), _stream(stream)), "gsr_lsq_backward")
         return gb, gg, res.as_dict()
 
+    def set_aprod2_fused(self, fused):
+        """aprod 2 (sorted instrumental path) in one launch with a shared work
+        queue (True, the default) or as separate passes (False)."""
+        check(lib().gsr_set_aprod2_fused(self._h, 1 if fused else 0), "gsr_set_aprod2_fused")
+
     def set_batch_tiling(self, kt, lanes):
         """Column tile (1, 2, 4, 8) and lanes per star (8, 16, 32) of the batched kernels."""
         check(lib().gsr_set_batch_tiling(self._h, int(kt), int(lanes)), "gsr_set_batch_tiling")

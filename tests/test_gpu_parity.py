@@ -67,13 +67,16 @@ def test_aprod_parity_ragged_and_empty_stars():
 
 
 def test_aprod_parity_instruments_beyond_shared_memory():
-    # I above the shared-memory privatisation limit takes the replica path
+    # I above the shared-memory privatisation limit; most instruments have
+    # no entry at all (empty segments of the instrument-sorted copy)
     check_aprods(small(300, 50, 7000, seed=9), 8)
 
 
-@pytest.mark.parametrize("mode", [_lib.GSR_INSTR_SMEM, _lib.GSR_INSTR_REPLICAS])
-def test_aprod_parity_instrument_modes(mode):
-    sys = gen.make("tiny")
+@pytest.mark.parametrize("mode", [_lib.GSR_INSTR_SMEM, _lib.GSR_INSTR_REPLICAS,
+                                  _lib.GSR_INSTR_SORTED])
+@pytest.mark.parametrize("shape", ["tiny", "ragged"])
+def test_aprod_parity_instrument_modes(mode, shape):
+    sys = gen.make("tiny") if shape == "tiny" else small(411, 37, 11, seed=12)
     rng = np.random.default_rng(8)
     y = rng.standard_normal(sys.m)
     ref = oracle.aprod2(sys, y)
@@ -81,7 +84,61 @@ def test_aprod_parity_instrument_modes(mode):
         xd = torch.zeros(sys.n, dtype=torch.float64, device=DEV)
         s.aprod2(torch.tensor(y, device=DEV), xd)
         g = xd.cpu().numpy()
+        # the preconditioner runs through the same instrumental path (squares)
+        p = torch.zeros(sys.n, dtype=torch.float64, device=DEV)
+        s.precondition(p)
+        pg = p.cpu().numpy()
     assert np.linalg.norm(g - ref) <= 1e-12 * np.linalg.norm(ref)
+    np.testing.assert_allclose(pg, oracle.precondition(sys)[0], rtol=1e-13)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("lanes", [8, 32])
+def test_aprod2_schedules(fused, lanes):
+    # aprod 2 in one launch (shared work queue) and as separate passes, on a
+    # ragged system; the solve graph is captured again after the switch
+    sys = small(411, 37, 11, seed=12)
+    rng = np.random.default_rng(21)
+    y = rng.standard_normal(sys.m)
+    ref = oracle.aprod2(sys, y)
+    b = _rhs(sys, 5)
+    o = oracle.pc_lsqr(sys, b, 40, 0.0, 0.0)
+    with _solver(sys, instr_mode=_lib.GSR_INSTR_SORTED, lanes_per_star=lanes) as s:
+        s.set_aprod2_fused(not fused)
+        s.set_aprod2_fused(fused)
+        for _ in range(2):  # the work counter is reset between launches
+            xd = torch.zeros(sys.n, dtype=torch.float64, device=DEV)
+            s.aprod2(torch.tensor(y, device=DEV), xd)
+            g = xd.cpu().numpy()
+            assert np.linalg.norm(g - ref) <= 1e-12 * np.linalg.norm(ref)
+        x, _, res = s.lsqr_solve(torch.tensor(b, device=DEV), 40, 0.0, 0.0, want_se=False)
+    assert res["itn"] == 40
+    xo = o["x"]
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_aprod2_schedule_needs_sorted_path():
+    sys = gen.make("tiny")
+    with _solver(sys, instr_mode=_lib.GSR_INSTR_SORTED) as s:
+        with pytest.raises(_lib.GsrError):
+            _lib.check(_lib.lib().gsr_set_aprod2_fused(s.handle, 2), "gsr_set_aprod2_fused")
+    with _solver(sys, instr_mode=_lib.GSR_INSTR_SMEM) as s:
+        with pytest.raises(_lib.GsrError):
+            s.set_aprod2_fused(True)
+
+
+def test_sorted_instrument_path_is_deterministic():
+    # segment sums in a fixed order: repeated products are bitwise identical
+    sys = gen.make("tiny")
+    rng = np.random.default_rng(3)
+    y = torch.tensor(rng.standard_normal(sys.m), device=DEV)
+    with _solver(sys, instr_mode=_lib.GSR_INSTR_SORTED) as s:
+        outs = []
+        for _ in range(3):
+            xd = torch.zeros(sys.n, dtype=torch.float64, device=DEV)
+            s.aprod2(y, xd)
+            outs.append(xd.cpu().numpy())
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
 
 
 def test_aprod_parity_single_star():
