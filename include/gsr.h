@@ -294,7 +294,8 @@ int gsr_batched_products(void *h, int k, const double *X, const double *Y,
 int gsr_set_batch_tiling(void *h, int kt, int lanes);
 
 /*
- * Schedule of the FP64 aprod 2 (Alg. 2) on the sorted instrumental path
+ * Schedule of aprod 2 (Alg. 2; FP64, and the binary32 form inside the
+ * mixed-precision inner solve) on the sorted instrumental path
  * (GSR_INSTR_SORTED, the default).  fused = 1 (default): the star-group
  * sums, the attitude segment sums and the instrumental segment sums run in
  * one launch whose warps take units of all three kinds from one work queue,

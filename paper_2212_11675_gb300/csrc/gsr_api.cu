@@ -239,7 +239,8 @@ static int create_mixed(gsr_handle_t *h, cudaStream_t st)
     h->n_nonempty = h->h_onorm[0];
     h->grid_rows32 = aprod1_f32_grid(h);
     h->grid_rows2_32 = aprod2_f32_grid(h);
-    if (h->grid_rows32 <= 0 || h->grid_rows2_32 <= 0)
+    h->grid_fused32 = aprod2_f32_fused_grid(h);
+    if (h->grid_rows32 <= 0 || h->grid_rows2_32 <= 0 || h->grid_fused32 <= 0)
         return cuda_fail(cudaGetLastError(), "mixed occupancy");
     cudaError_t e = build_cg_graph(h);
     if (e != cudaSuccess)
@@ -427,7 +428,11 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
         h->grid_fused = aprod2_fused_grid(h);
         if (h->grid_fused <= 0)
             return cuda_fail(cudaGetLastError(), "fused aprod2 occupancy");
-        const int64_t nsu = (h->sys.S + 32 / h->lanes - 1) / (32 / h->lanes);  // star units
+        // star units of the FP64 and of the binary32 (4 stars each) launches
+        int64_t nsu = (h->sys.S + 32 / h->lanes - 1) / (32 / h->lanes);
+        const int64_t nsu32 = (h->sys.S + 3) / 4;
+        if (nsu32 > nsu)
+            nsu = nsu32;
         if (nsu > ((int64_t)1 << 30))
             h->a2_fused = 0;  // one global partial per star unit: keep the buffer bounded
         else if (nsu > ngp)
@@ -926,9 +931,16 @@ extern "C" int gsr_set_aprod2_fused(void *hv, int fused)
         cudaGraphExecDestroy(h->cg64_exec);
         h->cg64_exec = nullptr;
     }
+    const bool mixed = h->cg_exec != nullptr;
+    if (h->cg_exec) {
+        cudaGraphExecDestroy(h->cg_exec);
+        h->cg_exec = nullptr;
+    }
     cudaError_t e = build_solve_graph(h);
     if (e == cudaSuccess)
         e = build_cg64_graph(h);
+    if (e == cudaSuccess && mixed)
+        e = build_cg_graph(h);
     if (e != cudaSuccess)
         return cuda_fail(e, "gsr_set_aprod2_fused");
     return GSR_OK;

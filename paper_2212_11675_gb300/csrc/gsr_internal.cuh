@@ -103,6 +103,18 @@ enum ReduceKind { kRedBnorm = 0, kRedU = 1, kRedV = 2, kRedCount = 3 };
 // instrumental part of the FP64 aprod 2: L2 replicas, shared memory per
 // block, or segment sums over the instrument-sorted copy
 enum InstrPath { kIpReplicas = 0, kIpSmem = 1, kIpSorted = 2 };
+// work queue of the single-launch aprod 2: star units (GPW stars each),
+// attitude segments and instrument chunks, interleaved by a repeating
+// pattern of ns + na + ni slots
+struct A2Queue {
+    unsigned long long *ctr;  // next unit index (zero on entry)
+    int ns, na, ni;           // slots per period of each unit type
+    int star_k;               // star groups (GPW stars each) per star unit
+    int64_t nstar_groups;     // ceil(S / GPW)
+    int64_t nstar_units;      // ceil(nstar_groups / star_k)
+    int64_t ninstr_units;     // I * nsplit
+    int64_t total;            // periods * (ns + na + ni)
+};
 constexpr int kPartialsPerKind = 4 * kMaxPartials;  // up to 4 sums per block
 
 }  // namespace gsr
@@ -164,7 +176,7 @@ struct gsr_handle_t {
     int b_kt = 8, b_lanes = 16, b_graph_k = 0, b_graph_kt = 0, b_graph_lanes = 0;
     int grid_b1 = 0, grid_b2 = 0;
     double *d_xp64 = nullptr, *d_q64 = nullptr;
-    int grid_rows32 = 0, grid_rows2_32 = 0;
+    int grid_rows32 = 0, grid_rows2_32 = 0, grid_fused32 = 0;
     double n_nonempty = 0.0;
     double *d_p = nullptr;              // preconditioner
     double *d_u = nullptr;              // m
@@ -223,6 +235,7 @@ cudaError_t launch_att_combine(const gsr_handle_t *h, double *out, int nb_att, i
                                double *rep, int nrep, const double *gpart, int ngpart,
                                bool accumulate, cudaStream_t st, unsigned long long *ctr = nullptr);
 int instr_path(const gsr_config &cfg, int64_t I);
+A2Queue a2_queue(const gsr_handle_t *h, int G);
 cudaError_t launch_gather_instr64(const gsr_handle_t *h, const uint32_t *code, double *out,
                                   cudaStream_t st);
 // mixed precision (gsr_mixed.cu)
@@ -239,6 +252,7 @@ cudaError_t launch_count_pos(const gsr_handle_t *h, const double *a, double *out
 cudaError_t launch_to_f32(const gsr_handle_t *h, const double *a, float *b, int64_t n, cudaStream_t st);
 int aprod1_f32_grid(const gsr_handle_t *h);
 int aprod2_f32_grid(const gsr_handle_t *h);
+int aprod2_f32_fused_grid(const gsr_handle_t *h);
 cudaError_t enqueue_precondition(const gsr_handle_t *h, double *p, cudaStream_t st);
 // LSQR pieces (gsr_lsqr.cu)
 cudaError_t build_solve_graph(gsr_handle_t *h);

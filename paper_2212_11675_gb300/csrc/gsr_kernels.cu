@@ -471,14 +471,6 @@ k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
 // resets the counter.  Which warp computes a unit does not change its sums:
 // the global column gets one partial per star unit, gpart[unit].
 // ---------------------------------------------------------------------------
-struct A2Queue {
-    unsigned long long *ctr;  // next unit index (zero on entry)
-    int ns, na, ni;           // slots per period of each unit type
-    int64_t nstar_units;      // ceil(S / GPW)
-    int64_t ninstr_units;     // I * nsplit
-    int64_t total;            // periods * (ns + na + ni)
-};
-
 template <int G, int MODE>
 __global__ void __launch_bounds__(kThreads)
 k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out,
@@ -501,10 +493,17 @@ k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out
         if (slot < q.ns) {
             const int64_t i = c * q.ns + slot;
             if (i < q.nstar_units) {
-                // the unit's global-column partial, summed in unit order by
-                // the combine kernel (independent of which warp took it)
-                const double g = warp_sum(stars_body<G, MODE, kIpSorted>(
-                    A, y, out, nullptr, 1, nullptr, i, q.nstar_units));
+                // star_k consecutive star groups; the unit's global-column
+                // partial is summed in unit order by the combine kernel
+                // (independent of which warp took the unit)
+                double g = 0.0;
+                for (int k = 0; k < q.star_k; k++) {
+                    const int64_t grp = i * q.star_k + k;
+                    if (grp < q.nstar_groups)
+                        g += stars_body<G, MODE, kIpSorted>(A, y, out, nullptr, 1, nullptr, grp,
+                                                            q.nstar_groups);
+                }
+                g = warp_sum(g);
                 if (lane == 0)
                     gpart[i] = g;
             }
@@ -537,9 +536,16 @@ k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out,
         // the global column from the star pass's partials (per block, or per
         // star unit of the single-launch aprod 2, whose work counter is reset
         // here for the next launch)
-        double t[1] = {0.0};
-        for (int b = threadIdx.x; b < ngpart; b += blockDim.x)
-            t[0] += gpart[b];
+        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int b = threadIdx.x;
+        for (; b + 7 * (int)blockDim.x < ngpart; b += 8 * blockDim.x) {  // 8 loads in flight
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                acc[u] += gpart[b + u * blockDim.x];
+        }
+        for (int u = 0; b < ngpart; b += blockDim.x, u++)
+            acc[u & 7] += gpart[b];
+        double t[1] = {((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]))};
         block_sum<1>(t);
         if (threadIdx.x == 0) {
             out[A.glb0] += t[0];
@@ -711,12 +717,18 @@ static cudaError_t launch_aprod2_split(const gsr_handle_t *h, const double *y, d
     return a2_rest(h, y, out, mode, h->grid_rows2, st);
 }
 
-// the unit queue of the single-launch aprod 2 for G lanes per star
+// the unit queue of the single-launch aprod 2 for G lanes per star; a star
+// unit is 4 star groups (16 stars at G = 8: about as many rows as one
+// attitude segment at the medium size)
+constexpr int kStarGroupsPerUnit = 4;
+
 A2Queue a2_queue(const gsr_handle_t *h, int G)
 {
     A2Queue q;
     q.ctr = h->d_a2ctr;
-    q.nstar_units = (h->sys.S + 32 / G - 1) / (32 / G);
+    q.star_k = kStarGroupsPerUnit;
+    q.nstar_groups = (h->sys.S + 32 / G - 1) / (32 / G);
+    q.nstar_units = (q.nstar_groups + q.star_k - 1) / q.star_k;
     q.ninstr_units = h->sys.I * h->isplit;
     const int64_t n[3] = {q.nstar_units, h->sys.nseg, q.ninstr_units};
     const int64_t tot = n[0] + n[1] + n[2];

@@ -38,8 +38,8 @@ constexpr int64_t kSmemInstrMax32 = 12288;  // binary32 instrument entries in sh
 // MODE 0: y (FP64) += A32 x32.  MODE 1 (CG): q32 = fl32(A32 x32), |q|^2
 // reduced and alpha = gamma / |q|^2 stored by the last block.
 // ---------------------------------------------------------------------------
-template <int MODE, bool SMEMX>
-__global__ void __launch_bounds__(kThreads)
+template <int MODE, bool SMEMX, int U>
+__global__ void __launch_bounds__(kThreads, U == 1 ? 4 : 2)
 k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
              float *__restrict__ q32, CgState *cg, double *partial, unsigned *counter)
 {
@@ -56,14 +56,14 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
     const int64_t mp = A.mp;
     const float xg = __ldg(x32 + A.glb0);
     double nrm = 0.0;
-    // two tiles per step: all loads of both rows are issued before the sums
-    for (int64_t t0 = warp; t0 < ntiles; t0 += 2 * nwarps) {
-        float vk[2][kNPar];
-        uint4 rc[2];
-        uint32_t st[2];
-        bool ok[2];
+    // U tiles per step: all loads of the U rows are issued before the sums
+    for (int64_t t0 = warp; t0 < ntiles; t0 += U * nwarps) {
+        float vk[U][kNPar];
+        uint4 rc[U];
+        uint32_t st[U];
+        bool ok[U];
 #pragma unroll
-        for (int u = 0; u < 2; u++) {
+        for (int u = 0; u < U; u++) {
             const int64_t t = t0 + u * nwarps;
             const int64_t r = (t << 5) + lane;
             ok[u] = (t < ntiles) && (r < A.m);
@@ -81,7 +81,7 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; u++) {
+        for (int u = 0; u < U; u++) {
             if (!ok[u])
                 continue;
             const int64_t r = ((t0 + u * nwarps) << 5) + lane;
@@ -131,27 +131,20 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
 // part written, instrumental/global accumulated into zeroed memory.
 // Instrumental products go to per-SM replicas (FP64 reductions in L2).
 // ---------------------------------------------------------------------------
-template <int G, int MODE, bool SMEM_INSTR>
-__global__ void __launch_bounds__(kThreads)
-k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict__ out,
-                   double *__restrict__ rep, int nrep)
+// Star-group part of warp `warp` of `nwarps` (binary32 products, double-float
+// sums): astrometric sums, instrumental products unless the sorted path
+// takes them, and this thread's share of the global column (returned).
+template <int G, int MODE, int IP>
+__device__ __forceinline__ double stars_body_f32(const SysView &A, const float *__restrict__ y32,
+                                                 double *__restrict__ out, double *myrep,
+                                                 double *s_ins, int64_t warp, int64_t nwarps)
 {
-    extern __shared__ double s_ins[];
-    __shared__ double s_red[kThreads / 32];
-    if (SMEM_INSTR) {
-        for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x)
-            s_ins[f] = 0.0;
-        __syncthreads();
-    }
     constexpr int GPW = 32 / G;
+    constexpr bool INS = IP != kIpSorted;
     const int lane = threadIdx.x & (G - 1);
     const int gw = (threadIdx.x & 31) / G;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t mp = A.mp;
-    double *myrep = rep + (int64_t)(blockIdx.x % nrep) * A.I;
     float gh = 0.f, gl = 0.f;
-
     for (int64_t s0 = warp * GPW; s0 < A.S; s0 += nwarps * GPW) {
         const int64_t s = s0 + gw;
         uint32_t r0 = 0, r1 = 0;
@@ -164,19 +157,21 @@ k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict_
         for (int k = 0; k < kNAstro; k++)
             ah[k] = al[k] = 0.f;
         for (uint32_t r = r0 + lane; r < r1; r += G) {
-            const uint4 rc = __ldcs(A.rec + r);
             const float *v = A.val32 + r;
             const float yi = __ldcs(y32 + r);
 #pragma unroll
             for (int k = 0; k < kNAstro; k++)
                 df_acc(ah[k], al[k], __fmul_rn(__ldcs(v + k * mp), yi));
+            if (INS) {
+                const uint4 rc = __ldcs(A.rec + r);
 #pragma unroll
-            for (int j = 0; j < kNInstr; j++) {
-                const float pr = __fmul_rn(__ldcs(v + (17 + j) * mp), yi);
-                if (SMEM_INSTR)
-                    atomicAdd(&s_ins[instr_at32(rc, j)], f2d(pr));
-                else
-                    atomicAdd(myrep + instr_at32(rc, j), f2d(pr));
+                for (int j = 0; j < kNInstr; j++) {
+                    const float pr = __fmul_rn(__ldcs(v + (17 + j) * mp), yi);
+                    if (IP == kIpSmem)
+                        atomicAdd(&s_ins[instr_at32(rc, j)], f2d(pr));
+                    else
+                        atomicAdd(myrep + instr_at32(rc, j), f2d(pr));
+                }
             }
             df_acc(gh, gl, __fmul_rn(__ldcs(v + 23 * mp), yi));
         }
@@ -199,7 +194,27 @@ k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict_
             }
         }
     }
-    double g = warp_sum(df_to_d(gh, gl));
+    return df_to_d(gh, gl);
+}
+
+template <int G, int MODE, bool SMEM_INSTR>
+__global__ void __launch_bounds__(kThreads)
+k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict__ out,
+                   double *__restrict__ rep, int nrep)
+{
+    extern __shared__ double s_ins[];
+    __shared__ double s_red[kThreads / 32];
+    if (SMEM_INSTR) {
+        for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x)
+            s_ins[f] = 0.0;
+        __syncthreads();
+    }
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double *myrep = rep + (int64_t)(blockIdx.x % nrep) * A.I;
+    const double gpart = stars_body_f32<G, MODE, SMEM_INSTR ? kIpSmem : kIpReplicas>(
+        A, y32, out, myrep, s_ins, warp, nwarps);
+    double g = warp_sum(gpart);
     if ((threadIdx.x & 31) == 0)
         s_red[threadIdx.x >> 5] = g;
     __syncthreads();
@@ -219,12 +234,10 @@ k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict_
 }
 
 // inner aprod 2, attitude part over the offset-sorted binary32 copy
-__global__ void __launch_bounds__(kThreads)
-k_att_segments_f32(SysView A, const float *__restrict__ y32, double *__restrict__ S)
+__device__ __forceinline__ void att_body_f32(const SysView &A, const float *__restrict__ y32,
+                                             double *__restrict__ S, int64_t warp, int64_t nwarps)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t mp = A.mp;
     for (int64_t o = warp; o < A.nseg; o += nwarps) {
         const uint32_t e0 = A.seg[o], e1 = A.seg[o + 1];
@@ -272,6 +285,104 @@ k_att_segments_f32(SysView A, const float *__restrict__ y32, double *__restrict_
         const int kk = lane >> 1;
         if ((lane & 1) == 0 && kk < kNAtt)
             S[o * kNAtt + kk] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_att_segments_f32(SysView A, const float *__restrict__ y32, double *__restrict__ S)
+{
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    att_body_f32(A, y32, S, warp, nwarps);
+}
+
+// inner aprod 2, instrumental part over the instrument-sorted binary32 copy:
+// chunk q of instrument f (unit w = f nsplit + q), four gathers in flight
+// per lane, double-float sums, chunk total to part[q I + f]
+__device__ __forceinline__ void instr_body_f32(const SysView &A, const uint32_t *__restrict__ iseg,
+                                               const uint32_t *__restrict__ irow,
+                                               const float *__restrict__ ival32,
+                                               const float *__restrict__ y32,
+                                               double *__restrict__ part, int nsplit, int64_t warp,
+                                               int64_t nwarps)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t w = warp; w < A.I * nsplit; w += nwarps) {
+        const int64_t f = w / nsplit;
+        const int q = (int)(w - f * nsplit);
+        const uint32_t s0 = iseg[f];
+        const uint64_t len = iseg[f + 1] - s0;
+        const uint32_t e1 = s0 + (uint32_t)(len * (q + 1) / nsplit);
+        uint32_t e = s0 + (uint32_t)(len * q / nsplit) + lane;
+        float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+        for (; e + 96 < e1; e += 128) {
+            uint32_t r[4];
+            float v[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                r[u] = __ldcs(irow + e + 32 * u);
+                v[u] = __ldcs(ival32 + e + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                yv[u] = __ldg(y32 + r[u]);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                df_acc(h[u], l[u], __fmul_rn(v[u], yv[u]));
+        }
+        for (int u = 0; e < e1; e += 32, u++)
+            df_acc(h[u & 3], l[u & 3], __fmul_rn(__ldcs(ival32 + e), __ldg(y32 + __ldcs(irow + e))));
+        const double t = warp_sum((df_to_d(h[0], l[0]) + df_to_d(h[1], l[1])) +
+                                  (df_to_d(h[2], l[2]) + df_to_d(h[3], l[3])));
+        if (lane == 0)
+            part[(int64_t)q * A.I + f] = t;
+    }
+}
+
+// inner aprod 2 in one launch (sorted instrumental path), the binary32 form
+// of k_aprod2_fused: units of the three kinds from one work queue, one
+// global-column partial per star unit
+template <int G, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_aprod2_f32_fused(SysView A, const float *__restrict__ y32, double *__restrict__ out,
+                   double *__restrict__ S, const uint32_t *__restrict__ iseg,
+                   const uint32_t *__restrict__ irow, const float *__restrict__ ival32,
+                   double *__restrict__ part, int nsplit, double *__restrict__ gpart, A2Queue q)
+{
+    const int lane = threadIdx.x & 31;
+    const int L = q.ns + q.na + q.ni;
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0)
+            u = atomicAdd(q.ctr, 1ull);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if ((int64_t)u >= q.total)
+            break;
+        const int64_t c = (int64_t)u / L;
+        const int slot = (int)((int64_t)u - c * L);
+        if (slot < q.ns) {
+            const int64_t i = c * q.ns + slot;
+            if (i < q.nstar_units) {
+                double g = 0.0;
+                for (int k = 0; k < q.star_k; k++) {
+                    const int64_t grp = i * q.star_k + k;
+                    if (grp < q.nstar_groups)
+                        g += stars_body_f32<G, MODE, kIpSorted>(A, y32, out, nullptr, nullptr, grp,
+                                                                q.nstar_groups);
+                }
+                g = warp_sum(g);
+                if (lane == 0)
+                    gpart[i] = g;
+            }
+        } else if (slot < q.ns + q.na) {
+            const int64_t i = c * q.na + (slot - q.ns);
+            if (i < A.nseg)
+                att_body_f32(A, y32, S, i, A.nseg);
+        } else {
+            const int64_t i = c * q.ni + (slot - q.ns - q.na);
+            if (i < q.ninstr_units)
+                instr_body_f32(A, iseg, irow, ival32, y32, part, nsplit, i, q.ninstr_units);
+        }
     }
 }
 
@@ -421,18 +532,22 @@ __global__ void k_count_pos(const double *__restrict__ a, int64_t n, double *par
 // ---------------------------------------------------------------------------
 bool x32_in_smem(const gsr_handle_t *h) { return h->sys.I <= kSmemInstrMax32; }
 
+// rows in flight per lane of the binary32 aprod 1 (see k_aprod1_f32)
+constexpr int kA1f32Tiles = 2;
+
 template <int MODE>
 static cudaError_t a1f_launch(const gsr_handle_t *h, const float *x32, double *y, float *q32,
                               cudaStream_t st)
 {
     double *part = h->d_partial + kRedU * kPartialsPerKind;
     unsigned *cnt = h->d_counter + kRedU;
+    constexpr int U = kA1f32Tiles;
     if (x32_in_smem(h))
-        k_aprod1_f32<MODE, true><<<h->grid_rows32, kThreads, (size_t)h->sys.I * sizeof(float), st>>>(
-            h->sys, x32, y, q32, h->d_cg, part, cnt);
+        k_aprod1_f32<MODE, true, U><<<h->grid_rows32, kThreads, (size_t)h->sys.I * sizeof(float),
+                                      st>>>(h->sys, x32, y, q32, h->d_cg, part, cnt);
     else
-        k_aprod1_f32<MODE, false><<<h->grid_rows32, kThreads, 0, st>>>(h->sys, x32, y, q32, h->d_cg,
-                                                                        part, cnt);
+        k_aprod1_f32<MODE, false, U><<<h->grid_rows32, kThreads, 0, st>>>(h->sys, x32, y, q32,
+                                                                           h->d_cg, part, cnt);
     return cudaGetLastError();
 }
 
@@ -440,6 +555,19 @@ template <int MODE>
 static cudaError_t a2f_launch(const gsr_handle_t *h, const float *y32, double *out, cudaStream_t st)
 {
     const int G = 8;
+    if (h->ipath == kIpSorted && h->a2_fused) {
+        const A2Queue q = a2_queue(h, G);
+        k_aprod2_f32_fused<G, MODE><<<h->grid_fused32, kThreads, 0, st>>>(
+            h->sys, y32, out, h->d_attS, h->d_iseg, h->d_irow, h->d_ival32, h->d_ipart, h->isplit,
+            h->d_gpart, q);
+        const int nb_att = (int)((3 * h->sys.D + kThreads - 1) / kThreads < 4 * h->nsm
+                                     ? (3 * h->sys.D + kThreads - 1) / kThreads
+                                     : 4 * h->nsm);
+        const int nb_ins = (int)((h->sys.I + kThreads / 32 - 1) / (kThreads / 32));
+        launch_att_combine(h, out, nb_att, nb_ins, h->d_ipart, h->isplit, h->d_gpart,
+                           (int)q.nstar_units, MODE == kA2Accumulate, st, h->d_a2ctr);
+        return cudaGetLastError();
+    }
     const bool smem = instr_in_smem(h);
     if (smem)
         k_aprod2_f32_stars<G, MODE, true><<<h->grid_rows2_32, kThreads,
@@ -619,13 +747,24 @@ int aprod1_f32_grid(const gsr_handle_t *h)
     int occ = 0;
     cudaError_t e = x32_in_smem(h)
                         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                              &occ, k_aprod1_f32<1, true>, kThreads, (size_t)h->sys.I * sizeof(float))
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1_f32<1, false>,
-                                                                        kThreads, 0);
+                              &occ, k_aprod1_f32<1, true, kA1f32Tiles>, kThreads,
+                              (size_t)h->sys.I * sizeof(float))
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                              &occ, k_aprod1_f32<1, false, kA1f32Tiles>, kThreads, 0);
     if (e != cudaSuccess || occ <= 0)
         return -1;
     int64_t g = (int64_t)h->nsm * occ;
     return (int)(g > kMaxPartials ? kMaxPartials : g);
+}
+
+int aprod2_f32_fused_grid(const gsr_handle_t *h)
+{
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, k_aprod2_f32_fused<8, kA2Overwrite>, kThreads, 0);
+    if (e != cudaSuccess || occ <= 0)
+        return -1;
+    return h->nsm * occ;
 }
 
 int aprod2_f32_grid(const gsr_handle_t *h)
