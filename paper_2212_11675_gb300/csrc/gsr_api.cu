@@ -137,7 +137,7 @@ static void release(gsr_handle_t *h)
         cudaFreeHost(h->h_onorm);
     if (h->cap_stream)
         cudaStreamDestroy(h->cap_stream);
-    void *dev[] = {h->d_star_ptr, h->d_rec, h->d_val, h->d_tile_star, h->d_tval, h->d_perm,
+    void *dev[] = {h->d_star_ptr, h->d_rec, h->d_val, h->d_tile_star, h->d_sdelta, h->d_tval, h->d_perm,
                    h->d_seg, h->d_attS, h->d_irep, h->d_p, h->d_u, h->d_v, h->d_w, h->d_z,
                    h->d_var, h->d_q, h->d_vp, h->d_vt, h->d_bstage, h->d_xstage, h->d_sestage,
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err,
@@ -271,6 +271,7 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     TRY(dalloc(h, &h->d_rec, m));
     TRY(dalloc(h, &h->d_val, kNPar * mp));
     TRY(dalloc(h, &h->d_tile_star, ntiles));
+    TRY(dalloc(h, &h->d_sdelta, m));
     TRY(dalloc(h, &h->d_tval, (int64_t)kNAtt * mp));
     TRY(dalloc(h, &h->d_perm, m));
     TRY(dalloc(h, &h->d_seg, A.nseg + 1));
@@ -297,6 +298,7 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     A.rec = h->d_rec;
     A.val = h->d_val;
     A.tile_star = h->d_tile_star;
+    A.sdelta = h->d_sdelta;
     A.tval = h->d_tval;
     A.perm = h->d_perm;
     A.seg = h->d_seg;

@@ -82,9 +82,7 @@ k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ld
         const int64_t r = (t << 5) + lane;
         if (r >= A.m)
             continue;
-        uint32_t s = A.tile_star[t];
-        while ((int64_t)A.star_ptr[s + 1] <= r)
-            ++s;
+        const uint32_t s = star_of_row(A, t, r);
         const uint4 rc = __ldcs(A.rec + r);
         float h[KT], l[KT];
 #pragma unroll

@@ -26,6 +26,7 @@ struct SysView {
     const float *val32;        // [24][mp] binary32 copy (mixed precision), or null
     const float *tval32;       // [12][mp] binary32 offset-sorted attitude copy, or null
     const uint32_t *tile_star; // [ceil(m/32)] star of the first row of each 32-row tile
+    const uint16_t *sdelta;    // [m] star of row r minus tile_star[r/32]; 0xffff: walk on
     // attitude values re-ordered by attitude offset (stable in the row index):
     // entry e is row perm[e]; offset o owns entries seg[o] .. seg[o+1]-1
     const double *tval;        // [12][mp]
@@ -36,6 +37,19 @@ struct SysView {
     int64_t att0, ins0, glb0;  // first column of each section
     int64_t nseg;              // D-3 attitude offsets
 };
+
+// Star of row r of tile t = r / 32: the tile's star plus the stored delta
+// (both loads independent of each other); a saturated delta continues with
+// the walk over star_ptr, which ends at a star < S because r < m.
+__device__ __forceinline__ uint32_t star_of_row(const SysView &A, int64_t t, int64_t r)
+{
+    const uint32_t d = __ldcs(A.sdelta + r);
+    uint32_t s = __ldg(A.tile_star + t) + d;
+    if (d == 0xffffu)
+        while ((int64_t)A.star_ptr[s + 1] <= r)
+            ++s;
+    return s;
+}
 
 // LSQR scalars kept on the device (Paige & Saunders 1982 notation).
 struct SolveState {
@@ -131,6 +145,7 @@ struct gsr_handle_t {
     uint4 *d_rec = nullptr;
     double *d_val = nullptr;
     uint32_t *d_tile_star = nullptr;
+    uint16_t *d_sdelta = nullptr;
     double *d_tval = nullptr;
     uint32_t *d_perm = nullptr, *d_seg = nullptr;
     double *d_attS = nullptr;           // [nseg][12] attitude segment sums

@@ -70,9 +70,7 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
     for (int64_t t = warp; t < ntiles; t += nwarps) {
         const int64_t r = (t << 5) + lane;
         if (r < A.m) {
-            uint32_t s = A.tile_star[t];
-            while ((int64_t)A.star_ptr[s + 1] <= r)  // ends at s < S because r < m
-                ++s;
+            const uint32_t s = star_of_row(A, t, r);
             const uint4 rc = __ldcs(A.rec + r);
             const double *v = A.val + r;
             double vk[kNPar];
@@ -897,9 +895,24 @@ __global__ void k_tile_star(SysView A, uint32_t *tile_star)
     }
 }
 
+// sdelta[r] = star of row r - tile_star[r / 32], saturated at 0xffff
+__global__ void k_star_delta(SysView A, const uint32_t *__restrict__ tile_star,
+                             uint16_t *__restrict__ sdelta)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.m;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s0 = tile_star[r >> 5];
+        uint32_t s = s0;
+        while ((int64_t)A.star_ptr[s + 1] <= r && s - s0 < 0xffffu)
+            ++s;
+        sdelta[r] = (uint16_t)(s - s0);
+    }
+}
+
 cudaError_t launch_tile_star(const gsr_handle_t *h, cudaStream_t st)
 {
     k_tile_star<<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_tile_star);
+    k_star_delta<<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_tile_star, h->d_sdelta);
     return cudaGetLastError();
 }
 

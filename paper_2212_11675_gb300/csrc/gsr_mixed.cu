@@ -69,10 +69,7 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
             ok[u] = (t < ntiles) && (r < A.m);
             st[u] = 0;
             if (ok[u]) {
-                uint32_t s = A.tile_star[t];
-                while ((int64_t)A.star_ptr[s + 1] <= r)
-                    ++s;
-                st[u] = s;
+                st[u] = star_of_row(A, t, r);
                 rc[u] = __ldcs(A.rec + r);
                 const float *v = A.val32 + r;
 #pragma unroll

@@ -12,7 +12,7 @@ import pytest
 import oracle
 from paper_2212_11675_gb300 import _lib, gen
 from tests._dense import small
-from tests._systems import drop_stars, ragged
+from tests._systems import drop_stars, empty_run, ragged
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -64,6 +64,23 @@ def test_aprod_parity_ragged_and_empty_stars():
     assert (np.diff(sys.star_ptr.astype(np.int64)) == 0).any()
     check_aprods(sys, 8)
     check_aprods(drop_stars(gen.make("tiny"), [0, 1, 500, 999]), 16, seed=3)
+
+
+def test_aprod_parity_long_run_of_empty_stars():
+    # more than 65535 empty stars inside one 32-row tile: the stored per-row
+    # star delta saturates and the kernels walk on over star_ptr
+    sys = empty_run()
+    assert sys.m <= 32
+    check_aprods(sys, 8)
+    with _solver(sys, precision=_lib.GSR_PREC_MIXED) as s:
+        x = np.random.default_rng(4).standard_normal(sys.n)
+        yd = torch.zeros(sys.m, dtype=torch.float64, device=DEV)
+        s.aprod1_f32(torch.tensor(x, device=DEV), yd)
+        ref = oracle.aprod1_f32(sys, x)
+        absys = gen.GaiaSystem(sys.n_stars, sys.n_dfa, sys.n_instr, sys.star_ptr, sys.attoff,
+                               sys.instr, np.abs(sys.values))
+        bound = 1e-12 * oracle.aprod1_f32(absys, np.abs(x))  # of sum |products|
+        assert np.all(np.abs(yd.cpu().numpy() - ref) <= bound)
 
 
 def test_aprod_parity_instruments_beyond_shared_memory():
