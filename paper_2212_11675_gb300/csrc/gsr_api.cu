@@ -141,7 +141,7 @@ static void release(gsr_handle_t *h)
                    h->d_seg, h->d_attS, h->d_irep, h->d_p, h->d_u, h->d_v, h->d_w, h->d_z,
                    h->d_var, h->d_q, h->d_vp, h->d_vt, h->d_bstage, h->d_xstage, h->d_sestage,
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err,
-                   h->d_val32, h->d_tval32, h->d_x32, h->d_q32, h->d_c, h->d_s, h->d_d, h->d_t,
+                   h->d_val32, h->d_tval32, h->d_x32, h->d_xatt4, h->d_q32, h->d_c, h->d_s, h->d_d, h->d_t,
                    h->d_zc, h->d_xm, h->d_r, h->d_xneg, h->d_onorm, h->d_cg, h->d_cgargs,
                    h->d_xp64, h->d_q64, h->d_iseg, h->d_irow, h->d_ival32, h->d_ival, h->d_ipart, h->d_gpart, h->d_a2ctr, h->d_bX32, h->d_bQ32,
                    h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT, h->d_bS, h->d_bXcm,
@@ -224,6 +224,8 @@ static int create_mixed(gsr_handle_t *h, cudaStream_t st)
     TRY(dalloc(h, &h->d_tval32, (int64_t)kNAtt * mp));
     TRY(dalloc(h, &h->d_ival32, kNInstr * m));
     TRY(dalloc(h, &h->d_x32, n));
+    TRY(dalloc(h, &h->d_xatt4, 3 * A.D * 4));
+    CK(cudaMemset(h->d_xatt4, 0, 3 * A.D * 4 * sizeof(float)));
     TRY(dalloc(h, &h->d_q32, m));
     CK(launch_to_f32(h, h->d_val, h->d_val32, kNPar * mp, st));
     CK(launch_to_f32(h, h->d_tval, h->d_tval32, kNAtt * mp, st));

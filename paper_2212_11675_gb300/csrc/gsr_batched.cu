@@ -74,10 +74,10 @@ k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ld
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t ntiles = (A.m + 31) >> 5;
     const int64_t mp = A.mp;
-    double nrm[KT];
+    float nh[KT], nl[KT];  // |Q[:, c]|^2 of this thread (double-float)
 #pragma unroll
     for (int c = 0; c < KT; c++)
-        nrm[c] = 0.0;
+        nh[c] = nl[c] = 0.f;
     for (int64_t t = warp; t < ntiles; t += nwarps) {
         const int64_t r = (t << 5) + lane;
         if (r >= A.m)
@@ -112,10 +112,15 @@ k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ld
         for (int c = 0; c < KT; c++) {
             const float qv = __fadd_rn(h[c], l[c]);
             q[c] = qv;
-            const double qd = f2d(qv);
-            nrm[c] = fma(qd, qd, nrm[c]);
+            const float pq = __fmul_rn(qv, qv);  // q^2 = pq + fma(q, q, -pq) exactly
+            df_acc(nh[c], nl[c], pq);
+            nl[c] = __fadd_rn(nl[c], __fmaf_rn(qv, qv, -pq));
         }
     }
+    double nrm[KT];
+#pragma unroll
+    for (int c = 0; c < KT; c++)
+        nrm[c] = df_to_d(nh[c], nl[c]);
     if (grid_reduce_cols<KT>(nrm, partial, counter) && threadIdx.x == 0) {
 #pragma unroll
         for (int c = 0; c < KT; c++) {
@@ -174,17 +179,24 @@ k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ld
             for (int c = 0; c < KT; c++)
                 df_acc(gh[c], gl[c], __fmul_rn(ag, yv[c]));
         }
+        // the star's 5 KT sums over its G lanes: double-float reduce-scatter
+        // of the values padded to P (value v = k KT + c)
+        constexpr int NV = kNAstro * KT;
+        constexpr int P = NV <= 8 ? 8 : (NV <= 16 ? 16 : 32);
+        float rh[P], rl[P];
 #pragma unroll
-        for (int k = 0; k < kNAstro; k++) {
+        for (int v = 0; v < P; v++) {
+            rh[v] = v < NV ? ah[v / KT][v % KT] : 0.f;
+            rl[v] = v < NV ? al[v / KT][v % KT] : 0.f;
+        }
+        df_reduce_scatter<P, G>(rh, rl, lane);
+        constexpr int PER = P >= G ? P / G : 1;
 #pragma unroll
-            for (int c = 0; c < KT; c++) {
-                double t = df_to_d(ah[k][c], al[k][c]);
-#pragma unroll
-                for (int off = G / 2; off > 0; off >>= 1)
-                    t += __shfl_xor_sync(0xffffffffu, t, off);
-                if (lane == 0 && s < A.S)
-                    T[((int64_t)kNAstro * s + k) * ldk + c0 + c] = t;
-            }
+        for (int k = 0; k < PER; k++) {
+            const int v = P >= G ? lane * PER + k : lane / (G / P);
+            const bool owner = P >= G || (lane % (G / P)) == 0;
+            if (owner && v < NV && s < A.S)
+                T[((int64_t)kNAstro * s + v / KT) * ldk + c0 + v % KT] = df_to_d(rh[k], rl[k]);
         }
     }
 #pragma unroll
@@ -234,33 +246,12 @@ k_b_att(SysView A, const float *__restrict__ Y, double *__restrict__ S, int ldk,
                     df_acc(h[j * KT + c], l[j * KT + c], __fmul_rn(v, yv[c]));
             }
         }
-        // reduce-scatter of NV sums over the warp (NV is a power of two <= 32)
-        double r[NV];
-#pragma unroll
-        for (int k = 0; k < NV; k++)
-            r[k] = df_to_d(h[k], l[k]);
-#pragma unroll
-        for (int half = NV / 2, off = 16; half >= 1; half >>= 1, off >>= 1) {
-            const bool upper = (lane & off) != 0;
-#pragma unroll
-            for (int k = 0; k < half; k++) {
-                const double send = upper ? r[k] : r[k + half];
-                const double keep = upper ? r[k + half] : r[k];
-                r[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-            }
-        }
-        // the first log2(NV) exchanges used offsets 16, 8, ...; lanes that
-        // differ only in the lower bits hold partial sums of the same index
-        constexpr int LOGNV = (NV >= 32) ? 5 : (NV >= 16) ? 4 : (NV >= 8) ? 3 : (NV >= 4) ? 2 : 1;
-        constexpr int REST = 32 >> LOGNV;
-        double tot = r[0];
-#pragma unroll
-        for (int off = REST / 2; off > 0; off >>= 1)
-            tot += __shfl_xor_sync(0xffffffffu, tot, off);
-        // index held by this lane: bits 4 .. 5-LOGNV of the lane, high first
-        const int idx = lane / REST;
+        // double-float reduce-scatter of the NV sums (a power of two <= 32)
+        // over the warp: lane l ends with the total of index l / (32 / NV)
+        df_reduce_scatter<NV, 32>(h, l, lane);
+        constexpr int REST = 32 / NV;
         if ((lane % REST) == 0)
-            S[(o * 3 + a) * NV + idx] = tot;
+            S[(o * 3 + a) * NV + lane / REST] = df_to_d(h[0], l[0]);
     }
 }
 
@@ -336,9 +327,9 @@ k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restri
         }
 #pragma unroll
         for (int c = 0; c < KT; c++) {
-            const double t = warp_sum(df_to_d(h[c], l[c]));
+            df_warp_sum(h[c], l[c]);
             if (lane == 0)
-                part[(f * kInstrSplit + q) * KT + c] = t;
+                part[(f * kInstrSplit + q) * KT + c] = df_to_d(h[c], l[c]);
         }
     }
 }
@@ -567,6 +558,18 @@ static cudaError_t b_aprod1(const gsr_handle_t *h, const float *X, float *Q, int
     return cudaGetLastError();
 }
 
+// all resident blocks of the star pass for this column tile and lane count
+template <int KS, int G>
+static int stars_grid(const gsr_handle_t *h)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_b_stars<KS, G>, kThreads, 0) !=
+            cudaSuccess ||
+        occ <= 0)
+        occ = 1;
+    return h->nsm * occ;
+}
+
 template <int KT>
 static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, int ldk, int c0,
                             cudaStream_t st)
@@ -576,9 +579,9 @@ static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, in
     constexpr int KS = (KT > 4) ? 4 : KT;
     for (int cs = c0; cs < c0 + KT; cs += KS) {
         switch (h->b_lanes) {
-        case 8: k_b_stars<KS, 8><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
-        case 32: k_b_stars<KS, 32><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
-        default: k_b_stars<KS, 16><<<h->grid_b2, kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
+        case 8: k_b_stars<KS, 8><<<stars_grid<KS, 8>(h), kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
+        case 32: k_b_stars<KS, 32><<<stars_grid<KS, 32>(h), kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
+        default: k_b_stars<KS, 16><<<stars_grid<KS, 16>(h), kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
         }
         k_b_att<KS><<<h->grid_att, kThreads, 0, st>>>(h->sys, Y, h->d_bS, ldk, cs);
         k_b_att_combine<KS><<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_bS, T, ldk, cs);
@@ -766,13 +769,7 @@ int batched_grid_rows(const gsr_handle_t *h)
 
 int batched_grid_stars(const gsr_handle_t *h)
 {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_b_stars<8, 16>, kThreads, 0) !=
-            cudaSuccess ||
-        occ <= 0)
-        return -1;
-    int64_t g = (int64_t)h->nsm * occ;
-    return (int)(g > kMaxPartials ? kMaxPartials : g);
+    return stars_grid<4, 16>(h);
 }
 
 }  // namespace gsr

@@ -166,6 +166,7 @@ struct gsr_handle_t {
     // mixed precision
     float *d_val32 = nullptr, *d_tval32 = nullptr;
     float *d_x32 = nullptr, *d_q32 = nullptr;
+    float *d_xatt4 = nullptr;           // [3D][4] attitude part of x32 as one float4 per offset
     double *d_c = nullptr, *d_s = nullptr, *d_d = nullptr, *d_t = nullptr, *d_zc = nullptr;
     double *d_xm = nullptr, *d_r = nullptr, *d_xneg = nullptr, *d_onorm = nullptr;
     gsr::CgState *d_cg = nullptr, *h_cg = nullptr;

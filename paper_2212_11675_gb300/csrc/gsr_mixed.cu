@@ -40,8 +40,9 @@ constexpr int64_t kSmemInstrMax32 = 12288;  // binary32 instrument entries in sh
 // ---------------------------------------------------------------------------
 template <int MODE, bool SMEMX, int U>
 __global__ void __launch_bounds__(kThreads, U == 1 ? 4 : 2)
-k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
-             float *__restrict__ q32, CgState *cg, double *partial, unsigned *counter)
+k_aprod1_f32(SysView A, const float *__restrict__ x32, const float4 *__restrict__ xatt4,
+             double *__restrict__ y, float *__restrict__ q32, CgState *cg, double *partial,
+             unsigned *counter)
 {
     extern __shared__ float s_x32[];
     if (SMEMX) {
@@ -55,7 +56,7 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
     const int64_t ntiles = (A.m + 31) >> 5;
     const int64_t mp = A.mp;
     const float xg = __ldg(x32 + A.glb0);
-    double nrm = 0.0;
+    float nh = 0.f, nl = 0.f;  // ||q||^2 of this thread (double-float)
     // U tiles per step: all loads of the U rows are issued before the sums
     for (int64_t t0 = warp; t0 < ntiles; t0 += U * nwarps) {
         float vk[U][kNPar];
@@ -87,12 +88,14 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
 #pragma unroll
             for (int k = 0; k < kNAstro; k++)
                 df_acc(h0, l0, __fmul_rn(vk[u][k], __ldg(xs + k)));
-            const float *xa = x32 + A.att0 + rc[u].x;
 #pragma unroll
-            for (int a = 0; a < 3; a++)
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    df_acc(h1, l1, __fmul_rn(vk[u][5 + 4 * a + j], __ldg(xa + a * A.D + j)));
+            for (int a = 0; a < 3; a++) {
+                const float4 xa = __ldg(xatt4 + a * A.D + rc[u].x);
+                df_acc(h1, l1, __fmul_rn(vk[u][5 + 4 * a + 0], xa.x));
+                df_acc(h1, l1, __fmul_rn(vk[u][5 + 4 * a + 1], xa.y));
+                df_acc(h1, l1, __fmul_rn(vk[u][5 + 4 * a + 2], xa.z));
+                df_acc(h1, l1, __fmul_rn(vk[u][5 + 4 * a + 3], xa.w));
+            }
 #pragma unroll
             for (int j = 0; j < kNInstr; j++) {
                 const uint32_t f = instr_at32(rc[u], j);
@@ -107,13 +110,16 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, double *__restrict__ y,
             } else {
                 const float qv = __fadd_rn(h0, l0);
                 q32[r] = qv;
-                const double qd = f2d(qv);
-                nrm = fma(qd, qd, nrm);
+                // q^2 = pq + eq exactly (product error by FMA), accumulated
+                // in double-float on the FP32 pipe
+                const float pq = __fmul_rn(qv, qv);
+                df_acc(nh, nl, pq);
+                nl = __fadd_rn(nl, __fmaf_rn(qv, qv, -pq));
             }
         }
     }
     if (MODE == 1) {
-        double v1[1] = {nrm};
+        double v1[1] = {df_to_d(nh, nl)};
         if (grid_reduce<1>(v1, partial, counter) && threadIdx.x == 0) {
             const double xi = v1[0];
             cg->xi = xi;
@@ -136,6 +142,7 @@ __device__ __forceinline__ double stars_body_f32(const SysView &A, const float *
                                                  double *__restrict__ out, double *myrep,
                                                  double *s_ins, int64_t warp, int64_t nwarps)
 {
+    static_assert(G >= kNAstro, "a star group needs a lane per astrometric sum");
     constexpr int GPW = 32 / G;
     constexpr bool INS = IP != kIpSorted;
     const int lane = threadIdx.x & (G - 1);
@@ -172,23 +179,30 @@ __device__ __forceinline__ double stars_body_f32(const SysView &A, const float *
             }
             df_acc(gh, gl, __fmul_rn(__ldcs(v + 23 * mp), yi));
         }
-        double a0 = df_to_d(ah[0], al[0]), a1 = df_to_d(ah[1], al[1]), a2 = df_to_d(ah[2], al[2]);
-        double a3 = df_to_d(ah[3], al[3]), a4 = df_to_d(ah[4], al[4]);
+        // the star's five sums over its G lanes, in double-float
 #pragma unroll
         for (int off = G / 2; off > 0; off >>= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, off);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, off);
-            a2 += __shfl_xor_sync(0xffffffffu, a2, off);
-            a3 += __shfl_xor_sync(0xffffffffu, a3, off);
-            a4 += __shfl_xor_sync(0xffffffffu, a4, off);
-        }
-        if (lane == 0 && s < A.S) {
-            double *xs = out + kNAstro * s;
-            if (MODE == kA2Accumulate) {
-                xs[0] += a0; xs[1] += a1; xs[2] += a2; xs[3] += a3; xs[4] += a4;
-            } else {
-                xs[0] = a0; xs[1] = a1; xs[2] = a2; xs[3] = a3; xs[4] = a4;
+#pragma unroll
+            for (int k = 0; k < kNAstro; k++) {
+                const float oh = __shfl_xor_sync(0xffffffffu, ah[k], off);
+                const float ol = __shfl_xor_sync(0xffffffffu, al[k], off);
+                df_add(ah[k], al[k], oh, ol);
             }
+        }
+        if (lane < kNAstro && s < A.S) {
+            // lane k writes sum k (all lanes of the group hold all five)
+            float kh = ah[0], kl = al[0];
+#pragma unroll
+            for (int k = 1; k < kNAstro; k++)
+                if (lane == k) {
+                    kh = ah[k];
+                    kl = al[k];
+                }
+            double *xs = out + kNAstro * s + lane;
+            if (MODE == kA2Accumulate)
+                *xs += df_to_d(kh, kl);
+            else
+                *xs = df_to_d(kh, kl);
         }
     }
     return df_to_d(gh, gl);
@@ -264,24 +278,34 @@ __device__ __forceinline__ void att_body_f32(const SysView &A, const float *__re
             for (int k = 0; k < kNAtt; k++)
                 df_acc(h[k], l[k], __fmul_rn(__ldcs(A.tval32 + k * mp + e), yi));
         }
-        double r16[16];
+        // reduce-scatter over the warp in double-float (FP32 pipe): after
+        // the butterfly, lane pair (2k, 2k+1) holds sum k
+        float rh[16], rl[16];
 #pragma unroll
-        for (int k = 0; k < 16; k++)
-            r16[k] = k < kNAtt ? df_to_d(h[k], l[k]) : 0.0;
+        for (int k = 0; k < 16; k++) {
+            rh[k] = k < kNAtt ? h[k] : 0.f;
+            rl[k] = k < kNAtt ? l[k] : 0.f;
+        }
 #pragma unroll
         for (int half = 8; half >= 1; half >>= 1) {
             const bool upper = (lane & (2 * half)) != 0;
 #pragma unroll
             for (int k = 0; k < half; k++) {
-                const double send = upper ? r16[k] : r16[k + half];
-                const double keep = upper ? r16[k + half] : r16[k];
-                r16[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * half);
+                const float sh = upper ? rh[k] : rh[k + half];
+                const float sl = upper ? rl[k] : rl[k + half];
+                float kh = upper ? rh[k + half] : rh[k];
+                float kl = upper ? rl[k + half] : rl[k];
+                df_add(kh, kl, __shfl_xor_sync(0xffffffffu, sh, 2 * half),
+                       __shfl_xor_sync(0xffffffffu, sl, 2 * half));
+                rh[k] = kh;
+                rl[k] = kl;
             }
         }
-        const double tot = r16[0] + __shfl_xor_sync(0xffffffffu, r16[0], 1);
+        float th = rh[0], tl = rl[0];
+        df_add(th, tl, __shfl_xor_sync(0xffffffffu, rh[0], 1), __shfl_xor_sync(0xffffffffu, rl[0], 1));
         const int kk = lane >> 1;
         if ((lane & 1) == 0 && kk < kNAtt)
-            S[o * kNAtt + kk] = tot;
+            S[o * kNAtt + kk] = df_to_d(th, tl);
     }
 }
 
@@ -329,10 +353,12 @@ __device__ __forceinline__ void instr_body_f32(const SysView &A, const uint32_t 
         }
         for (int u = 0; e < e1; e += 32, u++)
             df_acc(h[u & 3], l[u & 3], __fmul_rn(__ldcs(ival32 + e), __ldg(y32 + __ldcs(irow + e))));
-        const double t = warp_sum((df_to_d(h[0], l[0]) + df_to_d(h[1], l[1])) +
-                                  (df_to_d(h[2], l[2]) + df_to_d(h[3], l[3])));
+        df_add(h[0], l[0], h[1], l[1]);
+        df_add(h[2], l[2], h[3], l[3]);
+        df_add(h[0], l[0], h[2], l[2]);
+        df_warp_sum(h[0], l[0]);
         if (lane == 0)
-            part[(int64_t)q * A.I + f] = t;
+            part[(int64_t)q * A.I + f] = df_to_d(h[0], l[0]);
     }
 }
 
@@ -395,6 +421,34 @@ __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, in
         b[j] = __double2float_rn(a[j]);
 }
 
+// Attitude part of a binary32 x, also stored as one float4 per (axis a,
+// offset o) holding x[a D + o .. a D + o + 3], so that a row reads its 12
+// attitude entries with 3 aligned vector loads.  Entry j of x (attitude
+// column a D + o) is component jj of the float4 of offset o - jj.
+__device__ __forceinline__ void att4_scatter(float *__restrict__ xatt4, int64_t j, float v,
+                                             int64_t att0, int64_t D)
+{
+    const int64_t c = j - att0;
+    if (c < 0 || c >= 3 * D)
+        return;
+    const int64_t a = c / D, o = c - a * D;
+#pragma unroll
+    for (int jj = 0; jj < 4; jj++)
+        if (o - jj >= 0)
+            xatt4[((a * D + o - jj) << 2) + jj] = v;
+}
+
+// API form: x32 = fl32(x) and its attitude float4 copy
+__global__ void k_x_to_f32(const double *__restrict__ x, float *__restrict__ x32,
+                           float *__restrict__ xatt4, int64_t n, int64_t att0, int64_t D)
+{
+    for (int64_t j = gtid32(); j < n; j += gstride32()) {
+        const float v = __double2float_rn(x[j]);
+        x32[j] = v;
+        att4_scatter(xatt4, j, v, att0, D);
+    }
+}
+
 // s = p o c, d = s, z = 0, xp32 = fl32(p o d), gamma = |s|^2; clears the
 // instrumental/global part of t for the first inner aprod 2
 template <typename XT>
@@ -402,7 +456,8 @@ __global__ void __launch_bounds__(kThreads)
 k_cg_init(const double *__restrict__ p, const double *__restrict__ c, double *__restrict__ s,
           double *__restrict__ d, double *__restrict__ z, XT *__restrict__ xp32,
           double *__restrict__ t, int64_t n, int64_t ins0, CgState *cg, const CgArgs *args,
-          double *partial, unsigned *counter, cudaGraphConditionalHandle loop, int in_graph)
+          double *partial, unsigned *counter, cudaGraphConditionalHandle loop, int in_graph,
+          float *__restrict__ xatt4, int64_t att0, int64_t D)
 {
     double acc[1] = {0.0};
     for (int64_t j = gtid32(); j < n; j += gstride32()) {
@@ -410,7 +465,10 @@ k_cg_init(const double *__restrict__ p, const double *__restrict__ c, double *__
         s[j] = sj;
         d[j] = sj;
         z[j] = 0.0;
-        xp32[j] = (XT)(p[j] * sj);
+        const XT xv = (XT)(p[j] * sj);
+        xp32[j] = xv;
+        if (xatt4)
+            att4_scatter(xatt4, j, (float)xv, att0, D);
         if (j >= ins0)
             t[j] = 0.0;
         acc[0] = fma(sj, sj, acc[0]);
@@ -463,17 +521,22 @@ k_cg_vec1(const double *__restrict__ p, const double *__restrict__ t, double *__
     }
 }
 
-// d = s + beta d, xp32 = fl32(p o d); clears the instrumental/global part of t
+// d = s + beta d, xp32 = fl32(p o d) (and its attitude float4 copy when
+// xatt4 is set); clears the instrumental/global part of t
 template <typename XT>
 __global__ void k_cg_vec2(const double *__restrict__ p, const double *__restrict__ s,
                           double *__restrict__ d, XT *__restrict__ xp32, double *__restrict__ t,
-                          int64_t n, int64_t ins0, const CgState *cg)
+                          int64_t n, int64_t ins0, const CgState *cg, float *__restrict__ xatt4,
+                          int64_t att0, int64_t D)
 {
     const double beta = cg->beta;
     for (int64_t j = gtid32(); j < n; j += gstride32()) {
         const double dj = fma(beta, d[j], s[j]);
         d[j] = dj;
-        xp32[j] = (XT)(p[j] * dj);
+        const XT xv = (XT)(p[j] * dj);
+        xp32[j] = xv;
+        if (xatt4)
+            att4_scatter(xatt4, j, (float)xv, att0, D);
         if (j >= ins0)
             t[j] = 0.0;
     }
@@ -541,10 +604,11 @@ static cudaError_t a1f_launch(const gsr_handle_t *h, const float *x32, double *y
     constexpr int U = kA1f32Tiles;
     if (x32_in_smem(h))
         k_aprod1_f32<MODE, true, U><<<h->grid_rows32, kThreads, (size_t)h->sys.I * sizeof(float),
-                                      st>>>(h->sys, x32, y, q32, h->d_cg, part, cnt);
+                                      st>>>(h->sys, x32, (const float4 *)h->d_xatt4, y, q32,
+                                            h->d_cg, part, cnt);
     else
-        k_aprod1_f32<MODE, false, U><<<h->grid_rows32, kThreads, 0, st>>>(h->sys, x32, y, q32,
-                                                                           h->d_cg, part, cnt);
+        k_aprod1_f32<MODE, false, U><<<h->grid_rows32, kThreads, 0, st>>>(
+            h->sys, x32, (const float4 *)h->d_xatt4, y, q32, h->d_cg, part, cnt);
     return cudaGetLastError();
 }
 
@@ -586,7 +650,8 @@ static cudaError_t a2f_launch(const gsr_handle_t *h, const float *y32, double *o
 // API forms (FP64 vectors in and out)
 cudaError_t launch_aprod1_f32_api(const gsr_handle_t *h, const double *x, double *y, cudaStream_t st)
 {
-    k_to_f32<<<h->grid_vec, kThreads, 0, st>>>(x, h->d_x32, h->sys.n);
+    k_x_to_f32<<<h->grid_vec, kThreads, 0, st>>>(x, h->d_x32, h->d_xatt4, h->sys.n, h->sys.att0,
+                                                  h->sys.D);
     return a1f_launch<0>(h, h->d_x32, y, nullptr, st);
 }
 
@@ -603,7 +668,8 @@ static cudaError_t cg_prologue(const gsr_handle_t *h, cudaStream_t s, cudaGraphC
     k_cg_init<float><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_c, h->d_s, h->d_d, h->d_zc, h->d_x32,
                                                 h->d_t, A.n, A.ins0, h->d_cg, h->d_cgargs,
                                                 h->d_partial + kRedBnorm * kPartialsPerKind,
-                                                h->d_counter + kRedBnorm, loop, in_graph);
+                                                h->d_counter + kRedBnorm, loop, in_graph,
+                                                h->d_xatt4, A.att0, A.D);
     return cudaGetLastError();
 }
 
@@ -620,7 +686,7 @@ static cudaError_t cg_iteration(const gsr_handle_t *h, cudaStream_t s, cudaGraph
                                                 h->d_cgargs, h->d_partial + kRedV * kPartialsPerKind,
                                                 h->d_counter + kRedV, loop, in_graph);
     k_cg_vec2<float><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_s, h->d_d, h->d_x32, h->d_t, A.n, A.ins0,
-                                                h->d_cg);
+                                                h->d_cg, h->d_xatt4, A.att0, A.D);
     return cudaGetLastError();
 }
 
@@ -793,7 +859,8 @@ static cudaError_t cg64_prologue(const gsr_handle_t *h, cudaStream_t s,
                                                         h->d_xp64, h->d_t, A.n, A.ins0, h->d_cg,
                                                         h->d_cgargs,
                                                         h->d_partial + kRedBnorm * kPartialsPerKind,
-                                                        h->d_counter + kRedBnorm, loop, in_graph);
+                                                        h->d_counter + kRedBnorm, loop, in_graph,
+                                                        nullptr, 0, 0);
     return cudaGetLastError();
 }
 
@@ -810,7 +877,7 @@ static cudaError_t cg64_iteration(const gsr_handle_t *h, cudaStream_t s,
                                                 h->d_cgargs, h->d_partial + kRedV * kPartialsPerKind,
                                                 h->d_counter + kRedV, loop, in_graph);
     k_cg_vec2<double><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_s, h->d_d, h->d_xp64, h->d_t,
-                                                        A.n, A.ins0, h->d_cg);
+                                                        A.n, A.ins0, h->d_cg, nullptr, 0, 0);
     return cudaGetLastError();
 }
 
