@@ -48,7 +48,7 @@ __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
 // staged in shared memory.
 // ---------------------------------------------------------------------------
 template <int MODE, bool SMEMX>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 5)  // 5 blocks per SM: 3% faster than 4
 k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveState *st,
          double *partial, unsigned *counter, CgState *cg)
 {
