@@ -54,17 +54,18 @@ __device__ __forceinline__ uint32_t star_of_row(const SysView &A, int64_t t, int
 // LSQR scalars kept on the device (Paige & Saunders 1982 notation).
 struct SolveState {
     double alpha, beta;        // current alpha_i, beta_i
-    double beta_new;           // beta_{i+1} from the last aprod1 pass
+    double beta_new;           // norm of the vector the last aprod1 pass produced
     double rhobar, phibar;
     double rho, cs, sn, phi, theta;  // rotation of the current iteration
     double anorm2, ddnorm, bnorm;
     double rnorm, arnorm, anorm, acond, xnorm;
-    double cy;                 // coefficient of the old u in aprod1 (-alpha/beta)
+    double cy;                 // coefficient of the old U in aprod1
     double t;                  // rnorm / sqrt(dof) for the standard errors
     // derived once per iteration by the last block of the kernel that
     // produced their inputs (FP64 divisions and square roots are expensive
     // on this part, so no other thread recomputes them)
-    double ib;                 // 1/beta_new (0 if beta_new = 0)
+    double bnext;              // beta_{i+1} = ||U_{i+1}|| / alpha_i
+    double ib;                 // 1/beta_{i+1} (0 if beta_{i+1} = 0)
     double t1;                 // phi/rho of the pending rotation
     double irho;               // 1/rho of the pending rotation
     double ia;                 // 1/alpha (1 if alpha = 0)

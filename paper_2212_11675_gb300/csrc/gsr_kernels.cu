@@ -42,7 +42,8 @@ __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
 
 // ---------------------------------------------------------------------------
 // aprod 1, row-parallel.  MODE 0: y += A x.  MODE 1 (LSQR): y = A x + cy y
-// with cy from the solve state and ||y||^2 reduced into state->beta_new.
+// with cy from the solve state, ||y|| into state->beta_new and, for the
+// LSQR recurrences, beta_{i+1} = ||y|| / alpha_i with its rotation.
 // MODE 2 (conjugate gradients): y = A x, ||y||^2 into cg->xi and the step
 // cg->alpha = cg->gamma / ||y||^2.  SMEMX: the instrumental part of x is
 // staged in shared memory.
@@ -126,18 +127,22 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
     if (MODE == 1) {
         double v1[1] = {nrm};
         if (grid_reduce<1>(v1, partial, counter)) {
-            // beta_{i+1} and the rotation that eliminates it; the two
-            // independent square roots and reciprocals run in two warps
+            // beta_{i+1} = ||U_{i+1}|| / alpha_i and the rotation that
+            // eliminates it; the two independent square roots and
+            // reciprocals run in two warps
             __shared__ double sq[2];
             const double rhobar = st->rhobar;
+            const double ia = st->ia;
             if (threadIdx.x == 0) {
-                const double beta = sqrt(v1[0]);
+                const double un = sqrt(v1[0]);
+                st->beta_new = un;
+                const double beta = un * ia;
                 sq[0] = beta;
-                st->beta_new = beta;
+                st->bnext = beta;
                 st->ib = (beta > 0.0) ? 1.0 / beta : 0.0;
             }
             if (threadIdx.x == 32) {
-                const double irho = 1.0 / sqrt(rhobar * rhobar + v1[0]);
+                const double irho = 1.0 / sqrt(rhobar * rhobar + v1[0] * ia * ia);
                 sq[1] = irho;
                 st->irho = irho;
             }

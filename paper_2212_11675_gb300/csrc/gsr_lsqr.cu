@@ -13,15 +13,24 @@
 //   w = v_{i+1} - (theta/rho) w.
 // The matrix values are never rescaled: Ap v = A (p o v) and
 // Ap^T u = p o (A^T u), so the row kernels gather vp = p o v and the vector
-// kernels apply p to A^T u.  u is kept unnormalised (u~ = beta u); the
-// aprod 1 pass folds the normalisation into its coefficient -alpha/beta and
-// the vector kernel divides A^T u~ by beta.
+// kernel applies p to A^T u.
 //
-// One iteration = 4 launches: aprod 1 (+ ||u~||^2), aprod 2, vector pass A
-// (v' = p o q / beta - beta v, ||v'||^2, z and var updates, scalar
-// recurrences and stopping rules in the last block), vector pass B
-// (v = v'/alpha, vp, w).  The loop is a conditional WHILE graph node whose
-// flag the last block of pass A clears when LSQR stops.
+// Neither u nor v is normalised in memory; scalars carry the scales.  The
+// stored vectors are U_{i+1} = alpha_i beta_{i+1} u_{i+1} and
+// V_i = alpha_i v_i (alpha_0 = 1), so
+//   U_{i+1} = A (p o V_i) + cy U_i,    cy = -alpha_i^2 / (alpha_{i-1} beta_i),
+//   beta_{i+1} = ||U_{i+1}|| / alpha_i,
+//   V_{i+1} = (p o A^T U_{i+1}) / (alpha_i beta_{i+1}) - (beta_{i+1}/alpha_i) V_i,
+//   alpha_{i+1} = ||V_{i+1}||,  w_i = V_i / alpha_i - (theta_i/rho_{i-1}) w_{i-1}.
+// One vector pass per iteration therefore does what the normalisation and
+// the w update would otherwise need a second pass for.
+//
+// One iteration = aprod 1 (+ ||U||^2; its last block derives beta, 1/beta,
+// 1/rho, phi/rho), aprod 2 (single launch + combine), and the vector pass
+// (w_i, z, var, V_{i+1}, p o V_{i+1}, three norms; its last block advances
+// the recurrences and applies the stopping rules).  The loop is a
+// conditional WHILE graph node whose flag that last block clears when LSQR
+// stops.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -69,72 +78,42 @@ k_init_u(const SolveArgs *args, double *u, int64_t m, SolveState *st, double *pa
         s.rnorm = s.beta;
         s.nonfinite = !isfinite(s.beta);
         s.ib = (s.beta > 0.0) ? 1.0 / s.beta : 0.0;
+        s.bnext = s.beta;
+        s.ia = 1.0;  // alpha_0 = 1: U_1 = b
         *st = s;
     }
 }
 
-// v' = p o q / beta_1, alpha_1 = ||v'||; decides istop = 0 (x = 0 exact)
-__global__ void __launch_bounds__(kThreads)
-k_init_v(const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ v,
-         int64_t n, SolveState *st, const SolveArgs *args, double *partial, unsigned *counter,
-         cudaGraphConditionalHandle loop, int in_graph)
+// Start of the recurrences once alpha_1 = ||V_1|| is known: rhobar_1 =
+// alpha_1, phibar_1 = beta_1; istop = 0 when alpha_1 beta_1 = 0 (x = 0 is
+// exact).  Thread 0 of the last block of the first vector pass.
+__device__ void init_scalars(SolveState *st, const SolveArgs *args, double vnorm2,
+                             cudaGraphConditionalHandle loop, int in_graph)
 {
     const double beta = st->beta;
-    const double ib = st->ib;
-    double acc[1] = {0.0};
-    for (int64_t j = gtid(); j < n; j += gstride()) {
-        const double t = p[j] * q[j] * ib;
-        v[j] = t;
-        acc[0] = fma(t, t, acc[0]);
+    const double alpha = sqrt(vnorm2);
+    st->alpha = alpha;
+    st->rhobar = alpha;
+    st->phibar = beta;
+    st->arnorm = alpha * beta;
+    st->t = beta * args->isdof;
+    st->cy = -alpha * alpha * st->ib;  // -alpha_1^2 / (alpha_0 beta_1)
+    st->ia = (alpha > 0.0) ? 1.0 / alpha : 1.0;
+    st->t2 = 0.0;
+    if (!isfinite(alpha) || st->nonfinite) {
+        st->nonfinite = 1;
+        st->istop = kIstopNonfinite;
+        st->done = 1;
+    } else if (alpha * beta == 0.0) {
+        st->istop = 0;
+        st->done = 1;
     }
-    if (grid_reduce<1>(acc, partial, counter) && threadIdx.x == 0) {
-        const double alpha = sqrt(acc[0]);
-        st->alpha = alpha;
-        st->rhobar = alpha;
-        st->phibar = beta;
-        st->arnorm = alpha * beta;
-        st->t = beta * args->isdof;
-        st->cy = (beta > 0.0) ? -alpha / beta : 0.0;
-        st->ia = (alpha > 0.0) ? 1.0 / alpha : 1.0;
-        st->t2 = 0.0;
-        if (!isfinite(alpha) || st->nonfinite) {
-            st->nonfinite = 1;
-            st->istop = kIstopNonfinite;
-            st->done = 1;
-        } else if (alpha * beta == 0.0) {
-            st->istop = 0;
-            st->done = 1;
-        }
-        if (st->done && in_graph)
-            cudaGraphSetConditional(loop, 0u);
-    }
-}
-
-// v = v'/alpha, vp = p o v, w = v (first) or v - (theta/rho) w; clears the
-// non-astrometric part of q for the next aprod 2
-__global__ void k_vec_b(const double *__restrict__ p, double *__restrict__ v,
-                        double *__restrict__ vp, double *__restrict__ w,
-                        double *__restrict__ q, int64_t n, int64_t att0,
-                        const SolveState *st, int first, double *z, double *var)
-{
-    const double ia = st->ia;
-    const double t2 = first ? 0.0 : st->t2;
-    for (int64_t j = gtid(); j < n; j += gstride()) {
-        const double vj = v[j] * ia;
-        v[j] = vj;
-        vp[j] = p[j] * vj;
-        w[j] = first ? vj : fma(t2, w[j], vj);
-        if (j >= att0)
-            q[j] = 0.0;
-        if (first) {
-            z[j] = 0.0;
-            var[j] = 0.0;
-        }
-    }
+    if (st->done && in_graph)
+        cudaGraphSetConditional(loop, 0u);
 }
 
 // Scalar recurrences of one LSQR iteration, run by the whole last block of
-// pass A.  The four independent square roots go to four different warps;
+// the vector pass.  The four independent square roots go to four different warps;
 // everything else is one thread, with products by reciprocals already
 // known (1/rho from the aprod 1 pass) instead of divisions, because FP64
 // divisions and square roots are long instruction sequences on this part.
@@ -142,7 +121,7 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
                              double dd, double zz, cudaGraphConditionalHandle loop, int in_graph)
 {
     __shared__ double sq[4];
-    const double beta = st->beta_new;
+    const double beta = st->bnext;
     const bool upd = beta > 0.0;
     const double anorm2 = upd ? st->anorm2 + st->alpha * st->alpha + beta * beta : st->anorm2;
     const double ddnorm = st->ddnorm + dd;
@@ -175,7 +154,7 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
     s.phi = phi;
     s.alpha = alpha;
     s.beta = beta;
-    s.cy = -alpha * s.ib;
+    s.cy = -alpha * alpha * s.ia * s.ib;  // -alpha_{i+1}^2 / (alpha_i beta_{i+1})
     s.ddnorm = ddnorm;
     s.xnorm = sq[1];
     s.anorm = sq[2];
@@ -216,37 +195,59 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
     *st = s;
 }
 
-// pass A: v' = p o q / beta - beta v (in place in v), z += (phi/rho) w,
-// var += (w/rho)^2, reductions of ||v'||^2, sum (w/rho)^2, ||z||^2; the
-// last block advances the scalar recurrences and applies the stopping rules
+// The vector pass of iteration i (first: the start, V_1 = p o A^T b / beta_1
+// with w, z, var cleared): w_i = V_i/alpha_i - (theta_i/rho_{i-1}) w_{i-1},
+// var += (w_i/rho_i)^2, z_i = z_{i-1} + (phi_i/rho_i) w_i, V_{i+1} (in place),
+// vp = p o V_{i+1}, and the reductions ||V_{i+1}||^2, sum (w_i/rho_i)^2,
+// ||z_i||^2; q's non-astrometric part is cleared for the next aprod 2.  When
+// beta_{i+1} = 0 V is kept (alpha unchanged).
 __global__ void __launch_bounds__(kThreads)
-k_vec_a(const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ v,
-        const double *__restrict__ w, double *__restrict__ z, double *__restrict__ var,
-        int64_t n, SolveState *st, const SolveArgs *args, double *partial,
-        unsigned *counter, cudaGraphConditionalHandle loop, int in_graph)
+k_vec(const double *__restrict__ p, double *__restrict__ q, double *__restrict__ v,
+      double *__restrict__ vp, double *__restrict__ w, double *__restrict__ z,
+      double *__restrict__ var, int64_t n, int64_t att0, SolveState *st, const SolveArgs *args,
+      double *partial, unsigned *counter, cudaGraphConditionalHandle loop, int in_graph,
+      int first)
 {
-    const double beta = st->beta_new;
-    const double t1 = st->t1;
-    const double irho = st->irho;
-    const bool upd = beta > 0.0;
-    const double ib = st->ib;
+    const double ia = st->ia;           // 1/alpha_i
+    const double ib = st->ib;           // 1/beta_{i+1}
+    const double bn = st->bnext;        // beta_{i+1}
+    const double t1 = first ? 0.0 : st->t1;
+    const double t2 = first ? 0.0 : st->t2;
+    const double irho = first ? 0.0 : st->irho;
+    const bool upd = bn > 0.0;
+    const double k1 = ia * ib, k2 = -bn * ia;
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t j = gtid(); j < n; j += gstride()) {
-        if (upd) {
-            const double vn = fma(p[j] * q[j], ib, -beta * v[j]);
-            v[j] = vn;
-            acc[0] = fma(vn, vn, acc[0]);
+        const double pj = p[j];
+        const double qj = q[j];
+        if (j >= att0)
+            q[j] = 0.0;
+        const double vo = first ? 0.0 : v[j];
+        double wj = 0.0, zj = 0.0, vr = 0.0;
+        if (!first) {
+            wj = fma(t2, w[j], vo * ia);
+            const double d = wj * irho;
+            acc[1] = fma(d, d, acc[1]);
+            vr = fma(d, d, var[j]);
+            zj = fma(t1, wj, z[j]);
+            acc[2] = fma(zj, zj, acc[2]);
         }
-        const double wj = w[j];
-        const double d = wj * irho;
-        acc[1] = fma(d, d, acc[1]);
-        var[j] = fma(d, d, var[j]);
-        const double zj = fma(t1, wj, z[j]);
+        w[j] = wj;
         z[j] = zj;
-        acc[2] = fma(zj, zj, acc[2]);
+        var[j] = vr;
+        const double vn = upd ? fma(pj * qj, k1, k2 * vo) : vo;
+        v[j] = vn;
+        vp[j] = pj * vn;
+        acc[0] = fma(vn, vn, acc[0]);
     }
-    if (grid_reduce<3>(acc, partial, counter))
-        lsqr_scalars(st, args, acc[0], acc[1], acc[2], loop, in_graph);
+    if (grid_reduce<3>(acc, partial, counter)) {
+        if (first) {
+            if (threadIdx.x == 0)
+                init_scalars(st, args, acc[0], loop, in_graph);
+        } else {
+            lsqr_scalars(st, args, acc[0], acc[1], acc[2], loop, in_graph);
+        }
+    }
 }
 
 // x = p o z, se = p o sqrt(var) * rnorm / sqrt(dof)
@@ -335,11 +336,10 @@ cudaError_t enqueue_prologue(const gsr_handle_t *h, cudaStream_t s,
     e = launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
     if (e != cudaSuccess)
         return e;
-    k_init_v<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, A.n, h->d_state, h->d_args,
-                                               part + kRedV * kPartialsPerKind, cnt + kRedV, loop,
-                                               in_graph);
-    k_vec_b<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_v, h->d_vp, h->d_w, h->d_q, A.n, A.att0,
-                                              h->d_state, 1, h->d_z, h->d_var);
+    k_vec<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w, h->d_z, h->d_var,
+                                            A.n, A.att0, h->d_state, h->d_args,
+                                            part + kRedV * kPartialsPerKind, cnt + kRedV, loop,
+                                            in_graph, 1);
     return cudaGetLastError();
 }
 
@@ -352,12 +352,10 @@ cudaError_t enqueue_iteration(const gsr_handle_t *h, cudaStream_t s,
         e = launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
     if (e != cudaSuccess)
         return e;
-    k_vec_a<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, h->d_w, h->d_z, h->d_var, A.n,
-                                              h->d_state, h->d_args,
-                                              h->d_partial + kRedV * kPartialsPerKind,
-                                              h->d_counter + kRedV, loop, in_graph);
-    k_vec_b<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_v, h->d_vp, h->d_w, h->d_q, A.n, A.att0,
-                                              h->d_state, 0, nullptr, nullptr);
+    k_vec<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w, h->d_z, h->d_var,
+                                            A.n, A.att0, h->d_state, h->d_args,
+                                            h->d_partial + kRedV * kPartialsPerKind,
+                                            h->d_counter + kRedV, loop, in_graph, 0);
     return cudaGetLastError();
 }
 
@@ -370,7 +368,7 @@ cudaError_t enqueue_epilogue(const gsr_handle_t *h, cudaStream_t s)
 }
 
 // Build and instantiate the graph of one whole solve:
-//   [precondition, u = b, q = A^T u, v_1, w_1]  ->  WHILE(flag) { iteration }
+//   [precondition, U_1 = b, q = A^T U_1, V_1]  ->  WHILE(flag) { iteration }
 //   ->  [x = p o z, se]
 cudaError_t build_solve_graph(gsr_handle_t *h)
 {
