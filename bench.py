@@ -531,11 +531,12 @@ def main():
                     sm, xt, lambda j: torch.tensor(gen.noise(sys_, seed + 1000 * (j + 1)), device=dev),
                     torch, stream)
 
-    # per solve (ncu launch list of --eager): 9 prologue launches (2 clears,
+    # per solve (ncu launch list of --eager): 8 prologue launches (2 clears,
     # preconditioner: single-launch aprod 2 of squares + combine + finish;
-    # init: U, aprod 2 + combine, first vector pass), 4 per LSQR iteration
-    # (aprod 1, single-launch aprod 2, combine, vector pass), 1 epilogue
-    launches_per_step = 10 + 4 * (iters // args.steps)
+    # init: U, aprod 2, first vector pass), 3 per LSQR iteration (aprod 1,
+    # single-launch aprod 2, vector pass that also combines aprod 2's
+    # partial sums), 1 epilogue
+    launches_per_step = 9 + 3 * (iters // args.steps)
     line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

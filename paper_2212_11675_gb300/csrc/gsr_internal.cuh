@@ -253,6 +253,9 @@ cudaError_t launch_att_combine(const gsr_handle_t *h, double *out, int nb_att, i
                                bool accumulate, cudaStream_t st, unsigned long long *ctr = nullptr);
 int instr_path(const gsr_config &cfg, int64_t I);
 A2Queue a2_queue(const gsr_handle_t *h, int G);
+bool aprod2_partials(const gsr_handle_t *h, const double *y, double *out, const double **S,
+                     const double **ipart, int *isplit, const double **gpart, int *ngpart,
+                     unsigned long long **ctr, cudaStream_t st);
 cudaError_t launch_gather_instr64(const gsr_handle_t *h, const uint32_t *code, double *out,
                                   cudaStream_t st);
 // mixed precision (gsr_mixed.cu)

@@ -791,6 +791,25 @@ cudaError_t launch_aprod2(const gsr_handle_t *h, const double *y, double *out, i
     return launch_aprod2_split(h, y, out, mode, st);
 }
 
+// With the single-launch aprod 2: launch it without the combine, writing the
+// astrometric part of out (overwrite) and the partial sums, and return their
+// locations (true); otherwise launch nothing and return false.
+bool aprod2_partials(const gsr_handle_t *h, const double *y, double *out, const double **S,
+                     const double **ipart, int *isplit, const double **gpart, int *ngpart,
+                     unsigned long long **ctr, cudaStream_t st)
+{
+    if (!(h->ipath == kIpSorted && h->a2_fused))
+        return false;
+    fused_launch_g<kA2Overwrite>(h, y, out, st);
+    *S = h->d_attS;
+    *ipart = h->d_ipart;
+    *isplit = h->isplit;
+    *gpart = h->d_gpart;
+    *ngpart = (int)a2_queue(h, h->lanes).nstar_units;
+    *ctr = h->d_a2ctr;
+    return true;
+}
+
 // the instrumental pass (sorted path) and the combine after the star and
 // attitude passes; ngpart star-pass blocks wrote global partials
 static cudaError_t a2_rest(const gsr_handle_t *h, const double *y, double *out, int mode,

@@ -195,19 +195,58 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
     *st = s;
 }
 
+// Partial sums of the single-launch aprod 2 that the vector pass combines
+// itself (no combine launch): attitude segment sums S, instrument chunk
+// totals, per-star-unit global partials, and the work counter to reset.
+struct A2Parts {
+    const double *S;
+    const double *ipart;
+    int isplit;
+    const double *gpart;
+    int ngpart;
+    unsigned long long *ctr;
+};
+
+// q_j of the non-astrometric columns from the partial sums: column a D + k of
+// the attitude block is sum_{jj<4} S[k-jj][4a+jj]; instrument f the sum of its
+// chunk totals (both in the combine kernel's order)
+__device__ __forceinline__ double q_from_parts(const SysView &A, const A2Parts &P, int64_t j)
+{
+    double t = 0.0;
+    if (j < A.ins0) {
+        const int64_t c = j - A.att0, a = c / A.D, k = c - a * A.D;
+#pragma unroll
+        for (int jj = 0; jj < 4; jj++) {
+            const int64_t o = k - jj;
+            if (o >= 0 && o < A.nseg)
+                t += P.S[o * kNAtt + 4 * a + jj];
+        }
+    } else {
+        const int64_t f = j - A.ins0;
+        for (int qq = 0; qq < P.isplit; qq++)
+            t += P.ipart[(int64_t)qq * A.I + f];
+    }
+    return t;
+}
+
 // The vector pass of iteration i (first: the start, V_1 = p o A^T b / beta_1
 // with w, z, var cleared): w_i = V_i/alpha_i - (theta_i/rho_{i-1}) w_{i-1},
 // var += (w_i/rho_i)^2, z_i = z_{i-1} + (phi_i/rho_i) w_i, V_{i+1} (in place),
 // vp = p o V_{i+1}, and the reductions ||V_{i+1}||^2, sum (w_i/rho_i)^2,
-// ||z_i||^2; q's non-astrometric part is cleared for the next aprod 2.  When
-// beta_{i+1} = 0 V is kept (alpha unchanged).
+// ||z_i||^2.  When beta_{i+1} = 0 V is kept (alpha unchanged).
+// INL: q holds only the astrometric part of A^T U (single-launch aprod 2);
+// the other columns come from its partial sums, and the global column from
+// one fixed slice of the per-unit partials per block, added by the last
+// block, which also updates V at the global column.  Otherwise q is complete
+// and its non-astrometric part is cleared for the next aprod 2.
+template <bool INL>
 __global__ void __launch_bounds__(kThreads)
-k_vec(const double *__restrict__ p, double *__restrict__ q, double *__restrict__ v,
+k_vec(const SysView A, const double *__restrict__ p, double *__restrict__ q, double *__restrict__ v,
       double *__restrict__ vp, double *__restrict__ w, double *__restrict__ z,
-      double *__restrict__ var, int64_t n, int64_t att0, SolveState *st, const SolveArgs *args,
-      double *partial, unsigned *counter, cudaGraphConditionalHandle loop, int in_graph,
-      int first)
+      double *__restrict__ var, SolveState *st, const SolveArgs *args, double *partial,
+      unsigned *counter, cudaGraphConditionalHandle loop, int in_graph, int first, A2Parts P)
 {
+    const int64_t n = A.n, att0 = A.att0, glb0 = A.glb0;
     const double ia = st->ia;           // 1/alpha_i
     const double ib = st->ib;           // 1/beta_{i+1}
     const double bn = st->bnext;        // beta_{i+1}
@@ -216,12 +255,17 @@ k_vec(const double *__restrict__ p, double *__restrict__ q, double *__restrict__
     const double irho = first ? 0.0 : st->irho;
     const bool upd = bn > 0.0;
     const double k1 = ia * ib, k2 = -bn * ia;
-    double acc[3] = {0.0, 0.0, 0.0};
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t j = gtid(); j < n; j += gstride()) {
         const double pj = p[j];
-        const double qj = q[j];
-        if (j >= att0)
-            q[j] = 0.0;
+        double qj;
+        if (INL) {
+            qj = (j < att0) ? q[j] : (j < glb0 ? q_from_parts(A, P, j) : 0.0);
+        } else {
+            qj = q[j];
+            if (j >= att0)
+                q[j] = 0.0;
+        }
         const double vo = first ? 0.0 : v[j];
         double wj = 0.0, zj = 0.0, vr = 0.0;
         if (!first) {
@@ -235,17 +279,39 @@ k_vec(const double *__restrict__ p, double *__restrict__ q, double *__restrict__
         w[j] = wj;
         z[j] = zj;
         var[j] = vr;
+        if (INL && j == glb0)
+            continue;  // V at the global column: the last block
         const double vn = upd ? fma(pj * qj, k1, k2 * vo) : vo;
         v[j] = vn;
         vp[j] = pj * vn;
         acc[0] = fma(vn, vn, acc[0]);
     }
-    if (grid_reduce<3>(acc, partial, counter)) {
+    if (INL) {  // this block's fixed slice of the global-column partials
+        const int64_t per = (P.ngpart + gridDim.x - 1) / gridDim.x;
+        const int64_t b0 = blockIdx.x * per, b1 = min((int64_t)P.ngpart, b0 + per);
+        for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+            acc[3] += P.gpart[b];
+    }
+    if (grid_reduce<4>(acc, partial, counter)) {
+        __shared__ double vn2;
+        if (threadIdx.x == 0) {
+            vn2 = acc[0];
+            if (INL) {
+                const double vo = first ? 0.0 : v[glb0];
+                const double pj = p[glb0];
+                const double vn = upd ? fma(pj * acc[3], k1, k2 * vo) : vo;
+                v[glb0] = vn;
+                vp[glb0] = pj * vn;
+                vn2 = fma(vn, vn, vn2);
+                *P.ctr = 0ull;  // work counter of the single-launch aprod 2
+            }
+        }
+        __syncthreads();
         if (first) {
             if (threadIdx.x == 0)
-                init_scalars(st, args, acc[0], loop, in_graph);
+                init_scalars(st, args, vn2, loop, in_graph);
         } else {
-            lsqr_scalars(st, args, acc[0], acc[1], acc[2], loop, in_graph);
+            lsqr_scalars(st, args, vn2, acc[1], acc[2], loop, in_graph);
         }
     }
 }
@@ -319,6 +385,31 @@ cudaError_t find_graph_leaf(cudaGraph_t g, cudaGraphNode_t *leaf)
         }                               \
     } while (0)
 
+// q = A^T U (overwrite) and the vector pass; with the single-launch aprod 2
+// the vector pass combines its partial sums itself
+static cudaError_t a2_and_vec(const gsr_handle_t *h, cudaStream_t s, cudaGraphConditionalHandle loop,
+                              int in_graph, int first)
+{
+    double *part = h->d_partial + kRedV * kPartialsPerKind;
+    unsigned *cnt = h->d_counter + kRedV;
+    A2Parts P = {};
+    const bool inl = aprod2_partials(h, h->d_u, h->d_q, &P.S, &P.ipart, &P.isplit, &P.gpart,
+                                     &P.ngpart, &P.ctr, s);
+    if (!inl) {
+        cudaError_t e = launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
+        if (e != cudaSuccess)
+            return e;
+        k_vec<false><<<h->grid_vec, kThreads, 0, s>>>(h->sys, h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w,
+                                                      h->d_z, h->d_var, h->d_state, h->d_args, part,
+                                                      cnt, loop, in_graph, first, P);
+    } else {
+        k_vec<true><<<h->grid_vec, kThreads, 0, s>>>(h->sys, h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w,
+                                                     h->d_z, h->d_var, h->d_state, h->d_args, part,
+                                                     cnt, loop, in_graph, first, P);
+    }
+    return cudaGetLastError();
+}
+
 // The three parts of one solve.  `in_graph` says whether the kernels run
 // inside the solve graph (and may clear its loop flag).
 cudaError_t enqueue_prologue(const gsr_handle_t *h, cudaStream_t s,
@@ -333,30 +424,16 @@ cudaError_t enqueue_prologue(const gsr_handle_t *h, cudaStream_t s,
     k_init_u<<<h->grid_vec, kThreads, 0, s>>>(h->d_args, h->d_u, A.m, h->d_state,
                                                part + kRedBnorm * kPartialsPerKind, cnt + kRedBnorm);
     k_zero<<<h->grid_vec, kThreads, 0, s>>>(h->d_q + A.att0, A.n - A.att0);
-    e = launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
-    if (e != cudaSuccess)
-        return e;
-    k_vec<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w, h->d_z, h->d_var,
-                                            A.n, A.att0, h->d_state, h->d_args,
-                                            part + kRedV * kPartialsPerKind, cnt + kRedV, loop,
-                                            in_graph, 1);
-    return cudaGetLastError();
+    return a2_and_vec(h, s, loop, in_graph, 1);
 }
 
 cudaError_t enqueue_iteration(const gsr_handle_t *h, cudaStream_t s,
                               cudaGraphConditionalHandle loop, int in_graph)
 {
-    const SysView &A = h->sys;
     cudaError_t e = launch_aprod1(h, h->d_vp, h->d_u, 1, s);
-    if (e == cudaSuccess)
-        e = launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
     if (e != cudaSuccess)
         return e;
-    k_vec<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w, h->d_z, h->d_var,
-                                            A.n, A.att0, h->d_state, h->d_args,
-                                            h->d_partial + kRedV * kPartialsPerKind,
-                                            h->d_counter + kRedV, loop, in_graph, 0);
-    return cudaGetLastError();
+    return a2_and_vec(h, s, loop, in_graph, 0);
 }
 
 cudaError_t enqueue_epilogue(const gsr_handle_t *h, cudaStream_t s)
