@@ -51,6 +51,40 @@ __device__ __forceinline__ uint32_t star_of_row(const SysView &A, int64_t t, int
     return s;
 }
 
+// Partial sums of the single-launch aprod 2 that a following vector pass
+// combines itself (no combine launch): attitude segment sums S, instrument chunk
+// totals, per-star-unit global partials, and the work counter to reset.
+struct A2Parts {
+    const double *S;
+    const double *ipart;
+    int isplit;
+    const double *gpart;
+    int ngpart;
+    unsigned long long *ctr;
+};
+
+// q_j of the non-astrometric columns from the partial sums: column a D + k of
+// the attitude block is sum_{jj<4} S[k-jj][4a+jj]; instrument f the sum of its
+// chunk totals (both in the combine kernel's order)
+__device__ __forceinline__ double q_from_parts(const SysView &A, const A2Parts &P, int64_t j)
+{
+    double t = 0.0;
+    if (j < A.ins0) {
+        const int64_t c = j - A.att0, a = c / A.D, k = c - a * A.D;
+#pragma unroll
+        for (int jj = 0; jj < 4; jj++) {
+            const int64_t o = k - jj;
+            if (o >= 0 && o < A.nseg)
+                t += P.S[o * kNAtt + 4 * a + jj];
+        }
+    } else {
+        const int64_t f = j - A.ins0;
+        for (int qq = 0; qq < P.isplit; qq++)
+            t += P.ipart[(int64_t)qq * A.I + f];
+    }
+    return t;
+}
+
 // LSQR scalars kept on the device (Paige & Saunders 1982 notation).
 struct SolveState {
     double alpha, beta;        // current alpha_i, beta_i

@@ -195,40 +195,6 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
     *st = s;
 }
 
-// Partial sums of the single-launch aprod 2 that the vector pass combines
-// itself (no combine launch): attitude segment sums S, instrument chunk
-// totals, per-star-unit global partials, and the work counter to reset.
-struct A2Parts {
-    const double *S;
-    const double *ipart;
-    int isplit;
-    const double *gpart;
-    int ngpart;
-    unsigned long long *ctr;
-};
-
-// q_j of the non-astrometric columns from the partial sums: column a D + k of
-// the attitude block is sum_{jj<4} S[k-jj][4a+jj]; instrument f the sum of its
-// chunk totals (both in the combine kernel's order)
-__device__ __forceinline__ double q_from_parts(const SysView &A, const A2Parts &P, int64_t j)
-{
-    double t = 0.0;
-    if (j < A.ins0) {
-        const int64_t c = j - A.att0, a = c / A.D, k = c - a * A.D;
-#pragma unroll
-        for (int jj = 0; jj < 4; jj++) {
-            const int64_t o = k - jj;
-            if (o >= 0 && o < A.nseg)
-                t += P.S[o * kNAtt + 4 * a + jj];
-        }
-    } else {
-        const int64_t f = j - A.ins0;
-        for (int qq = 0; qq < P.isplit; qq++)
-            t += P.ipart[(int64_t)qq * A.I + f];
-    }
-    return t;
-}
-
 // The vector pass of iteration i (first: the start, V_1 = p o A^T b / beta_1
 // with w, z, var cleared): w_i = V_i/alpha_i - (theta_i/rho_{i-1}) w_{i-1},
 // var += (w_i/rho_i)^2, z_i = z_{i-1} + (phi_i/rho_i) w_i, V_{i+1} (in place),

@@ -488,24 +488,45 @@ k_cg_init(const double *__restrict__ p, const double *__restrict__ c, double *__
 }
 
 // s -= alpha p o t, z += alpha d, gamma' = |s|^2; the last block forms beta
-// and applies the inner stopping rule
+// and applies the inner stopping rule.  INL: t holds only the astrometric
+// part of A^T q (single-launch aprod 2); the other columns come from its
+// partial sums, the global column from one fixed slice of the per-unit
+// partials per block, updated by the last block (which also resets the
+// aprod 2 work counter).
+template <bool INL>
 __global__ void __launch_bounds__(kThreads)
-k_cg_vec1(const double *__restrict__ p, const double *__restrict__ t, double *__restrict__ s,
-          const double *__restrict__ d, double *__restrict__ z, int64_t n, CgState *cg,
+k_cg_vec1(const SysView A, const double *__restrict__ p, const double *__restrict__ t,
+          double *__restrict__ s, const double *__restrict__ d, double *__restrict__ z, CgState *cg,
           const CgArgs *args, double *partial, unsigned *counter,
-          cudaGraphConditionalHandle loop, int in_graph)
+          cudaGraphConditionalHandle loop, int in_graph, A2Parts P)
 {
+    const int64_t n = A.n, glb0 = A.glb0;
     const double alpha = cg->alpha;
-    double acc[1] = {0.0};
+    double acc[2] = {0.0, 0.0};
     for (int64_t j = gtid32(); j < n; j += gstride32()) {
-        const double sj = fma(-alpha, p[j] * t[j], s[j]);
-        s[j] = sj;
         z[j] = fma(alpha, d[j], z[j]);
+        if (INL && j == glb0)
+            continue;  // the global column: the last block
+        const double tj = (!INL || j < A.att0) ? t[j] : q_from_parts(A, P, j);
+        const double sj = fma(-alpha, p[j] * tj, s[j]);
+        s[j] = sj;
         acc[0] = fma(sj, sj, acc[0]);
     }
-    if (grid_reduce<1>(acc, partial, counter) && threadIdx.x == 0) {
+    if (INL) {
+        const int64_t per = (P.ngpart + gridDim.x - 1) / gridDim.x;
+        const int64_t b0 = blockIdx.x * per, b1 = min((int64_t)P.ngpart, b0 + per);
+        for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+            acc[1] += P.gpart[b];
+    }
+    if (grid_reduce<2>(acc, partial, counter) && threadIdx.x == 0) {
         CgState g = *cg;
-        const double gnew = acc[0];
+        double gnew = acc[0];
+        if (INL) {
+            const double sj = fma(-alpha, p[glb0] * acc[1], s[glb0]);
+            s[glb0] = sj;
+            gnew = fma(sj, sj, gnew);
+            *P.ctr = 0ull;
+        }
         g.beta = gnew / g.gamma;
         g.gamma = gnew;
         g.it += 1;
@@ -680,13 +701,29 @@ static cudaError_t cg_iteration(const gsr_handle_t *h, cudaStream_t s, cudaGraph
 {
     const SysView &A = h->sys;
     cudaError_t e = a1f_launch<1>(h, h->d_x32, nullptr, h->d_q32, s);
-    if (e == cudaSuccess)
-        e = a2f_launch<kA2Overwrite>(h, h->d_q32, h->d_t, s);
     if (e != cudaSuccess)
         return e;
-    k_cg_vec1<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc, A.n, h->d_cg,
-                                                h->d_cgargs, h->d_partial + kRedV * kPartialsPerKind,
-                                                h->d_counter + kRedV, loop, in_graph);
+    A2Parts P = {};
+    double *part = h->d_partial + kRedV * kPartialsPerKind;
+    unsigned *cnt = h->d_counter + kRedV;
+    if (h->ipath == kIpSorted && h->a2_fused) {
+        // single-launch aprod 2 without the combine; the CG pass combines
+        const A2Queue q = a2_queue(h, 8);
+        k_aprod2_f32_fused<8, kA2Overwrite><<<h->grid_fused32, kThreads, 0, s>>>(
+            h->sys, h->d_q32, h->d_t, h->d_attS, h->d_iseg, h->d_irow, h->d_ival32, h->d_ipart,
+            h->isplit, h->d_gpart, q);
+        P = {h->d_attS, h->d_ipart, h->isplit, h->d_gpart, (int)q.nstar_units, h->d_a2ctr};
+        k_cg_vec1<true><<<h->grid_vec, kThreads, 0, s>>>(A, h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc,
+                                                         h->d_cg, h->d_cgargs, part, cnt, loop,
+                                                         in_graph, P);
+    } else {
+        e = a2f_launch<kA2Overwrite>(h, h->d_q32, h->d_t, s);
+        if (e != cudaSuccess)
+            return e;
+        k_cg_vec1<false><<<h->grid_vec, kThreads, 0, s>>>(A, h->d_p, h->d_t, h->d_s, h->d_d,
+                                                          h->d_zc, h->d_cg, h->d_cgargs, part, cnt,
+                                                          loop, in_graph, P);
+    }
     k_cg_vec2<float><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_s, h->d_d, h->d_x32, h->d_t, A.n, A.ins0,
                                                 h->d_cg, h->d_xatt4, A.att0, A.D);
     return cudaGetLastError();
@@ -875,9 +912,11 @@ static cudaError_t cg64_iteration(const gsr_handle_t *h, cudaStream_t s,
         e = launch_aprod2(h, h->d_q64, h->d_t, kA2Overwrite, s);
     if (e != cudaSuccess)
         return e;
-    k_cg_vec1<<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc, A.n, h->d_cg,
-                                                h->d_cgargs, h->d_partial + kRedV * kPartialsPerKind,
-                                                h->d_counter + kRedV, loop, in_graph);
+    k_cg_vec1<false><<<h->grid_vec, kThreads, 0, s>>>(A, h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc,
+                                                      h->d_cg, h->d_cgargs,
+                                                      h->d_partial + kRedV * kPartialsPerKind,
+                                                      h->d_counter + kRedV, loop, in_graph,
+                                                      A2Parts{});
     k_cg_vec2<double><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_s, h->d_d, h->d_xp64, h->d_t,
                                                         A.n, A.ins0, h->d_cg, nullptr, 0, 0);
     return cudaGetLastError();
