@@ -361,10 +361,14 @@ def cpu_baseline(sys_, seed, seconds):
     import oracle
     xt = gen.x_true(sys_, seed)
     b = oracle.aprod1(sys_, xt) + gen.noise(sys_, seed + 1)
+    # calibrate: the preconditioner and start cost once, each iteration again
     t0 = time.perf_counter()
-    r = oracle.pc_lsqr(sys_, b, 1, 0.0, 0.0)
-    one = time.perf_counter() - t0
-    iters = max(1, min(500, int(seconds / max(one, 1e-6))))
+    oracle.pc_lsqr(sys_, b, 1, 0.0, 0.0)
+    t1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.pc_lsqr(sys_, b, 3, 0.0, 0.0)
+    per_it = max((time.perf_counter() - t0 - t1) / 2.0, 1e-6)
+    iters = max(1, min(500, int((seconds - t1) / per_it)))
     t0 = time.perf_counter()
     r = oracle.pc_lsqr(sys_, b, iters, 0.0, 0.0)
     dt = time.perf_counter() - t0
