@@ -143,7 +143,7 @@ static void release(gsr_handle_t *h)
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err,
                    h->d_val32, h->d_tval32, h->d_x32, h->d_xatt4, h->d_q32, h->d_c, h->d_s, h->d_d, h->d_t,
                    h->d_zc, h->d_xm, h->d_r, h->d_xneg, h->d_onorm, h->d_cg, h->d_cgargs,
-                   h->d_xp64, h->d_q64, h->d_iseg, h->d_irow, h->d_ival32, h->d_ival, h->d_ipart, h->d_gpart, h->d_a2ctr, h->d_bX32, h->d_bQ32,
+                   h->d_xp64, h->d_q64, h->d_iseg, h->d_cseg, h->d_irow, h->d_ival32, h->d_ival, h->d_ipart, h->d_gpart, h->d_a2ctr, h->d_bX32, h->d_bQ32,
                    h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT, h->d_bS, h->d_bXcm,
                    h->d_bCcm, h->d_bB, h->d_bnorms, h->d_bpartial, h->d_bcounter, h->d_bs,
                    h->d_bipart,
@@ -161,12 +161,15 @@ static void release(gsr_handle_t *h)
     delete h;
 }
 
-// binary32 copies of the value planes and of the offset-sorted attitude
-// values, the mixed-precision workspace and the inner CG graph
 // Instrument-sorted copy of the instrumental nonzeros: a stable counting
 // sort of the 6 m entries (row, slot) by instrument on the host, so the
 // entries of every instrument keep ascending row order and their sums a
-// fixed order; the FP64 values are then gathered on the device.
+// fixed order; the FP64 values are then gathered on the device.  The
+// entries of each instrument are cut at row windows of R rows (a unit of
+// the instrumental sums is one instrument in one window): units are taken
+// window by window, so the y entries they gather stay within R rows, which
+// L2 holds also when the whole of y does not fit; R also bounds a unit to
+// about 4096 entries.
 static int build_instr_sorted(gsr_handle_t *h, cudaStream_t st)
 {
     SysView &A = h->sys;
@@ -205,9 +208,28 @@ static int build_instr_sorted(gsr_handle_t *h, cudaStream_t st)
     cudaFree(d_code);
     if (e != cudaSuccess)
         return cuda_fail(e, "instrument-sorted layout");
-    // chunks per instrument: about 64 warps' worth of units per SM
-    const int64_t want = ((int64_t)h->nsm * 64 + I - 1) / I;
-    h->isplit = (int)(want < 1 ? 1 : (want > 64 ? 64 : want));
+    // row windows: R = 4096 I / 6 rows (about 4096 entries per instrument and
+    // window), at most 4 Mi rows (32 MB of FP64 y), at least 64 Ki rows
+    int64_t R = 4096 * I / kNInstr;
+    if (R > ((int64_t)1 << 22))
+        R = (int64_t)1 << 22;
+    if (R < ((int64_t)1 << 16))
+        R = (int64_t)1 << 16;
+    const int64_t nq = (m + R - 1) / R;
+    std::vector<uint32_t> cseg((size_t)((nq + 1) * I));
+    for (int64_t f = 0; f < I; f++) {
+        uint32_t e = seg[f];
+        for (int64_t q = 0; q < nq; q++) {
+            cseg[q * I + f] = e;
+            const int64_t rend = (q + 1) * R;  // entries of window q: rows < rend
+            while (e < seg[f + 1] && (int64_t)irow[e] < rend)
+                e++;
+        }
+        cseg[nq * I + f] = seg[f + 1];
+    }
+    TRY(dalloc(h, &h->d_cseg, (nq + 1) * I));
+    CK(cudaMemcpy(h->d_cseg, cseg.data(), (nq + 1) * I * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    h->isplit = (int)nq;
     TRY(dalloc(h, &h->d_ipart, (int64_t)h->isplit * I));
     CK(cudaMemset(h->d_ipart, 0, (size_t)h->isplit * I * sizeof(double)));
     const int64_t units_blocks = (I * h->isplit + kThreads / 32 - 1) / (kThreads / 32);
@@ -216,6 +238,8 @@ static int build_instr_sorted(gsr_handle_t *h, cudaStream_t st)
     return GSR_OK;
 }
 
+// binary32 copies of the value planes and of the offset-sorted attitude
+// values, the mixed-precision workspace and the inner CG graph
 static int create_mixed(gsr_handle_t *h, cudaStream_t st)
 {
     SysView &A = h->sys;

@@ -192,8 +192,10 @@ struct gsr_handle_t {
     uint32_t *d_iseg = nullptr, *d_irow = nullptr;
     double *d_ival = nullptr;           // FP64 values of the sorted entries
     float *d_ival32 = nullptr;          // binary32 copy (mixed precision)
-    double *d_ipart = nullptr;          // [isplit][I] per-chunk instrumental sums
-    int isplit = 1;                     // chunks per instrument segment
+    uint32_t *d_cseg = nullptr;         // [isplit+1][I]: entries of instrument f in row
+                                        // window q are cseg[q I + f] .. cseg[(q+1) I + f]-1
+    double *d_ipart = nullptr;          // [isplit][I] per-window instrumental sums
+    int isplit = 1;                     // row windows of the instrumental sums
     double *d_gpart = nullptr;          // per-block partials of the global column (star pass)
     int a2_fused = 1;                   // aprod 2 in one launch (sorted path), else separate passes
     unsigned long long *d_a2ctr = nullptr;  // work counter of the single-launch aprod 2

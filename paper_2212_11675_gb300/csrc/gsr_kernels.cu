@@ -316,27 +316,26 @@ k_aprod2_stars(SysView A, const double *__restrict__ y, double *__restrict__ out
 // ---------------------------------------------------------------------------
 // aprod 2, instrumental part over the instrument-sorted copy (column f of
 // Alg. 2's instrumental block is the sum over its entries of value * y_row).
-// Unit w covers chunk q = w % nsplit of instrument f = w / nsplit; a warp
-// sums its chunk with four independent FMA chains (four gathers of y in
-// flight per lane) and writes the chunk's total to part[q * I + f].  The
-// combine kernel adds the nsplit chunk totals of each instrument in a fixed
-// order: no atomics, deterministic.  SQ: squares of the values.
+// Unit w covers instrument f = w % I in row window q = w / I; a warp sums
+// the unit's entries with four independent FMA chains (four gathers of y in
+// flight per lane) and writes the total to part[q * I + f].  The combine
+// adds the nwin window totals of each instrument in a fixed order: no
+// atomics, deterministic.  SQ: squares of the values.
 // ---------------------------------------------------------------------------
 template <bool SQ>
-__device__ __forceinline__ void instr_body(const SysView &A, const uint32_t *__restrict__ iseg,
+__device__ __forceinline__ void instr_body(const SysView &A, const uint32_t *__restrict__ cseg,
                                            const uint32_t *__restrict__ irow,
                                            const double *__restrict__ ival,
                                            const double *__restrict__ y, double *__restrict__ part,
-                                           int nsplit, int64_t warp, int64_t nwarps)
+                                           int nwin, int64_t warp, int64_t nwarps)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t w = warp; w < A.I * nsplit; w += nwarps) {
-        const int64_t f = w / nsplit;
-        const int q = (int)(w - f * nsplit);
-        const uint32_t s0 = iseg[f];
-        const uint64_t len = iseg[f + 1] - s0;
-        const uint32_t e1 = s0 + (uint32_t)(len * (q + 1) / nsplit);
-        uint32_t e = s0 + (uint32_t)(len * q / nsplit) + lane;
+    for (int64_t w = warp; w < A.I * nwin; w += nwarps) {
+        // unit w: instrument f in row window q, window-major
+        const int64_t q = w / A.I;
+        const int64_t f = w - q * A.I;
+        const uint32_t e1 = cseg[w + A.I];
+        uint32_t e = cseg[w] + lane;
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
         // four entries per lane in flight: the row indices first, then the
         // four independent gathers of y
@@ -368,19 +367,19 @@ __device__ __forceinline__ void instr_body(const SysView &A, const uint32_t *__r
         }
         const double t = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
         if (lane == 0)
-            part[(int64_t)q * A.I + f] = t;
+            part[q * A.I + f] = t;
     }
 }
 
 template <bool SQ>
 __global__ void __launch_bounds__(kThreads)
-k_instr_segments(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restrict__ irow,
+k_instr_segments(SysView A, const uint32_t *__restrict__ cseg, const uint32_t *__restrict__ irow,
                  const double *__restrict__ ival, const double *__restrict__ y,
-                 double *__restrict__ part, int nsplit)
+                 double *__restrict__ part, int nwin)
 {
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    instr_body<SQ>(A, iseg, irow, ival, y, part, nsplit, warp, nwarps);
+    instr_body<SQ>(A, cseg, irow, ival, y, part, nwin, warp, nwarps);
 }
 
 // ival[e] = val[17 + code % 6][code / 6] for the entry code 6 row + slot
@@ -477,7 +476,7 @@ k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
 template <int G, int MODE>
 __global__ void __launch_bounds__(kThreads)
 k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out,
-               double *__restrict__ S, const uint32_t *__restrict__ iseg,
+               double *__restrict__ S, const uint32_t *__restrict__ cseg,
                const uint32_t *__restrict__ irow, const double *__restrict__ ival,
                double *__restrict__ part, int nsplit, double *__restrict__ gpart, A2Queue q)
 {
@@ -517,7 +516,7 @@ k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out
         } else {
             const int64_t i = c * q.ni + (slot - q.ns - q.na);
             if (i < q.ninstr_units)
-                instr_body<SQ>(A, iseg, irow, ival, y, part, nsplit, i, q.ninstr_units);
+                instr_body<SQ>(A, cseg, irow, ival, y, part, nsplit, i, q.ninstr_units);
         }
     }
 }
@@ -759,7 +758,7 @@ template <int G, int MODE>
 static void fused_launch(const gsr_handle_t *h, const double *y, double *out, cudaStream_t st)
 {
     k_aprod2_fused<G, MODE><<<h->grid_fused, kThreads, 0, st>>>(
-        h->sys, y, out, h->d_attS, h->d_iseg, h->d_irow, h->d_ival, h->d_ipart, h->isplit,
+        h->sys, y, out, h->d_attS, h->d_cseg, h->d_irow, h->d_ival, h->d_ipart, h->isplit,
         h->d_gpart, a2_queue(h, G));
 }
 
@@ -819,10 +818,10 @@ static cudaError_t a2_rest(const gsr_handle_t *h, const double *y, double *out, 
     if (h->ipath == kIpSorted) {
         if (mode == kA2Squares)
             k_instr_segments<true><<<h->grid_ins, kThreads, 0, st>>>(
-                h->sys, h->d_iseg, h->d_irow, h->d_ival, y, h->d_ipart, h->isplit);
+                h->sys, h->d_cseg, h->d_irow, h->d_ival, y, h->d_ipart, h->isplit);
         else
             k_instr_segments<false><<<h->grid_ins, kThreads, 0, st>>>(
-                h->sys, h->d_iseg, h->d_irow, h->d_ival, y, h->d_ipart, h->isplit);
+                h->sys, h->d_cseg, h->d_irow, h->d_ival, y, h->d_ipart, h->isplit);
         return launch_att_combine(h, out, nb_att, instr_combine_blocks(h), h->d_ipart, h->isplit,
                                   h->d_gpart, ngpart, mode == kA2Accumulate, st);
     }

@@ -318,23 +318,22 @@ k_att_segments_f32(SysView A, const float *__restrict__ y32, double *__restrict_
 }
 
 // inner aprod 2, instrumental part over the instrument-sorted binary32 copy:
-// chunk q of instrument f (unit w = f nsplit + q), four gathers in flight
-// per lane, double-float sums, chunk total to part[q I + f]
-__device__ __forceinline__ void instr_body_f32(const SysView &A, const uint32_t *__restrict__ iseg,
+// instrument f in row window q (unit w = q I + f), four gathers in flight
+// per lane, double-float sums, window total to part[q I + f]
+__device__ __forceinline__ void instr_body_f32(const SysView &A, const uint32_t *__restrict__ cseg,
                                                const uint32_t *__restrict__ irow,
                                                const float *__restrict__ ival32,
                                                const float *__restrict__ y32,
-                                               double *__restrict__ part, int nsplit, int64_t warp,
+                                               double *__restrict__ part, int nwin, int64_t warp,
                                                int64_t nwarps)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t w = warp; w < A.I * nsplit; w += nwarps) {
-        const int64_t f = w / nsplit;
-        const int q = (int)(w - f * nsplit);
-        const uint32_t s0 = iseg[f];
-        const uint64_t len = iseg[f + 1] - s0;
-        const uint32_t e1 = s0 + (uint32_t)(len * (q + 1) / nsplit);
-        uint32_t e = s0 + (uint32_t)(len * q / nsplit) + lane;
+    for (int64_t w = warp; w < A.I * nwin; w += nwarps) {
+        // unit w: instrument f in row window q, window-major
+        const int64_t q = w / A.I;
+        const int64_t f = w - q * A.I;
+        const uint32_t e1 = cseg[w + A.I];
+        uint32_t e = cseg[w] + lane;
         float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
         for (; e + 96 < e1; e += 128) {
             uint32_t r[4];
@@ -358,7 +357,7 @@ __device__ __forceinline__ void instr_body_f32(const SysView &A, const uint32_t 
         df_add(h[0], l[0], h[2], l[2]);
         df_warp_sum(h[0], l[0]);
         if (lane == 0)
-            part[(int64_t)q * A.I + f] = df_to_d(h[0], l[0]);
+            part[q * A.I + f] = df_to_d(h[0], l[0]);
     }
 }
 
@@ -368,7 +367,7 @@ __device__ __forceinline__ void instr_body_f32(const SysView &A, const uint32_t 
 template <int G, int MODE>
 __global__ void __launch_bounds__(kThreads)
 k_aprod2_f32_fused(SysView A, const float *__restrict__ y32, double *__restrict__ out,
-                   double *__restrict__ S, const uint32_t *__restrict__ iseg,
+                   double *__restrict__ S, const uint32_t *__restrict__ cseg,
                    const uint32_t *__restrict__ irow, const float *__restrict__ ival32,
                    double *__restrict__ part, int nsplit, double *__restrict__ gpart, A2Queue q)
 {
@@ -404,7 +403,7 @@ k_aprod2_f32_fused(SysView A, const float *__restrict__ y32, double *__restrict_
         } else {
             const int64_t i = c * q.ni + (slot - q.ns - q.na);
             if (i < q.ninstr_units)
-                instr_body_f32(A, iseg, irow, ival32, y32, part, nsplit, i, q.ninstr_units);
+                instr_body_f32(A, cseg, irow, ival32, y32, part, nsplit, i, q.ninstr_units);
         }
     }
 }
@@ -642,7 +641,7 @@ static cudaError_t a2f_launch(const gsr_handle_t *h, const float *y32, double *o
     if (h->ipath == kIpSorted && h->a2_fused) {
         const A2Queue q = a2_queue(h, G);
         k_aprod2_f32_fused<G, MODE><<<h->grid_fused32, kThreads, 0, st>>>(
-            h->sys, y32, out, h->d_attS, h->d_iseg, h->d_irow, h->d_ival32, h->d_ipart, h->isplit,
+            h->sys, y32, out, h->d_attS, h->d_cseg, h->d_irow, h->d_ival32, h->d_ipart, h->isplit,
             h->d_gpart, q);
         const int nb_att = (int)((3 * h->sys.D + kThreads - 1) / kThreads < 4 * h->nsm
                                      ? (3 * h->sys.D + kThreads - 1) / kThreads
@@ -710,7 +709,7 @@ static cudaError_t cg_iteration(const gsr_handle_t *h, cudaStream_t s, cudaGraph
         // single-launch aprod 2 without the combine; the CG pass combines
         const A2Queue q = a2_queue(h, 8);
         k_aprod2_f32_fused<8, kA2Overwrite><<<h->grid_fused32, kThreads, 0, s>>>(
-            h->sys, h->d_q32, h->d_t, h->d_attS, h->d_iseg, h->d_irow, h->d_ival32, h->d_ipart,
+            h->sys, h->d_q32, h->d_t, h->d_attS, h->d_cseg, h->d_irow, h->d_ival32, h->d_ipart,
             h->isplit, h->d_gpart, q);
         P = {h->d_attS, h->d_ipart, h->isplit, h->d_gpart, (int)q.nstar_units, h->d_a2ctr};
         k_cg_vec1<true><<<h->grid_vec, kThreads, 0, s>>>(A, h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc,
