@@ -143,7 +143,7 @@ static void release(gsr_handle_t *h)
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err,
                    h->d_val32, h->d_tval32, h->d_x32, h->d_xatt4, h->d_q32, h->d_c, h->d_s, h->d_d, h->d_t,
                    h->d_zc, h->d_xm, h->d_r, h->d_xneg, h->d_onorm, h->d_cg, h->d_cgargs,
-                   h->d_xp64, h->d_q64, h->d_iseg, h->d_cseg, h->d_irow, h->d_ival32, h->d_ival, h->d_ipart, h->d_gpart, h->d_a2ctr, h->d_bX32, h->d_bQ32,
+                   h->d_xp64, h->d_q64, h->d_iseg, h->d_cseg, h->d_cseg32, h->d_irow, h->d_ival32, h->d_ival, h->d_ipart, h->d_gpart, h->d_a2ctr, h->d_bX32, h->d_bQ32,
                    h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT, h->d_bS, h->d_bXcm,
                    h->d_bCcm, h->d_bB, h->d_bnorms, h->d_bpartial, h->d_bcounter, h->d_bs,
                    h->d_bipart,
@@ -230,8 +230,34 @@ static int build_instr_sorted(gsr_handle_t *h, cudaStream_t st)
     TRY(dalloc(h, &h->d_cseg, (nq + 1) * I));
     CK(cudaMemcpy(h->d_cseg, cseg.data(), (nq + 1) * I * sizeof(uint32_t), cudaMemcpyHostToDevice));
     h->isplit = (int)nq;
-    TRY(dalloc(h, &h->d_ipart, (int64_t)h->isplit * I));
-    CK(cudaMemset(h->d_ipart, 0, (size_t)h->isplit * I * sizeof(double)));
+    int64_t nparts = nq;
+    if (h->cfg.precision == GSR_PREC_MIXED) {
+        // binary32 units: windows of 32 MB of binary32 y (8 Mi rows), each
+        // instrument's window cut by count into ks32 pieces of <= 4096 entries
+        const int64_t R32 = (int64_t)1 << 23;
+        const int64_t nq32 = (m + R32 - 1) / R32;
+        const int64_t per = kNInstr * (R32 < m ? R32 : m) / I + 1;  // entries per window
+        const int64_t ks32 = (per + 4095) / 4096;
+        std::vector<uint32_t> c32((size_t)((nq32 + 1) * I));
+        for (int64_t f = 0; f < I; f++) {
+            uint32_t e = seg[f];
+            for (int64_t q = 0; q < nq32; q++) {
+                c32[q * I + f] = e;
+                while (e < seg[f + 1] && (int64_t)irow[e] < (q + 1) * R32)
+                    e++;
+            }
+            c32[nq32 * I + f] = seg[f + 1];
+        }
+        TRY(dalloc(h, &h->d_cseg32, (nq32 + 1) * I));
+        CK(cudaMemcpy(h->d_cseg32, c32.data(), (nq32 + 1) * I * sizeof(uint32_t),
+                      cudaMemcpyHostToDevice));
+        h->nq32 = (int)nq32;
+        h->ks32 = (int)ks32;
+        if (nq32 * ks32 > nparts)
+            nparts = nq32 * ks32;
+    }
+    TRY(dalloc(h, &h->d_ipart, nparts * I));
+    CK(cudaMemset(h->d_ipart, 0, (size_t)nparts * I * sizeof(double)));
     const int64_t units_blocks = (I * h->isplit + kThreads / 32 - 1) / (kThreads / 32);
     const int64_t cap = (int64_t)h->nsm * 16;
     h->grid_ins = (int)(units_blocks < cap ? units_blocks : cap);

@@ -196,6 +196,10 @@ struct gsr_handle_t {
                                         // window q are cseg[q I + f] .. cseg[(q+1) I + f]-1
     double *d_ipart = nullptr;          // [isplit][I] per-window instrumental sums
     int isplit = 1;                     // row windows of the instrumental sums
+    // binary32 units: row window q (8 Mi rows) of instrument f, cut by count
+    // into ks32 pieces; partial sums at d_ipart[(q ks32 + k) I + f]
+    uint32_t *d_cseg32 = nullptr;       // [nq32+1][I] window bounds as d_cseg
+    int nq32 = 1, ks32 = 1;
     double *d_gpart = nullptr;          // per-block partials of the global column (star pass)
     int a2_fused = 1;                   // aprod 2 in one launch (sorted path), else separate passes
     unsigned long long *d_a2ctr = nullptr;  // work counter of the single-launch aprod 2
@@ -288,7 +292,7 @@ cudaError_t launch_att_combine(const gsr_handle_t *h, double *out, int nb_att, i
                                double *rep, int nrep, const double *gpart, int ngpart,
                                bool accumulate, cudaStream_t st, unsigned long long *ctr = nullptr);
 int instr_path(const gsr_config &cfg, int64_t I);
-A2Queue a2_queue(const gsr_handle_t *h, int G);
+A2Queue a2_queue(const gsr_handle_t *h, int G, int64_t ninstr_units = -1);
 bool aprod2_partials(const gsr_handle_t *h, const double *y, double *out, const double **S,
                      const double **ipart, int *isplit, const double **gpart, int *ngpart,
                      unsigned long long **ctr, cudaStream_t st);

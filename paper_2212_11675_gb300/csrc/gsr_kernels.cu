@@ -331,9 +331,10 @@ __device__ __forceinline__ void instr_body(const SysView &A, const uint32_t *__r
 {
     const int lane = threadIdx.x & 31;
     for (int64_t w = warp; w < A.I * nwin; w += nwarps) {
-        // unit w: instrument f in row window q, window-major
-        const int64_t q = w / A.I;
-        const int64_t f = w - q * A.I;
+        // unit w: instrument f in row window q, window-major (32-bit decode)
+        const uint32_t I = (uint32_t)A.I;
+        const uint32_t q = (uint32_t)w / I;
+        const uint32_t f = (uint32_t)w - q * I;
         const uint32_t e1 = cseg[w + A.I];
         uint32_t e = cseg[w] + lane;
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -367,7 +368,7 @@ __device__ __forceinline__ void instr_body(const SysView &A, const uint32_t *__r
         }
         const double t = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
         if (lane == 0)
-            part[q * A.I + f] = t;
+            part[(size_t)q * I + f] = t;
     }
 }
 
@@ -724,14 +725,14 @@ static cudaError_t launch_aprod2_split(const gsr_handle_t *h, const double *y, d
 // attitude segment at the medium size)
 constexpr int kStarGroupsPerUnit = 4;
 
-A2Queue a2_queue(const gsr_handle_t *h, int G)
+A2Queue a2_queue(const gsr_handle_t *h, int G, int64_t ninstr_units)
 {
     A2Queue q;
     q.ctr = h->d_a2ctr;
     q.star_k = kStarGroupsPerUnit;
     q.nstar_groups = (h->sys.S + 32 / G - 1) / (32 / G);
     q.nstar_units = (q.nstar_groups + q.star_k - 1) / q.star_k;
-    q.ninstr_units = h->sys.I * h->isplit;
+    q.ninstr_units = ninstr_units >= 0 ? ninstr_units : h->sys.I * h->isplit;
     const int64_t n[3] = {q.nstar_units, h->sys.nseg, q.ninstr_units};
     const int64_t tot = n[0] + n[1] + n[2];
     int sl[3];

@@ -318,22 +318,23 @@ k_att_segments_f32(SysView A, const float *__restrict__ y32, double *__restrict_
 }
 
 // inner aprod 2, instrumental part over the instrument-sorted binary32 copy:
-// instrument f in row window q (unit w = q I + f), four gathers in flight
-// per lane, double-float sums, window total to part[q I + f]
-__device__ __forceinline__ void instr_body_f32(const SysView &A, const uint32_t *__restrict__ cseg,
+// piece k of instrument f in row window q (unit w = (q I + f) ks + k), four
+// gathers in flight per lane, double-float sums, total to part[(q ks + k) I + f]
+__device__ __forceinline__ void instr_body_f32_one(const SysView &A, const uint32_t *__restrict__ iseg,
                                                const uint32_t *__restrict__ irow,
                                                const float *__restrict__ ival32,
                                                const float *__restrict__ y32,
-                                               double *__restrict__ part, int nwin, int64_t warp,
+                                               double *__restrict__ part, int nsplit, int64_t warp,
                                                int64_t nwarps)
 {
     const int lane = threadIdx.x & 31;
-    for (int64_t w = warp; w < A.I * nwin; w += nwarps) {
-        // unit w: instrument f in row window q, window-major
-        const int64_t q = w / A.I;
-        const int64_t f = w - q * A.I;
-        const uint32_t e1 = cseg[w + A.I];
-        uint32_t e = cseg[w] + lane;
+    for (int64_t w = warp; w < A.I * nsplit; w += nwarps) {
+        const int64_t f = w / nsplit;
+        const int q = (int)(w - f * nsplit);
+        const uint32_t s0 = iseg[f];
+        const uint64_t len = iseg[f + 1] - s0;
+        const uint32_t e1 = s0 + (uint32_t)(len * (q + 1) / nsplit);
+        uint32_t e = s0 + (uint32_t)(len * q / nsplit) + lane;
         float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
         for (; e + 96 < e1; e += 128) {
             uint32_t r[4];
@@ -357,19 +358,66 @@ __device__ __forceinline__ void instr_body_f32(const SysView &A, const uint32_t 
         df_add(h[0], l[0], h[2], l[2]);
         df_warp_sum(h[0], l[0]);
         if (lane == 0)
-            part[q * A.I + f] = df_to_d(h[0], l[0]);
+            part[(int64_t)q * A.I + f] = df_to_d(h[0], l[0]);
+    }
+}
+
+__device__ __forceinline__ void instr_body_f32_win(const SysView &A, const uint32_t *__restrict__ seg,
+                                               const uint32_t *__restrict__ irow,
+                                               const float *__restrict__ ival32,
+                                               const float *__restrict__ y32,
+                                               double *__restrict__ part, int nwin, int ks,
+                                               int64_t warp, int64_t nwarps)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t per = A.I * ks;  // units per window
+    for (int64_t w = warp; w < per * nwin; w += nwarps) {
+        // unit w: piece k of instrument f in row window q (window-major,
+        // then instrument-major); seg is the window table (d_cseg32)
+        const int64_t q = w / per;
+        const int64_t r = w - q * per;
+        const int64_t f = r / ks;
+        const int k = (int)(r - f * ks);
+        const uint32_t s0 = seg[q * A.I + f];
+        const uint64_t len = seg[(q + 1) * A.I + f] - s0;
+        const uint32_t e1 = s0 + (uint32_t)(len * (k + 1) / ks);
+        uint32_t e = s0 + (uint32_t)(len * k / ks) + lane;
+        float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+        for (; e + 96 < e1; e += 128) {
+            uint32_t r[4];
+            float v[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                r[u] = __ldcs(irow + e + 32 * u);
+                v[u] = __ldcs(ival32 + e + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                yv[u] = __ldg(y32 + r[u]);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                df_acc(h[u], l[u], __fmul_rn(v[u], yv[u]));
+        }
+        for (int u = 0; e < e1; e += 32, u++)
+            df_acc(h[u & 3], l[u & 3], __fmul_rn(__ldcs(ival32 + e), __ldg(y32 + __ldcs(irow + e))));
+        df_add(h[0], l[0], h[1], l[1]);
+        df_add(h[2], l[2], h[3], l[3]);
+        df_add(h[0], l[0], h[2], l[2]);
+        df_warp_sum(h[0], l[0]);
+        if (lane == 0)
+            part[(q * ks + k) * A.I + f] = df_to_d(h[0], l[0]);
     }
 }
 
 // inner aprod 2 in one launch (sorted instrumental path), the binary32 form
 // of k_aprod2_fused: units of the three kinds from one work queue, one
 // global-column partial per star unit
-template <int G, int MODE>
+template <int G, int MODE, bool WIN>
 __global__ void __launch_bounds__(kThreads)
 k_aprod2_f32_fused(SysView A, const float *__restrict__ y32, double *__restrict__ out,
                    double *__restrict__ S, const uint32_t *__restrict__ cseg,
                    const uint32_t *__restrict__ irow, const float *__restrict__ ival32,
-                   double *__restrict__ part, int nsplit, double *__restrict__ gpart, A2Queue q)
+                   double *__restrict__ part, int nsplit, int ks, double *__restrict__ gpart, A2Queue q)
 {
     const int lane = threadIdx.x & 31;
     const int L = q.ns + q.na + q.ni;
@@ -403,7 +451,11 @@ k_aprod2_f32_fused(SysView A, const float *__restrict__ y32, double *__restrict_
         } else {
             const int64_t i = c * q.ni + (slot - q.ns - q.na);
             if (i < q.ninstr_units)
-                instr_body_f32(A, cseg, irow, ival32, y32, part, nsplit, i, q.ninstr_units);
+                if (WIN)
+                    instr_body_f32_win(A, cseg, irow, ival32, y32, part, nsplit, ks, i,
+                                       q.ninstr_units);
+                else  // one window: pieces by count over iseg
+                    instr_body_f32_one(A, cseg, irow, ival32, y32, part, ks, i, q.ninstr_units);
         }
     }
 }
@@ -639,15 +691,20 @@ static cudaError_t a2f_launch(const gsr_handle_t *h, const float *y32, double *o
 {
     const int G = 8;
     if (h->ipath == kIpSorted && h->a2_fused) {
-        const A2Queue q = a2_queue(h, G);
-        k_aprod2_f32_fused<G, MODE><<<h->grid_fused32, kThreads, 0, st>>>(
-            h->sys, y32, out, h->d_attS, h->d_cseg, h->d_irow, h->d_ival32, h->d_ipart, h->isplit,
-            h->d_gpart, q);
+        const A2Queue q = a2_queue(h, G, (int64_t)h->sys.I * h->nq32 * h->ks32);
+        if (h->nq32 > 1)
+            k_aprod2_f32_fused<G, MODE, true><<<h->grid_fused32, kThreads, 0, st>>>(
+                h->sys, y32, out, h->d_attS, h->d_cseg32, h->d_irow, h->d_ival32, h->d_ipart,
+                h->nq32, h->ks32, h->d_gpart, q);
+        else
+            k_aprod2_f32_fused<G, MODE, false><<<h->grid_fused32, kThreads, 0, st>>>(
+                h->sys, y32, out, h->d_attS, h->d_iseg, h->d_irow, h->d_ival32, h->d_ipart, 1,
+                h->ks32, h->d_gpart, q);
         const int nb_att = (int)((3 * h->sys.D + kThreads - 1) / kThreads < 4 * h->nsm
                                      ? (3 * h->sys.D + kThreads - 1) / kThreads
                                      : 4 * h->nsm);
         const int nb_ins = (int)((h->sys.I + kThreads / 32 - 1) / (kThreads / 32));
-        launch_att_combine(h, out, nb_att, nb_ins, h->d_ipart, h->isplit, h->d_gpart,
+        launch_att_combine(h, out, nb_att, nb_ins, h->d_ipart, h->nq32 * h->ks32, h->d_gpart,
                            (int)q.nstar_units, MODE == kA2Accumulate, st, h->d_a2ctr);
         return cudaGetLastError();
     }
@@ -707,11 +764,16 @@ static cudaError_t cg_iteration(const gsr_handle_t *h, cudaStream_t s, cudaGraph
     unsigned *cnt = h->d_counter + kRedV;
     if (h->ipath == kIpSorted && h->a2_fused) {
         // single-launch aprod 2 without the combine; the CG pass combines
-        const A2Queue q = a2_queue(h, 8);
-        k_aprod2_f32_fused<8, kA2Overwrite><<<h->grid_fused32, kThreads, 0, s>>>(
-            h->sys, h->d_q32, h->d_t, h->d_attS, h->d_cseg, h->d_irow, h->d_ival32, h->d_ipart,
-            h->isplit, h->d_gpart, q);
-        P = {h->d_attS, h->d_ipart, h->isplit, h->d_gpart, (int)q.nstar_units, h->d_a2ctr};
+        const A2Queue q = a2_queue(h, 8, (int64_t)A.I * h->nq32 * h->ks32);
+        if (h->nq32 > 1)
+            k_aprod2_f32_fused<8, kA2Overwrite, true><<<h->grid_fused32, kThreads, 0, s>>>(
+                h->sys, h->d_q32, h->d_t, h->d_attS, h->d_cseg32, h->d_irow, h->d_ival32,
+                h->d_ipart, h->nq32, h->ks32, h->d_gpart, q);
+        else
+            k_aprod2_f32_fused<8, kA2Overwrite, false><<<h->grid_fused32, kThreads, 0, s>>>(
+                h->sys, h->d_q32, h->d_t, h->d_attS, h->d_iseg, h->d_irow, h->d_ival32, h->d_ipart,
+                1, h->ks32, h->d_gpart, q);
+        P = {h->d_attS, h->d_ipart, h->nq32 * h->ks32, h->d_gpart, (int)q.nstar_units, h->d_a2ctr};
         k_cg_vec1<true><<<h->grid_vec, kThreads, 0, s>>>(A, h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc,
                                                          h->d_cg, h->d_cgargs, part, cnt, loop,
                                                          in_graph, P);
@@ -862,7 +924,7 @@ int aprod2_f32_fused_grid(const gsr_handle_t *h)
 {
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, k_aprod2_f32_fused<8, kA2Overwrite>, kThreads, 0);
+        &occ, k_aprod2_f32_fused<8, kA2Overwrite, true>, kThreads, 0);
     if (e != cudaSuccess || occ <= 0)
         return -1;
     return h->nsm * occ;
