@@ -511,7 +511,7 @@ def main():
     # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
     # --set full capture of the in-solve launches on the medium workload (null
     # for another workload, and to be nulled once that kernel changes)
-    traffic = {"aprod2": 2.2158e9 + 0.0247e9, "aprod1": 1.5328e9 + 0.0077e9}.get(dom) \
+    traffic = {"aprod2": 1.9440e9 + 0.0103e9, "aprod1": 1.5330e9 + 0.0078e9}.get(dom) \
         if args.workload == "medium" else None
     f_hbm = gbs_dom / hbm
     f_alu = tf_dom / FP64_NOMINAL_TFLOPS
