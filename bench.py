@@ -104,6 +104,18 @@ def dist_env():
     return ws, rank, local
 
 
+def whole_job(iters, t, dist, dev, torch):
+    """Replicas: the iterations of all ranks and the slowest rank's time (the
+    whole job's throughput is their ratio); one rank without dist."""
+    if not dist:
+        return float(iters), float(t)
+    it_all = torch.tensor([float(iters)], dtype=torch.float64, device=dev)
+    t_all = torch.tensor([float(t)], dtype=torch.float64, device=dev)
+    dist.all_reduce(it_all, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    return float(it_all), float(t_all)
+
+
 def make_system(workload, rank):
     shape = gen.SHAPES[workload]
     seed = gen.SEEDS[workload] + 7919 * rank
@@ -461,16 +473,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) * 1e-3
-    # whole job: iterations of all ranks over the slowest rank's time
-    tot = torch.tensor([iters, t], dtype=torch.float64, device=dev)
-    if dist:
-        it_all = tot[:1].clone()
-        dist.all_reduce(it_all, op=dist.ReduceOp.SUM)
-        t_all = tot[1:].clone()
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-        iters_total, t_max = float(it_all), float(t_all)
-    else:
-        iters_total, t_max = float(iters), t
+    iters_total, t_max = whole_job(iters, t, dist, dev, torch)
     value = iters_total / t_max
 
     # end to end through the C ABI with host buffers (H2D of b and D2H of x,
