@@ -54,10 +54,13 @@ extern "C" {
 
 /* Accumulation of the instrumental columns in aprod 2. */
 #define GSR_INSTR_AUTO 0     /* GSR_INSTR_SORTED */
-#define GSR_INSTR_SMEM 1     /* shared memory per block (needs I <= 6144, else replicas) */
+#define GSR_INSTR_SMEM 1     /* shared-memory sums per block (I <= 6144; larger I is
+                                GSR_ERR_UNSUPPORTED) */
 #define GSR_INSTR_REPLICAS 2 /* one replica per SM in device memory, L2 reductions */
-#define GSR_INSTR_SORTED 3   /* instrument-sorted copy of the instrumental values:
-                                per-instrument segment sums, no atomics, deterministic */
+#define GSR_INSTR_SORTED 3   /* instrument-sorted copy of the instrumental values,
+                                summed per instrument and row window (the gathered
+                                y of a window stays in L2): no atomics, and aprod 2
+                                is deterministic */
 
 /* Storage and arithmetic of the matrix values. */
 #define GSR_PREC_FP64 0  /* IEEE double values, native FP64 arithmetic */

@@ -95,3 +95,23 @@ def test_mixed_solve_host_buffers_and_errors():
         with pytest.raises(_lib.GsrError) as e:
             s64.mixed_solve(b)
         assert e.value.code == _lib.GSR_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("mode,fused", [(_lib.GSR_INSTR_SORTED, False), (_lib.GSR_INSTR_SMEM, None),
+                                        (_lib.GSR_INSTR_REPLICAS, None)])
+def test_mixed_solve_other_schedules(mode, fused):
+    # the inner solve's aprod 2 as separate launches, and on the shared-memory
+    # and replica instrumental paths (the inner CG graph is captured again
+    # when the schedule changes)
+    sys = small(257, 37, 11, seed=31)
+    xt = gen.x_true(sys, 3)
+    b = oracle.aprod1(sys, xt) + gen.noise(sys, 4)
+    ref = _fp64_solution(sys, b)
+    with _solver(sys, instr_mode=mode) as s:
+        if fused is not None:
+            s.set_aprod2_fused(fused)
+        x, res = s.mixed_solve(torch.tensor(b, device=DEV), max_outer=20, max_inner=200,
+                               inner_tol=1e-5, atol=1e-13)
+        x = x.cpu().numpy()
+    assert res["converged"] == 1, res
+    assert np.linalg.norm(x - ref["x"]) <= 1e-9 * np.linalg.norm(ref["x"]), res
