@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -137,7 +138,7 @@ static void release(gsr_handle_t *h)
         cudaFreeHost(h->h_onorm);
     if (h->cap_stream)
         cudaStreamDestroy(h->cap_stream);
-    void *dev[] = {h->d_star_ptr, h->d_rec, h->d_val, h->d_tile_star, h->d_sdelta, h->d_tval, h->d_perm,
+    void *dev[] = {h->d_star_ptr, h->d_rec, h->d_val, h->d_tile_star, h->d_sdelta, h->d_sorder, h->d_tval, h->d_perm,
                    h->d_seg, h->d_attS, h->d_irep, h->d_p, h->d_u, h->d_v, h->d_w, h->d_z,
                    h->d_var, h->d_q, h->d_vp, h->d_vt, h->d_bstage, h->d_xstage, h->d_sestage,
                    h->d_ystage, h->d_state, h->d_args, h->d_partial, h->d_counter, h->d_err,
@@ -324,6 +325,7 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     TRY(dalloc(h, &h->d_val, kNPar * mp));
     TRY(dalloc(h, &h->d_tile_star, ntiles));
     TRY(dalloc(h, &h->d_sdelta, m));
+    TRY(dalloc(h, &h->d_sorder, S));
     TRY(dalloc(h, &h->d_tval, (int64_t)kNAtt * mp));
     TRY(dalloc(h, &h->d_perm, m));
     TRY(dalloc(h, &h->d_seg, A.nseg + 1));
@@ -351,6 +353,7 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     A.val = h->d_val;
     A.tile_star = h->d_tile_star;
     A.sdelta = h->d_sdelta;
+    A.sorder = h->d_sorder;
     A.tval = h->d_tval;
     A.perm = h->d_perm;
     A.seg = h->d_seg;
@@ -421,6 +424,18 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
         return GSR_ERR_INDEX;
     if (err & 8)
         return GSR_ERR_NONFINITE;
+
+    // stars in decreasing row count (stable): the star groups of aprod 2
+    {
+        std::vector<uint32_t> sp((size_t)S + 1), order((size_t)S);
+        CK(cudaMemcpy(sp.data(), h->d_star_ptr, (S + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        for (int64_t s = 0; s < S; s++)
+            order[s] = (uint32_t)s;
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+            return sp[a + 1] - sp[a] > sp[b + 1] - sp[b];
+        });
+        CK(cudaMemcpy(h->d_sorder, order.data(), S * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
 
     // attitude copy sorted by offset: a stable counting sort on the host
     // (row order kept inside every offset, so the sums have a fixed order)

@@ -27,6 +27,7 @@ struct SysView {
     const float *tval32;       // [12][mp] binary32 offset-sorted attitude copy, or null
     const uint32_t *tile_star; // [ceil(m/32)] star of the first row of each 32-row tile
     const uint16_t *sdelta;    // [m] star of row r minus tile_star[r/32]; 0xffff: walk on
+    const uint32_t *sorder;    // [S] stars by decreasing row count (star groups of aprod 2)
     // attitude values re-ordered by attitude offset (stable in the row index):
     // entry e is row perm[e]; offset o owns entries seg[o] .. seg[o+1]-1
     const double *tval;        // [12][mp]
@@ -181,6 +182,7 @@ struct gsr_handle_t {
     double *d_val = nullptr;
     uint32_t *d_tile_star = nullptr;
     uint16_t *d_sdelta = nullptr;
+    uint32_t *d_sorder = nullptr;
     double *d_tval = nullptr;
     uint32_t *d_perm = nullptr, *d_seg = nullptr;
     double *d_attS = nullptr;           // [nseg][12] attitude segment sums

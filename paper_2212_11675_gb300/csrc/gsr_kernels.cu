@@ -174,7 +174,9 @@ __device__ __forceinline__ double stars_body(const SysView &A, const double *__r
     const int64_t mp = A.mp;
     double gacc = 0.0;
     for (int64_t s0 = warp * GPW; s0 < A.S; s0 += nwarps * GPW) {
-        const int64_t s = s0 + gw;
+        // the GPW stars of a warp have similar row counts (stars taken in
+        // decreasing row count), so its lane groups finish together
+        const int64_t s = (s0 + gw < A.S) ? (int64_t)A.sorder[s0 + gw] : A.S;
         uint32_t r0 = 0, r1 = 0;
         if (s < A.S) {
             r0 = A.star_ptr[s];
