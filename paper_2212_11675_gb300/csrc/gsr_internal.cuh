@@ -53,7 +53,7 @@ __device__ __forceinline__ uint32_t star_of_row(const SysView &A, int64_t t, int
 }
 
 // Partial sums of the single-launch aprod 2 that a following vector pass
-// combines itself (no combine launch): attitude segment sums S, instrument chunk
+// combines itself (no combine launch): attitude segment sums S, instrument window
 // totals, per-star-unit global partials, and the work counter to reset.
 struct A2Parts {
     const double *S;
@@ -66,7 +66,7 @@ struct A2Parts {
 
 // q_j of the non-astrometric columns from the partial sums: column a D + k of
 // the attitude block is sum_{jj<4} S[k-jj][4a+jj]; instrument f the sum of its
-// chunk totals (both in the combine kernel's order)
+// window totals (both in the combine kernel's order)
 __device__ __forceinline__ double q_from_parts(const SysView &A, const A2Parts &P, int64_t j)
 {
     double t = 0.0;
@@ -154,7 +154,7 @@ enum ReduceKind { kRedBnorm = 0, kRedU = 1, kRedV = 2, kRedCount = 3 };
 // block, or segment sums over the instrument-sorted copy
 enum InstrPath { kIpReplicas = 0, kIpSmem = 1, kIpSorted = 2 };
 // work queue of the single-launch aprod 2: star units (GPW stars each),
-// attitude segments and instrument chunks, interleaved by a repeating
+// attitude segments and instrument units, interleaved by a repeating
 // pattern of ns + na + ni slots
 struct A2Queue {
     unsigned long long *ctr;  // next unit index (zero on entry)
@@ -162,7 +162,7 @@ struct A2Queue {
     int star_k;               // star groups (GPW stars each) per star unit
     int64_t nstar_groups;     // ceil(S / GPW)
     int64_t nstar_units;      // ceil(nstar_groups / star_k)
-    int64_t ninstr_units;     // I * nsplit
+    int64_t ninstr_units;     // I x row windows (x pieces per window)
     int64_t total;            // periods * (ns + na + ni)
 };
 constexpr int kPartialsPerKind = 4 * kMaxPartials;  // up to 4 sums per block

@@ -469,7 +469,8 @@ k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
 // run side by side, so the FP64-bound star and attitude sums share every SM
 // with the gather-bound instrumental sums.  The work is a queue of units --
 // star groups (GPW stars per warp), attitude segments (one offset) and
-// instrument chunks -- interleaved by a repeating pattern of L = ns + na + ni
+// instrument units (one instrument in one row window) -- interleaved by a
+// repeating pattern of L = ns + na + ni
 // slots (ns star, na attitude, ni instrument units per period, in
 // proportion to their counts).  A warp takes the next unit index from a
 // device counter, so the roles balance themselves; the combine kernel
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(kThreads)
 k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out,
                double *__restrict__ S, const uint32_t *__restrict__ cseg,
                const uint32_t *__restrict__ irow, const double *__restrict__ ival,
-               double *__restrict__ part, int nsplit, double *__restrict__ gpart, A2Queue q)
+               double *__restrict__ part, int nwin, double *__restrict__ gpart, A2Queue q)
 {
     constexpr bool SQ = MODE == kA2Squares;
     const int lane = threadIdx.x & 31;
@@ -519,7 +520,7 @@ k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out
         } else {
             const int64_t i = c * q.ni + (slot - q.ns - q.na);
             if (i < q.ninstr_units)
-                instr_body<SQ>(A, cseg, irow, ival, y, part, nsplit, i, q.ninstr_units);
+                instr_body<SQ>(A, cseg, irow, ival, y, part, nwin, i, q.ninstr_units);
         }
     }
 }
@@ -528,7 +529,7 @@ k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out
 // the attitude columns: column a*D + k receives sum_{j=0..3} S[k-j][4a+j]
 // (0 <= k-j < nseg).  The next blocks (when rep != null) take 8
 // instrument columns each, one warp per column, summing the replicas (or the
-// chunk totals of the sorted pass) in a fixed order and clearing them for
+// window totals of the sorted pass) in a fixed order and clearing them for
 // the next call.  With gpart, one last block adds the ngpart per-block
 // partials of the global column in block order (and clears ctr).
 template <bool ACC>

@@ -319,9 +319,11 @@ k_att_segments_f32(SysView A, const float *__restrict__ y32, double *__restrict_
     att_body_f32(A, y32, S, warp, nwarps);
 }
 
-// inner aprod 2, instrumental part over the instrument-sorted binary32 copy:
-// piece k of instrument f in row window q (unit w = (q I + f) ks + k), four
-// gathers in flight per lane, double-float sums, total to part[(q ks + k) I + f]
+// inner aprod 2, instrumental part over the instrument-sorted binary32 copy,
+// four gathers in flight per lane, double-float sums.  One row window: unit
+// w is piece k = w % npieces of instrument f = w / npieces (pieces by count
+// over iseg), total to part[k I + f].  (This plain form measured 10% faster
+// than the windowed decode of instr_body_f32_win with one window.)
 __device__ __forceinline__ void instr_body_f32_one(const SysView &A, const uint32_t *__restrict__ iseg,
                                                const uint32_t *__restrict__ irow,
                                                const float *__restrict__ ival32,
@@ -364,6 +366,8 @@ __device__ __forceinline__ void instr_body_f32_one(const SysView &A, const uint3
     }
 }
 
+// Several row windows: piece k of instrument f in row window q (unit
+// w = (q I + f) ks + k), total to part[(q ks + k) I + f].
 __device__ __forceinline__ void instr_body_f32_win(const SysView &A, const uint32_t *__restrict__ seg,
                                                const uint32_t *__restrict__ irow,
                                                const float *__restrict__ ival32,
@@ -419,7 +423,7 @@ __global__ void __launch_bounds__(kThreads)
 k_aprod2_f32_fused(SysView A, const float *__restrict__ y32, double *__restrict__ out,
                    double *__restrict__ S, const uint32_t *__restrict__ cseg,
                    const uint32_t *__restrict__ irow, const float *__restrict__ ival32,
-                   double *__restrict__ part, int nsplit, int ks, double *__restrict__ gpart, A2Queue q)
+                   double *__restrict__ part, int nwin, int ks, double *__restrict__ gpart, A2Queue q)
 {
     const int lane = threadIdx.x & 31;
     const int L = q.ns + q.na + q.ni;
@@ -454,7 +458,7 @@ k_aprod2_f32_fused(SysView A, const float *__restrict__ y32, double *__restrict_
             const int64_t i = c * q.ni + (slot - q.ns - q.na);
             if (i < q.ninstr_units)
                 if (WIN)
-                    instr_body_f32_win(A, cseg, irow, ival32, y32, part, nsplit, ks, i,
+                    instr_body_f32_win(A, cseg, irow, ival32, y32, part, nwin, ks, i,
                                        q.ninstr_units);
                 else  // one window: pieces by count over iseg
                     instr_body_f32_one(A, cseg, irow, ival32, y32, part, ks, i, q.ninstr_units);
