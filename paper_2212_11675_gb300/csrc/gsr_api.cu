@@ -571,7 +571,16 @@ extern "C" int gsr_create(void **out, const gsr_dims *d, const uint32_t *star_pt
     if (!h)
         return GSR_ERR_OOM;
     h->cfg = c;
-    int rc = create_impl(h, d, star_ptr, attoff, instr, values);
+    int rc;
+    try {  // the host-side sorts allocate O(m) vectors; no exception leaves the ABI
+        rc = create_impl(h, d, star_ptr, attoff, instr, values);
+    } catch (const std::bad_alloc &) {
+        snprintf(g_last_error, sizeof g_last_error, "host allocation failed in gsr_create");
+        rc = GSR_ERR_OOM;
+    } catch (...) {
+        snprintf(g_last_error, sizeof g_last_error, "unexpected host error in gsr_create");
+        rc = GSR_ERR_CUDA;
+    }
     if (rc != GSR_OK) {
         release(h);
         return rc;
