@@ -368,6 +368,28 @@ def profile_main(args):
     return 0
 
 
+def cpu_baseline_openmp(sys_, seed, seconds):
+    """The multi-threaded (OpenMP) CPU PC-LSQR on all host cores, a second
+    reported baseline (not the oracle), on a bounded sample as cpu_baseline."""
+    import oracle
+    xt = gen.x_true(sys_, seed)
+    b = oracle.aprod1(sys_, xt) + gen.noise(sys_, seed + 1)
+    t0 = time.perf_counter()
+    oracle.omp_pc_lsqr(sys_, b, 1, 0.0, 0.0)
+    t1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.omp_pc_lsqr(sys_, b, 5, 0.0, 0.0)
+    per_it = max((time.perf_counter() - t0 - t1) / 4.0, 1e-6)
+    iters = max(1, min(2000, int((seconds - t1) / per_it)))
+    t0 = time.perf_counter()
+    r = oracle.omp_pc_lsqr(sys_, b, iters, 0.0, 0.0)
+    dt = time.perf_counter() - t0
+    return {"value": r["itn"] / dt, "unit": "iter/s", "cores": oracle.omp_threads(),
+            "kind": "openmp",
+            "sample": "preconditioner + %d LSQR iterations of the same system, OpenMP FP64 C "
+                      "on %d threads (%.1f s)" % (r["itn"], oracle.omp_threads(), dt)}
+
+
 def cpu_baseline(sys_, seed, seconds):
     """The oracle timed on a bounded sample: LSQR iterations of the same system."""
     import oracle
@@ -565,6 +587,7 @@ def main():
         line["batched_vs_sequential_fp64"] = batched
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sys_, seed, args.cpu_seconds)
+        line["cpu_baseline_openmp"] = cpu_baseline_openmp(sys_, seed, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()

@@ -147,3 +147,39 @@ def pc_lsqr(sys, b, itmax, atol=1e-12, btol=1e-12, conlim=1e8, trace=False):
     if trace:
         out["trace_rnorm"] = tr[: out["itn"]]
     return out
+
+
+_omp = None
+
+
+def _omp_lib():
+    global _omp
+    if _omp is None:
+        _build.build()
+        L = ctypes.CDLL(_build.OMP_LIB)
+        L.cpu_omp_pc_lsqr.argtypes = [_I, _I, _I, _P, _P, _P, _P, _P, _I, _D, _D, _D, _P, _P, _P]
+        L.cpu_omp_pc_lsqr.restype = ctypes.c_int
+        L.cpu_omp_threads.restype = ctypes.c_int
+        _omp = L
+    return _omp
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP CPU baseline runs on."""
+    return int(_omp_lib().cpu_omp_threads())
+
+
+def omp_pc_lsqr(sys, b, itmax, atol=1e-12, btol=1e-12, conlim=1e8):
+    """The multi-threaded CPU baseline (not the oracle): PC-LSQR as pc_lsqr."""
+    keep, a = _sysargs(sys)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.empty(sys.n)
+    se = np.empty(sys.n)
+    st = np.zeros(8)
+    if _omp_lib().cpu_omp_pc_lsqr(*a, _ptr(b), int(itmax), float(atol), float(btol), float(conlim),
+                                 _ptr(x), _ptr(se), _ptr(st)) != 0:
+        raise MemoryError("cpu_omp_pc_lsqr: allocation failed")
+    out = dict(zip(STAT_NAMES, st))
+    out["istop"], out["itn"] = int(out["istop"]), int(out["itn"])
+    out.update(x=x, se=se)
+    return out

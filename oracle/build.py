@@ -1,6 +1,8 @@
-"""Compile the CPU oracle (plain C, FP64, no fast-math, no FMA contraction).
+"""Compile the CPU oracle (plain C, FP64, no fast-math, no FMA contraction)
+and the multi-threaded (OpenMP) CPU baseline beside it.
 
-Test infrastructure: builds oracle/_build/libgsr_oracle.so with gcc.
+Test infrastructure: builds oracle/_build/libgsr_oracle.so and
+oracle/_build/libgsr_cpu_omp.so with gcc.
 """
 import os
 import subprocess
@@ -12,16 +14,30 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgsr_oracle.so")
 
 
-def build(force: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
+OMP_SRC = os.path.join(HERE, "gsr_cpu_omp.c")
+OMP_LIB = os.path.join(OUT_DIR, "libgsr_cpu_omp.so")
+
+
+def _compile(src, lib, extra):
+    if os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(src):
+        return lib
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
-           "-ffp-contract=off", "-fno-strict-aliasing", "-o", tmp, SRC, "-lm"]
+           "-ffp-contract=off", "-fno-strict-aliasing"] + extra + ["-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False) -> str:
+    """Build the oracle (and the OpenMP CPU baseline beside it); returns the oracle."""
+    if force:
+        for lib in (LIB, OMP_LIB):
+            if os.path.exists(lib):
+                os.remove(lib)
+    _compile(OMP_SRC, OMP_LIB, ["-fopenmp"])
+    return _compile(SRC, LIB, [])
 
 
 if __name__ == "__main__":
