@@ -587,7 +587,10 @@ def main():
         line["batched_vs_sequential_fp64"] = batched
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sys_, seed, args.cpu_seconds)
-        line["cpu_baseline_openmp"] = cpu_baseline_openmp(sys_, seed, args.cpu_seconds)
+        try:
+            line["cpu_baseline_openmp"] = cpu_baseline_openmp(sys_, seed, args.cpu_seconds)
+        except OSError as e:  # library not built on this host
+            line["cpu_baseline_openmp"] = {"unavailable": str(e)[:200]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()
