@@ -62,6 +62,21 @@ extern "C" {
                                 y of a window stays in L2): no atomics, and aprod 2
                                 is deterministic */
 
+/* How the FP64 row kernels form their products; every choice is
+ * FP64-accurate. */
+#define GSR_PRODUCTS_AUTO 0   /* library choice: GSR_PRODUCTS_SPLIT where it applies */
+#define GSR_PRODUCTS_NATIVE 1 /* every product on the FP64 pipe */
+#define GSR_PRODUCTS_SPLIT 2  /* aprod 1 forms the 6 instrumental and the global
+                                 products of each row on the binary32 pipes from
+                                 exact three-piece binary32 splits of both
+                                 operands, with error-free products and sums:
+                                 within 2^-60 of the sum of their magnitudes,
+                                 below the rounding of one FP64 FMA.  Needs
+                                 I <= 3072 (GSR_ERR_UNSUPPORTED otherwise);
+                                 rows (or x) with an operand
+                                 whose exponent is outside [-30, 30] (zero x
+                                 entries excepted) take native FP64 products */
+
 /* Storage and arithmetic of the matrix values. */
 #define GSR_PREC_FP64 0  /* IEEE double values, native FP64 arithmetic */
 #define GSR_PREC_MIXED 1 /* as FP64, plus a binary32 copy of the values for the
@@ -91,6 +106,7 @@ typedef struct {
                            profilers that cannot see kernels inside graphs
                            with conditional nodes); same arithmetic */
     int instr_mode;     /* GSR_INSTR_*; default GSR_INSTR_AUTO */
+    int products;       /* GSR_PRODUCTS_*; default GSR_PRODUCTS_AUTO */
 } gsr_config;
 
 typedef struct {

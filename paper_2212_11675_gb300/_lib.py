@@ -24,6 +24,7 @@ GSR_ERR_UNSUPPORTED = -7
 GSR_PREC_FP64 = 0
 GSR_PREC_MIXED = 1
 GSR_INSTR_AUTO, GSR_INSTR_SMEM, GSR_INSTR_REPLICAS, GSR_INSTR_SORTED = 0, 1, 2, 3
+GSR_PRODUCTS_AUTO, GSR_PRODUCTS_NATIVE, GSR_PRODUCTS_SPLIT = 0, 1, 2
 
 EXPORTS = (
     "gsr_config_default", "gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",
@@ -43,7 +44,7 @@ class Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("conlim", ctypes.c_double),
                 ("lanes_per_star", ctypes.c_int), ("validate", ctypes.c_int),
                 ("force_itmax", ctypes.c_int), ("eager", ctypes.c_int),
-                ("instr_mode", ctypes.c_int)]
+                ("instr_mode", ctypes.c_int), ("products", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

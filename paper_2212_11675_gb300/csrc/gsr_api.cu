@@ -567,6 +567,10 @@ extern "C" int gsr_create(void **out, const gsr_dims *d, const uint32_t *star_pt
         return GSR_ERR_ARG;
     if (c.instr_mode == GSR_INSTR_SMEM && d->n_instr > 6144)
         return GSR_ERR_UNSUPPORTED;
+    if (c.products < GSR_PRODUCTS_AUTO || c.products > GSR_PRODUCTS_SPLIT)
+        return GSR_ERR_ARG;
+    if (c.products == GSR_PRODUCTS_SPLIT && d->n_instr > 3072)
+        return GSR_ERR_UNSUPPORTED;
     gsr_handle_t *h = new (std::nothrow) gsr_handle_t();
     if (!h)
         return GSR_ERR_OOM;

@@ -29,6 +29,7 @@
 
 #include "gsr_internal.cuh"
 #include "gsr_reduce.cuh"
+#include "gsr_split.cuh"
 
 namespace gsr {
 
@@ -46,15 +47,46 @@ __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
 // LSQR recurrences, beta_{i+1} = ||y|| / alpha_i with its rotation.
 // MODE 2 (conjugate gradients): y = A x, ||y||^2 into cg->xi and the step
 // cg->alpha = cg->gamma / ||y||^2.  SMEMX: the instrumental part of x is
-// staged in shared memory.
+// staged in shared memory.  SPLIT (with SMEMX): the seven instrumental and
+// global products of a row are formed on the binary32 pipes from exact
+// three-piece splits of both operands (gsr_split.cuh: FP64-accurate, error
+// below 2^-60 of the sum of their magnitudes), which takes 6 of the 27
+// FP64-pipe operations of a row off the pipe that bounds this kernel; x is
+// staged as pieces, and a row (or a block, for x) with an operand outside
+// the split range takes the FP64 products instead.
 // ---------------------------------------------------------------------------
-template <int MODE, bool SMEMX>
-__global__ void __launch_bounds__(kThreads, 5)  // 5 blocks per SM: 3% faster than 4
+template <int MODE, bool SMEMX, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 5)  // measured best: 3 split, 5 native
 k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveState *st,
          double *partial, unsigned *counter, CgState *cg)
 {
+    static_assert(!SPLIT || SMEMX, "the split products stage x in shared memory");
     extern __shared__ double s_xi[];
-    if (SMEMX) {
+    float4 *s_x4 = reinterpret_cast<float4 *>(s_xi);
+    const double xg = __ldg(x + A.glb0);
+    float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+    bool split_x = false;  // block-uniform: every split operand of x is in range
+    if (SPLIT) {
+        int bad = 0;
+        for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x) {
+            const double xv = x[A.ins0 + f];
+            const uint32_t hi = (uint32_t)__double2hiint(xv), lo = (uint32_t)__double2loint(xv);
+            float p1, p2, p3;
+            split3(hi, lo, p1, p2, p3);
+            if (((hi & 0x7fffffffu) | lo) == 0u)
+                p1 = p2 = p3 = 0.f;  // zero splits exactly
+            else if (split3_range(hi) >= kSplitRangeSpan)
+                bad = 1;
+            s_x4[f] = make_float4(p1, p2, p3, 0.f);
+        }
+        const uint32_t ghi = (uint32_t)__double2hiint(xg), glo = (uint32_t)__double2loint(xg);
+        split3(ghi, glo, g1, g2, g3);
+        if (((ghi & 0x7fffffffu) | glo) == 0u)
+            g1 = g2 = g3 = 0.f;
+        else if (split3_range(ghi) >= kSplitRangeSpan)
+            bad = 1;
+        split_x = __syncthreads_or(bad) == 0;
+    } else if (SMEMX) {
         for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x)
             s_xi[f] = x[A.ins0 + f];
         __syncthreads();
@@ -65,7 +97,6 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
     const int64_t ntiles = (A.m + 31) >> 5;
     const double cy = (MODE == 1) ? st->cy : 1.0;
     const int64_t mp = A.mp;
-    const double xg = __ldg(x + A.glb0);
     double nrm = 0.0;
 
     for (int64_t t = warp; t < ntiles; t += nwarps) {
@@ -81,27 +112,74 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
             // two independent partial sums (astrometric + global +
             // instrumental, attitude) keep the FP64 pipe fed with one merge
             // (four sums were 4% slower: two more FP64 adds per row)
-            const double *xs = x + (int64_t)kNAstro * s;
-            double s0 = vk[0] * __ldg(xs);
+            double s0, s1;
+            if constexpr (SPLIT) {
+                bool native = true;
+                if (split_x) {
+                    // instrumental and global products on the binary32
+                    // pipes; their sum h + (m + l) starts the FP64 chains
+                    Acc3 c = {0.f, 0.f, 0.f};
+                    uint32_t rng = 0;
 #pragma unroll
-            for (int k = 1; k < kNAstro; k++)
-                s0 = fma(vk[k], __ldg(xs + k), s0);
-            const double *xa = x + A.att0 + rc.x;
-            double s1 = vk[5] * __ldg(xa);
+                    for (int j = 0; j <= kNInstr; j++) {
+                        const double a = vk[17 + j];
+                        const uint32_t hi = (uint32_t)__double2hiint(a);
+                        const uint32_t lo = (uint32_t)__double2loint(a);
+                        rng = max(rng, split3_range(hi));
+                        float a1, a2, a3;
+                        split3(hi, lo, a1, a2, a3);
+                        if (j < kNInstr) {
+                            const float4 xp = s_x4[instr_at(rc, j)];
+                            acc3_fma(c, a1, a2, a3, xp.x, xp.y, xp.z);
+                        } else {
+                            acc3_fma(c, a1, a2, a3, g1, g2, g3);
+                        }
+                    }
+                    if (rng < kSplitRangeSpan) {
+                        acc3_parts(c, s0, s1);
+                        native = false;
+                    }
+                }
+                if (native) {  // an operand outside the split range
+                    s0 = vk[23] * xg;
 #pragma unroll
-            for (int j = 1; j < 4; j++)
-                s1 = fma(vk[5 + j], __ldg(xa + j), s1);
+                    for (int j = 0; j < kNInstr; j++)
+                        s0 = fma(vk[17 + j], __ldg(x + A.ins0 + instr_at(rc, j)), s0);
+                    s1 = 0.0;
+                }
+                const double *xs = x + (int64_t)kNAstro * s;
 #pragma unroll
-            for (int j = 0; j < 4; j++)
-                s1 = fma(vk[9 + j], __ldg(xa + A.D + j), s1);
-            s0 = fma(vk[23], xg, s0);
+                for (int k = 0; k < kNAstro; k++)
+                    s0 = fma(vk[k], __ldg(xs + k), s0);
+                const double *xa = x + A.att0 + rc.x;
 #pragma unroll
-            for (int j = 0; j < 4; j++)
-                s1 = fma(vk[13 + j], __ldg(xa + 2 * A.D + j), s1);
+                for (int a = 0; a < 3; a++)
 #pragma unroll
-            for (int j = 0; j < kNInstr; j++) {
-                const uint32_t f = instr_at(rc, j);
-                s0 = fma(vk[17 + j], SMEMX ? s_xi[f] : __ldg(x + A.ins0 + f), s0);
+                    for (int j = 0; j < 4; j++)
+                        s1 = fma(vk[5 + 4 * a + j], __ldg(xa + a * A.D + j), s1);
+            } else {
+                const double *xs = x + (int64_t)kNAstro * s;
+                s0 = vk[0] * __ldg(xs);
+#pragma unroll
+                for (int k = 1; k < kNAstro; k++)
+                    s0 = fma(vk[k], __ldg(xs + k), s0);
+                const double *xa = x + A.att0 + rc.x;
+                s1 = vk[5] * __ldg(xa);
+#pragma unroll
+                for (int j = 1; j < 4; j++)
+                    s1 = fma(vk[5 + j], __ldg(xa + j), s1);
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    s1 = fma(vk[9 + j], __ldg(xa + A.D + j), s1);
+                s0 = fma(vk[23], xg, s0);
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    s1 = fma(vk[13 + j], __ldg(xa + 2 * A.D + j), s1);
+#pragma unroll
+                for (int j = 0; j < kNInstr; j++) {
+                    const uint32_t f = instr_at(rc, j);
+                    s0 = fma(vk[17 + j], SMEMX ? s_xi[f] : __ldg(x + A.ins0 + f), s0);
+                }
             }
             const double sum = s0 + s1;
             double yn;
@@ -600,19 +678,30 @@ k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out,
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// instrumental x as split pieces (16 bytes each) in shared memory up to this
+// many instruments (48 KB per block; three blocks per SM still fit)
+constexpr int64_t kSplitInstrMax = 3072;
+
+bool aprod1_split(const gsr_handle_t *h)
+{
+    return h->cfg.products != GSR_PRODUCTS_NATIVE && h->sys.I <= kSplitInstrMax;
+}
+
 template <int MODE>
 static cudaError_t a1_launch(const gsr_handle_t *h, const double *x, double *y,
                              SolveState *st_slot, double *partial, unsigned *counter,
                              cudaStream_t st, CgState *cg = nullptr)
 {
     const bool smem = h->sys.I <= kSmemInstrMax;
-    const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
-    if (smem)
-        k_aprod1<MODE, true><<<h->grid_rows, kThreads, shm, st>>>(h->sys, x, y, st_slot, partial,
-                                                                   counter, cg);
+    if (aprod1_split(h))
+        k_aprod1<MODE, true, true><<<h->grid_rows, kThreads, (size_t)h->sys.I * sizeof(float4),
+                                     st>>>(h->sys, x, y, st_slot, partial, counter, cg);
+    else if (smem)
+        k_aprod1<MODE, true, false><<<h->grid_rows, kThreads, (size_t)h->sys.I * sizeof(double),
+                                      st>>>(h->sys, x, y, st_slot, partial, counter, cg);
     else
-        k_aprod1<MODE, false><<<h->grid_rows, kThreads, 0, st>>>(h->sys, x, y, st_slot, partial,
-                                                                  counter, cg);
+        k_aprod1<MODE, false, false><<<h->grid_rows, kThreads, 0, st>>>(h->sys, x, y, st_slot,
+                                                                        partial, counter, cg);
     return cudaGetLastError();
 }
 
@@ -1053,12 +1142,17 @@ static int cap_grid(const gsr_handle_t *h, int occ)
 int aprod1_grid(const gsr_handle_t *h)
 {
     const bool smem = h->sys.I <= kSmemInstrMax;
-    const size_t shm = smem ? (size_t)h->sys.I * sizeof(double) : 0;
     int occ = 0;
-    cudaError_t e = smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1<1, true>,
-                                                                         kThreads, shm)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1<1, false>,
-                                                                         kThreads, 0);
+    cudaError_t e;
+    if (aprod1_split(h))
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1<1, true, true>, kThreads,
+                                                          (size_t)h->sys.I * sizeof(float4));
+    else if (smem)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1<1, true, false>, kThreads,
+                                                          (size_t)h->sys.I * sizeof(double));
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1<1, false, false>,
+                                                          kThreads, 0);
     return e == cudaSuccess ? cap_grid(h, occ) : -1;
 }
 

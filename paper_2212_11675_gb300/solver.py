@@ -62,7 +62,8 @@ class Solver:
 
     def __init__(self, system, conlim: float = 1e8, lanes_per_star: int = 0,
                  validate: bool = True, precision: int = _lib.GSR_PREC_FP64,
-                 force_itmax: bool = False, eager: bool = False, instr_mode: int = 0):
+                 force_itmax: bool = False, eager: bool = False, instr_mode: int = 0,
+                 products: int = 0):
         L = lib()
         self._h = ctypes.c_void_p()
         d = Dims(system.n_stars, system.n_dfa, system.n_instr, int(system.m))
@@ -75,6 +76,7 @@ class Solver:
         cfg.force_itmax = 1 if force_itmax else 0
         cfg.eager = 1 if eager else 0
         cfg.instr_mode = instr_mode
+        cfg.products = products
         arrs = []
         for a, dt in ((system.star_ptr, np.uint32), (system.attoff, np.uint32),
                       (system.instr, np.uint16), (system.values, np.float64)):

@@ -40,3 +40,30 @@ def test_strerror_and_null_handling_without_gpu():
     assert L.gsr_aprod1(None, None, None, None) == _lib.GSR_ERR_ARG
     assert L.gsr_lsqr_solve(None, None, 1, 0.0, 0.0, None, None, None, None) == _lib.GSR_ERR_ARG
     assert L.gsr_destroy(None) == _lib.GSR_OK
+
+
+def test_create_checks_the_product_form_before_any_cuda_call():
+    import ctypes
+
+    import numpy as np
+    L = _lib.lib()
+    sp = np.array([0, 1], dtype=np.uint32)
+    att = np.zeros(1, dtype=np.uint32)
+    ins = np.arange(6, dtype=np.uint16)
+    val = np.ones(24)
+    h = ctypes.c_void_p()
+
+    def create(n_instr, products):
+        d = _lib.Dims(1, 8, n_instr, 1)
+        cfg = _lib.Config()
+        L.gsr_config_default(ctypes.byref(cfg))
+        assert cfg.products == _lib.GSR_PRODUCTS_AUTO
+        cfg.products = products
+        return L.gsr_create(ctypes.byref(h), ctypes.byref(d), sp.ctypes.data, att.ctypes.data,
+                            ins.ctypes.data, val.ctypes.data, ctypes.byref(cfg))
+
+    assert create(60, 7) == _lib.GSR_ERR_ARG
+    assert create(60, -1) == _lib.GSR_ERR_ARG
+    # split products keep x in shared memory: at most 3072 instruments
+    assert create(4000, _lib.GSR_PRODUCTS_SPLIT) == _lib.GSR_ERR_UNSUPPORTED
+    assert not h.value
