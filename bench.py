@@ -540,17 +540,21 @@ def main():
     # x gathered / written once per unknown
     bytes_a1 = m * (24 * 8 + 16 + 16) + 4 * sys_.n_stars + 8 * n
     bytes_a2 = m * (24 * 8 + 16 + 8) + 4 * sys_.n_stars + 16 * n
-    flops = 2 * 24 * m  # one FMA per nonzero
+    # FLOPs on the FP64 pipe: one FMA per nonzero, less the products formed on
+    # the binary32 pipes from exact splits (7 per row in aprod 1, 6 in aprod 2)
+    split1, split2 = solver.product_forms()
+    flops_a1 = 2 * (24 - (7 if split1 else 0)) * m
+    flops_a2 = 2 * (24 - (6 if split2 else 0)) * m
     gbs_a1, gbs_a2 = bytes_a1 / t_a1 / 1e9, bytes_a2 / t_a2 / 1e9
-    tf_a1, tf_a2 = flops / t_a1 / 1e12, flops / t_a2 / 1e12
+    tf_a1, tf_a2 = flops_a1 / t_a1 / 1e12, flops_a2 / t_a2 / 1e12
     dom = "aprod2" if t_a2 >= t_a1 else "aprod1"
     t_dom, gbs_dom, tf_dom, byt = ((t_a2, gbs_a2, tf_a2, bytes_a2) if dom == "aprod2"
                                    else (t_a1, gbs_a1, tf_a1, bytes_a1))
     # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-    # --set full capture of the in-solve launches on the medium workload (null
-    # for another workload, and to be nulled once that kernel changes)
-    traffic = {"aprod2": 1.9440e9 + 0.0103e9, "aprod1": 1.5330e9 + 0.0078e9}.get(dom) \
-        if args.workload == "medium" else None
+    # capture of the in-solve launches of the current kernels on the medium
+    # workload (dram__bytes.sum.per_second x duration; null for another
+    # workload, and to be nulled once that kernel changes)
+    traffic = {"aprod2": 1.9412e9, "aprod1": 1.5422e9}.get(dom) if args.workload == "medium" else None
     f_hbm = gbs_dom / hbm
     f_alu = tf_dom / FP64_NOMINAL_TFLOPS
     if f_alu >= f_hbm:
@@ -562,9 +566,11 @@ def main():
     roof.update({"kernel": dom, "peak_source": "FP64 nominal (recipe)" if roof["bound"] == "alu"
                  else "%s HBM copy" % src,
                  "kernels": {"aprod1": {"ms": t_a1 * 1e3, "GB/s": gbs_a1, "hbm_frac": gbs_a1 / hbm,
-                                        "fp64_TFLOP/s": tf_a1, "fp64_frac": tf_a1 / FP64_NOMINAL_TFLOPS},
+                                        "fp64_TFLOP/s": tf_a1, "fp64_frac": tf_a1 / FP64_NOMINAL_TFLOPS,
+                                        "split_products": split1},
                              "aprod2": {"ms": t_a2 * 1e3, "GB/s": gbs_a2, "hbm_frac": gbs_a2 / hbm,
-                                        "fp64_TFLOP/s": tf_a2, "fp64_frac": tf_a2 / FP64_NOMINAL_TFLOPS}},
+                                        "fp64_TFLOP/s": tf_a2, "fp64_frac": tf_a2 / FP64_NOMINAL_TFLOPS,
+                                        "split_products": split2}},
                  "aprod_GB/s": (bytes_a1 + bytes_a2) / (t_a1 + t_a2) / 1e9})
 
     mixed = None

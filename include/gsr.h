@@ -64,18 +64,23 @@ extern "C" {
 
 /* How the FP64 row kernels form their products; every choice is
  * FP64-accurate. */
-#define GSR_PRODUCTS_AUTO 0   /* library choice: GSR_PRODUCTS_SPLIT where it applies */
+#define GSR_PRODUCTS_AUTO 0   /* library choice: aprod 1's split form where it
+                                 applies (I <= 3072), native products otherwise */
 #define GSR_PRODUCTS_NATIVE 1 /* every product on the FP64 pipe */
-#define GSR_PRODUCTS_SPLIT 2  /* aprod 1 forms the 6 instrumental and the global
-                                 products of each row on the binary32 pipes from
-                                 exact three-piece binary32 splits of both
-                                 operands, with error-free products and sums:
-                                 within 2^-60 of the sum of their magnitudes,
-                                 below the rounding of one FP64 FMA.  Needs
-                                 I <= 3072 (GSR_ERR_UNSUPPORTED otherwise);
-                                 rows (or x) with an operand
-                                 whose exponent is outside [-30, 30] (zero x
-                                 entries excepted) take native FP64 products */
+#define GSR_PRODUCTS_SPLIT 2  /* products formed on the binary32 pipes from exact
+                                 three-piece binary32 splits of both operands,
+                                 with error-free products and sums, within 2^-60
+                                 of the sum of their magnitudes (below the
+                                 rounding of one FP64 FMA): aprod 1's 6
+                                 instrumental and global products of each row
+                                 (needs I <= 3072, GSR_ERR_UNSUPPORTED
+                                 otherwise) and the astrometric and global
+                                 products of aprod 2's single-launch pass.
+                                 Operands whose exponent is outside [-30, 30]
+                                 (zero x or y entries excepted) send their row
+                                 (aprod 1), block (aprod 1's x) or star group
+                                 (aprod 2) to native FP64 products.
+                                 gsr_product_forms() tells which apply */
 
 /* Storage and arithmetic of the matrix values. */
 #define GSR_PREC_FP64 0  /* IEEE double values, native FP64 arithmetic */
@@ -244,6 +249,16 @@ int gsr_aprod2_f32(void *h, const double *y, double *x, void *stream);
 int gsr_mixed_solve(void *h, const double *b, int max_outer, int max_inner,
                     double inner_tol, double atol, double *x,
                     gsr_mixed_result *out, void *stream);
+
+/*
+ * Which FP64 products of the handle run on the binary32 pipes from exact
+ * splits (GSR_PRODUCTS_SPLIT form): *aprod1_split_on = 1 when aprod 1 forms
+ * its instrumental and global products that way, *aprod2_split_on = 1 when
+ * aprod 2's single-launch pass forms its astrometric and global products
+ * that way; 0 for native FP64 products.  Host only, no CUDA call.  Errors:
+ * GSR_ERR_ARG.
+ */
+int gsr_product_forms(void *h, int *aprod1_split_on, int *aprod2_split_on);
 
 /*
  * Replace nonzero k (0..23, in the order of the column map above) of every

@@ -832,6 +832,16 @@ extern "C" int gsr_mixed_solve(void *hv, const double *b, int max_outer, int max
     return GSR_OK;
 }
 
+extern "C" int gsr_product_forms(void *hv, int *aprod1_split_on, int *aprod2_split_on)
+{
+    const gsr_handle_t *h = (const gsr_handle_t *)hv;
+    if (!h || !aprod1_split_on || !aprod2_split_on)
+        return GSR_ERR_ARG;
+    *aprod1_split_on = aprod1_split(h) ? 1 : 0;
+    *aprod2_split_on = aprod2_split_active(h) ? 1 : 0;
+    return GSR_OK;
+}
+
 extern "C" int gsr_set_values(void *hv, int k, const double *values, void *stream)
 {
     gsr_handle_t *h = (gsr_handle_t *)hv;

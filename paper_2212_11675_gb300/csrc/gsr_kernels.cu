@@ -352,6 +352,147 @@ __device__ __forceinline__ double stars_body(const SysView &A, const double *__r
     return gacc;
 }
 
+// c += the Acc3 value (h, m, l) of another lane: both exact levels by TwoSum,
+// the third rounded
+__device__ __forceinline__ void acc3_add(Acc3 &c, float h, float m, float l)
+{
+    float t, u1, u2;
+    c.h = two_sum(c.h, h, t);
+    c.m = two_sum(c.m, m, u1);
+    c.m = two_sum(c.m, t, u2);
+    c.l = __fadd_rn(__fadd_rn(c.l, l), __fadd_rn(u1, u2));
+}
+
+__device__ __forceinline__ void acc3_add_shfl(Acc3 &c, const Acc3 &send, int off)
+{
+    acc3_add(c, __shfl_xor_sync(0xffffffffu, send.h, off), __shfl_xor_sync(0xffffffffu, send.m, off),
+             __shfl_xor_sync(0xffffffffu, send.l, off));
+}
+
+__device__ __forceinline__ double acc3_to_double(const Acc3 &c)
+{
+    double d0, d1;
+    acc3_parts(c, d0, d1);
+    return d0 + d1;
+}
+
+// Star-group part of the single-launch aprod 2 with the astrometric and
+// global products on the binary32 pipes (exact splits of the values and of
+// y, gsr_split.cuh): the five astrometric sums of a star and this lane's
+// global sum are three-level binary32 accumulators, reduced over the G lanes
+// with exact level sums.  A warp that meets an operand outside the split
+// range (a zero y excepted) redoes its stars with native FP64 products.
+// Returns this thread's share of the global column.
+template <int G, int MODE>
+__device__ __forceinline__ double stars_body_split(const SysView &A, const double *__restrict__ y,
+                                                   double *__restrict__ out, int64_t warp,
+                                                   int64_t nwarps)
+{
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & (G - 1);
+    const int gw = (threadIdx.x & 31) / G;
+    const int64_t mp = A.mp;
+    double gacc = 0.0;
+    for (int64_t s0 = warp * GPW; s0 < A.S; s0 += nwarps * GPW) {
+        const int64_t s = (s0 + gw < A.S) ? (int64_t)A.sorder[s0 + gw] : A.S;
+        uint32_t r0 = 0, r1 = 0;
+        if (s < A.S) {
+            r0 = A.star_ptr[s];
+            r1 = A.star_ptr[s + 1];
+        }
+        Acc3 c[kNAstro + 1];
+#pragma unroll
+        for (int k = 0; k <= kNAstro; k++)
+            c[k] = Acc3{0.f, 0.f, 0.f};
+        uint32_t rng = 0;
+        for (uint32_t r = r0 + lane; r < r1; r += G) {
+            const double *v = A.val + r;
+            double va[kNAstro + 1];
+#pragma unroll
+            for (int k = 0; k <= kNAstro; k++)
+                va[k] = __ldcs(v + (k < kNAstro ? k : 23) * mp);
+            const double yi = __ldcs(y + r);
+            const uint32_t yhi = (uint32_t)__double2hiint(yi), ylo = (uint32_t)__double2loint(yi);
+            float y1, y2, y3;
+            split3(yhi, ylo, y1, y2, y3);
+            if (((yhi & 0x7fffffffu) | ylo) == 0u)
+                y1 = y2 = y3 = 0.f;  // zero splits exactly
+            else
+                rng = max(rng, split3_range(yhi));
+#pragma unroll
+            for (int k = 0; k <= kNAstro; k++) {
+                const uint32_t hi = (uint32_t)__double2hiint(va[k]);
+                const uint32_t lo = (uint32_t)__double2loint(va[k]);
+                rng = max(rng, split3_range(hi));
+                float a1, a2, a3;
+                split3(hi, lo, a1, a2, a3);
+                acc3_fma(c[k], a1, a2, a3, y1, y2, y3);
+            }
+        }
+        if (__any_sync(0xffffffffu, rng >= kSplitRangeSpan)) {
+            // rare: native FP64 products for this warp's stars
+            gacc += stars_body<G, MODE, kIpSorted>(A, y, out, nullptr, 1, nullptr, s0 / GPW,
+                                                   A.S);
+            continue;
+        }
+        gacc += acc3_to_double(c[kNAstro]);
+        if constexpr (G >= 8) {
+            // reduce-scatter as in stars_body, on three-level accumulators
+            Acc3 r8[8] = {c[0], c[1], c[2], c[3], c[4], Acc3{0.f, 0.f, 0.f}, Acc3{0.f, 0.f, 0.f},
+                          Acc3{0.f, 0.f, 0.f}};
+#pragma unroll
+            for (int hw = 4, off = G / 2; hw >= 1; hw >>= 1, off >>= 1) {
+                const bool upper = (lane & off) != 0;
+#pragma unroll
+                for (int k = 0; k < hw; k++) {
+                    const Acc3 send = upper ? r8[k] : r8[k + hw];
+                    Acc3 keep = upper ? r8[k + hw] : r8[k];
+                    acc3_add_shfl(keep, send, off);
+                    r8[k] = keep;
+                }
+            }
+#pragma unroll
+            for (int off = G / 16; off > 0; off >>= 1) {
+                const Acc3 send = r8[0];
+                acc3_add_shfl(r8[0], send, off);
+            }
+            const int kidx = ((lane & (G / 2)) ? 4 : 0) | ((lane & (G / 4)) ? 2 : 0) |
+                             ((lane & (G / 8)) ? 1 : 0);
+            if (s < A.S && (lane & (G / 8 - 1)) == 0 && kidx < kNAstro) {
+                const double tot = acc3_to_double(r8[0]);
+                double *xs = out + kNAstro * s + kidx;
+                if (MODE == kA2Accumulate)
+                    *xs += tot;
+                else
+                    *xs = tot;
+            }
+        } else {
+            // fewer lanes than sums: butterfly, then lane l writes the sums
+            // k with k % G == l
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+                for (int k = 0; k < kNAstro; k++) {
+                    const Acc3 send = c[k];
+                    acc3_add_shfl(c[k], send, off);
+                }
+            if (s < A.S) {
+#pragma unroll
+                for (int k = 0; k < kNAstro; k++)
+                    if (k % G == lane) {
+                        const double tot = acc3_to_double(c[k]);
+                        double *xs = out + kNAstro * s + k;
+                        if (MODE == kA2Accumulate)
+                            *xs += tot;
+                        else
+                            *xs = tot;
+                    }
+            }
+        }
+    }
+    return gacc;
+}
+
 // global column: one partial per block, added in block order by the combine
 // kernel
 __device__ __forceinline__ void global_partial(double gacc, double *__restrict__ gpart)
@@ -555,13 +696,14 @@ k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
 // resets the counter.  Which warp computes a unit does not change its sums:
 // the global column gets one partial per star unit, gpart[unit].
 // ---------------------------------------------------------------------------
-template <int G, int MODE>
-__global__ void __launch_bounds__(kThreads)
+template <int G, int MODE, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 4)  // 64 registers: no spills in either form
 k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out,
                double *__restrict__ S, const uint32_t *__restrict__ cseg,
                const uint32_t *__restrict__ irow, const double *__restrict__ ival,
                double *__restrict__ part, int nwin, double *__restrict__ gpart, A2Queue q)
 {
+    static_assert(!SPLIT || MODE != kA2Squares, "the preconditioner keeps native products");
     constexpr bool SQ = MODE == kA2Squares;
     const int lane = threadIdx.x & 31;
     const int L = q.ns + q.na + q.ni;
@@ -583,9 +725,13 @@ k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out
                 double g = 0.0;
                 for (int k = 0; k < q.star_k; k++) {
                     const int64_t grp = i * q.star_k + k;
-                    if (grp < q.nstar_groups)
-                        g += stars_body<G, MODE, kIpSorted>(A, y, out, nullptr, 1, nullptr, grp,
-                                                            q.nstar_groups);
+                    if (grp < q.nstar_groups) {
+                        if constexpr (SPLIT)
+                            g += stars_body_split<G, MODE>(A, y, out, grp, q.nstar_groups);
+                        else
+                            g += stars_body<G, MODE, kIpSorted>(A, y, out, nullptr, 1, nullptr,
+                                                                grp, q.nstar_groups);
+                    }
                 }
                 g = warp_sum(g);
                 if (lane == 0)
@@ -847,12 +993,35 @@ A2Queue a2_queue(const gsr_handle_t *h, int G, int64_t ninstr_units)
     return q;
 }
 
+// the products of aprod 2 (not the preconditioner's squares) take the split
+// star pass only when asked for: measured on the medium workload it was
+// slower (0.411 against 0.388 ms per launch), the star units being a quarter
+// of the pass's FP64 work and its attitude and instrument units sharing the SMs
+bool aprod2_split(const gsr_handle_t *h)
+{
+    return h->cfg.products == GSR_PRODUCTS_SPLIT;
+}
+
+bool aprod2_split_active(const gsr_handle_t *h)
+{
+    return h->ipath == kIpSorted && h->a2_fused && aprod2_split(h);
+}
+
 template <int G, int MODE>
 static void fused_launch(const gsr_handle_t *h, const double *y, double *out, cudaStream_t st)
 {
-    k_aprod2_fused<G, MODE><<<h->grid_fused, kThreads, 0, st>>>(
+    const A2Queue q = a2_queue(h, G);
+    if constexpr (MODE != kA2Squares) {
+        if (aprod2_split(h)) {
+            k_aprod2_fused<G, MODE, true><<<h->grid_fused, kThreads, 0, st>>>(
+                h->sys, y, out, h->d_attS, h->d_cseg, h->d_irow, h->d_ival, h->d_ipart,
+                h->isplit, h->d_gpart, q);
+            return;
+        }
+    }
+    k_aprod2_fused<G, MODE, false><<<h->grid_fused, kThreads, 0, st>>>(
         h->sys, y, out, h->d_attS, h->d_cseg, h->d_irow, h->d_ival, h->d_ipart, h->isplit,
-        h->d_gpart, a2_queue(h, G));
+        h->d_gpart, q);
 }
 
 template <int MODE>
@@ -1179,15 +1348,25 @@ static int a2_occupancy(const gsr_handle_t *h)
 }
 
 // blocks of the fused aprod 2: all resident blocks, a multiple of 8
+template <int G>
+static cudaError_t fused_occupancy(const gsr_handle_t *h, int *occ)
+{
+    return aprod2_split(h)
+               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     occ, k_aprod2_fused<G, kA2Overwrite, true>, kThreads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     occ, k_aprod2_fused<G, kA2Overwrite, false>, kThreads, 0);
+}
+
 int aprod2_fused_grid(const gsr_handle_t *h)
 {
     int occ = 0;
     cudaError_t e;
     switch (h->lanes) {
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod2_fused<4, kA2Overwrite>, kThreads, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod2_fused<8, kA2Overwrite>, kThreads, 0); break;
-    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod2_fused<32, kA2Overwrite>, kThreads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod2_fused<16, kA2Overwrite>, kThreads, 0); break;
+    case 4: e = fused_occupancy<4>(h, &occ); break;
+    case 8: e = fused_occupancy<8>(h, &occ); break;
+    case 32: e = fused_occupancy<32>(h, &occ); break;
+    default: e = fused_occupancy<16>(h, &occ); break;
     }
     if (e != cudaSuccess || occ <= 0)
         return -1;

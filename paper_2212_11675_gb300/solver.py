@@ -194,6 +194,14 @@ class Solver:
         queue (True, the default) or as separate passes (False)."""
         check(lib().gsr_set_aprod2_fused(self._h, 1 if fused else 0), "gsr_set_aprod2_fused")
 
+    def product_forms(self):
+        """(aprod1_split, aprod2_split): which FP64 products run on the binary32
+        pipes from exact splits (GSR_PRODUCTS_SPLIT form)."""
+        a1, a2 = ctypes.c_int(), ctypes.c_int()
+        check(lib().gsr_product_forms(self._h, ctypes.byref(a1), ctypes.byref(a2)),
+              "gsr_product_forms")
+        return bool(a1.value), bool(a2.value)
+
     def set_batch_tiling(self, kt, lanes):
         """Column tile (1, 2, 4, 8) and lanes per star (8, 16, 32) of the batched kernels."""
         check(lib().gsr_set_batch_tiling(self._h, int(kt), int(lanes)), "gsr_set_batch_tiling")

@@ -30,7 +30,7 @@ def _solver(sys, **kw):
     return Solver(sys, **kw)
 
 
-def check_aprods(sys, lanes=0, seed=0):
+def check_aprods(sys, lanes=0, seed=0, **kw):
     rng = np.random.default_rng(seed)
     x = rng.standard_normal(sys.n)
     y = rng.standard_normal(sys.m)
@@ -41,7 +41,7 @@ def check_aprods(sys, lanes=0, seed=0):
     asys = _abs_sys(sys)
     bound1 = 1e-12 * (oracle.aprod1(asys, np.abs(x)) + np.abs(y0)) + 1e-300
     bound2 = 1e-12 * (oracle.aprod2(asys, np.abs(y)) + np.abs(x0)) + 1e-300
-    with _solver(sys, lanes_per_star=lanes) as s:
+    with _solver(sys, lanes_per_star=lanes, **kw) as s:
         yd = torch.tensor(y0, device=DEV)
         s.aprod1(torch.tensor(x, device=DEV), yd)
         xd = torch.tensor(x0, device=DEV)

@@ -1,10 +1,10 @@
-"""aprod 1 with the instrumental and global products on the binary32 pipes
-(GSR_PRODUCTS_SPLIT, the default where I <= 3072) against exact rational
-arithmetic: the split products are accumulated to within about 2^-60 of the
-sum of their magnitudes, so a row made only of them stays accurate under
-heavy cancellation, where a chain of FP64 FMAs loses up to 2^-53 of that sum
-per product.  Operands outside the split range take the native FP64
-products; the result then meets the FP64 bound."""
+"""The split product forms (GSR_PRODUCTS_SPLIT; aprod 1's is the default
+where I <= 3072) against exact rational arithmetic: the split products are
+accumulated to within about 2^-60 of the sum of their magnitudes, so a row
+(or a star's column sum) made only of them stays accurate under heavy
+cancellation, where a chain of FP64 FMAs loses up to 2^-53 of that sum per
+product.  Operands outside the split range take the native FP64 products;
+the result then meets the FP64 bound."""
 from fractions import Fraction
 
 import numpy as np
@@ -137,3 +137,100 @@ def test_split_matches_native_on_a_generated_system():
     mag = np.abs(y0) + np.sum(a.values * np.abs(x)[cols], axis=1)
     assert np.all(np.abs(gs - gn) <= 54 * U * mag)
     assert not np.array_equal(gs, gn)  # the two forms really differ in rounding
+
+
+def _exact_t(sys, y, x0):
+    """x0 + A^T y column by column in rational arithmetic, and sum |terms|."""
+    cols = columns(sys)
+    ex = [Fraction(float(v)) for v in x0]
+    mag = np.abs(x0).astype(float)
+    for i in range(sys.m):
+        yi = Fraction(float(y[i]))
+        for k in range(24):
+            p = Fraction(float(sys.values[i, k])) * yi
+            ex[cols[i, k]] += p
+            mag[cols[i, k]] += abs(float(p))
+    return ex, mag
+
+
+def _aprod2(sys, y, x0, products):
+    from paper_2212_11675_gb300.solver import Solver
+    with Solver(sys, products=products, instr_mode=_lib.GSR_INSTR_SORTED) as s:
+        xd = torch.tensor(x0, device=DEV)
+        s.aprod2(torch.tensor(y, device=DEV), xd)
+        return xd.cpu().numpy()
+
+
+def test_split_star_sums_exact_under_cancellation():
+    # aprod 2's astrometric sums: in every star the first astrometric value
+    # of the last row cancels the star's other products of that column
+    sys = small(40, 12, 9, obs=9, seed=11)
+    rng = np.random.default_rng(11)
+    vals = sys.values.copy()
+    y = rng.uniform(1.0, 2.0, size=sys.m) * 2.0 ** 20 * np.where(np.arange(sys.m) % 2 == 0, 1, -1)
+    vals[:, 0] = rng.uniform(1.0, 2.0, size=sys.m) * 2.0 ** 20
+    sp = sys.star_ptr.astype(np.int64)
+    for s in range(sys.n_stars):
+        r0, r1 = sp[s], sp[s + 1]
+        part = sum(Fraction(float(vals[r, 0])) * Fraction(float(y[r])) for r in range(r0, r1 - 1))
+        vals[r1 - 1, 0] = -float(part / Fraction(float(y[r1 - 1])))
+    sys = gen.GaiaSystem(sys.n_stars, sys.n_dfa, sys.n_instr, sys.star_ptr, sys.attoff,
+                         sys.instr, vals)
+    x0 = np.zeros(sys.n)
+    ex, mag = _exact_t(sys, y, x0)
+    exf = np.array([float(e) for e in ex])
+    c0 = 5 * np.arange(sys.n_stars)
+    assert np.median(mag[c0] / np.maximum(np.abs(exf[c0]), 1e-300)) > 1e6
+    g = _aprod2(sys, y, x0, _lib.GSR_PRODUCTS_SPLIT)
+    err = _err(g, ex)
+    astro = np.arange(5 * sys.n_stars)
+    assert np.all(err[astro] <= 3 * U * np.abs(exf[astro]) + 2.0 ** -60 * mag[astro])
+    assert np.all(err <= 30 * U * mag)
+    gn = _aprod2(sys, y, x0, _lib.GSR_PRODUCTS_NATIVE)
+    errn = _err(gn, ex)
+    assert np.all(errn <= 30 * U * mag)
+    assert np.max(errn[c0] / np.maximum(np.abs(exf[c0]), 1e-300)) > 1e-12
+
+
+def test_split_star_sums_out_of_range_fall_back():
+    sys = small(60, 20, 13, obs=12, seed=12)
+    rng = np.random.default_rng(13)
+    vals = sys.values.copy()
+    vals[5, 2] = 1e-13   # astrometric value below the split range
+    vals[40, 23] = 5e11  # global value above it
+    sys = gen.GaiaSystem(sys.n_stars, sys.n_dfa, sys.n_instr, sys.star_ptr, sys.attoff,
+                         sys.instr, vals)
+    x0 = rng.standard_normal(sys.n)
+    for case in range(3):
+        y = rng.standard_normal(sys.m)
+        if case == 1:
+            y[100] = 1e-16  # y below the range
+        if case == 2:
+            y[::7] = 0.0    # zero y splits exactly
+        ex, mag = _exact_t(sys, y, x0)
+        g = _aprod2(sys, y, x0, _lib.GSR_PRODUCTS_SPLIT)
+        assert np.all(_err(g, ex) <= 30 * U * mag), case
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+def test_split_star_pass_every_lane_count(lanes):
+    # the split star pass of aprod 2 (explicit GSR_PRODUCTS_SPLIT) with 4 lanes
+    # per star (fewer lanes than sums) up to a whole warp per star
+    from tests.test_gpu_parity import check_aprods
+    check_aprods(gen.make("tiny"), lanes, products=_lib.GSR_PRODUCTS_SPLIT)
+
+
+def test_product_forms_report_what_runs():
+    from paper_2212_11675_gb300.solver import Solver
+    tiny = gen.make("tiny")
+    with Solver(tiny) as s:  # default: split aprod 1, native aprod 2
+        assert s.product_forms() == (True, False)
+    with Solver(tiny, products=_lib.GSR_PRODUCTS_NATIVE) as s:
+        assert s.product_forms() == (False, False)
+    with Solver(tiny, products=_lib.GSR_PRODUCTS_SPLIT) as s:
+        assert s.product_forms() == (True, True)
+    with Solver(tiny, products=_lib.GSR_PRODUCTS_SPLIT, instr_mode=_lib.GSR_INSTR_SMEM) as s:
+        assert s.product_forms() == (True, False)  # no single-launch aprod 2 on this path
+    # more instruments than the split x fits in shared memory: native aprod 1
+    with Solver(small(300, 50, 7000, seed=9)) as s:
+        assert s.product_forms()[0] is False
