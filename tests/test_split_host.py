@@ -1,0 +1,113 @@
+"""The split-product arithmetic of the FP64 row kernels (csrc/gsr_split.cuh),
+compiled for the host with g++ and checked against exact rational arithmetic:
+split3 is exact and its range test right at the window ends, and sums of
+products accumulated with acc3_fma stay within 2^-60 of the sum of their
+magnitudes, including sums that cancel to about 2^-50 of it.  The same header
+is what the GPU kernels compile (no GPU needed here)."""
+import math
+import os
+import random
+import shutil
+import subprocess
+from fractions import Fraction
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2212_11675_gb300", "csrc")
+EMIN, EMAX = -30, 30
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not found")
+    d = tmp_path_factory.mktemp("split_host")
+    (d / "cuda_runtime.h").write_text("")  # the header's only CUDA include
+    exe = d / "split_host"
+    subprocess.run([gxx, "-O2", "-ffp-contract=off", "-std=c++17", "-I", str(d), "-I", CSRC,
+                    "-o", str(exe), os.path.join(ROOT, "tests", "split_host.cpp")],
+                   check=True, capture_output=True)
+
+    def run(lines):
+        out = subprocess.run([str(exe)], input="".join(lines), capture_output=True, text=True,
+                             check=True).stdout
+        return out.splitlines()
+    return run
+
+
+def _exp(v):
+    return math.frexp(v)[1] - 1
+
+
+def _split_lines(vals):
+    return ["S %s\n" % float(v).hex() for v in vals]
+
+
+def test_split_is_exact_and_the_range_test_is_right(harness):
+    rng = random.Random(1)
+    vals = []
+    for e in (EMIN - 1, EMIN, EMIN + 1, -1, 0, 1, EMAX - 1, EMAX, EMAX + 1):
+        for mant in (1.0, 2.0 - 2.0 ** -52, 1.5, 1 + 2.0 ** -52, 1 + 2.0 ** -23,
+                     1 + 2.0 ** -29, 1 + 2.0 ** -46, rng.uniform(1, 2)):
+            for sgn in (1.0, -1.0):
+                vals.append(sgn * mant * 2.0 ** e)
+    vals += [rng.gauss(0, 1) for _ in range(2000)]
+    out = harness(_split_lines(vals))
+    assert len(out) == len(vals)
+    for v, line in zip(vals, out):
+        h, m, l, ok = line.split()
+        in_range = EMIN <= _exp(v) <= EMAX
+        assert int(ok) == int(in_range), v
+        if in_range:
+            pieces = [float.fromhex(t) for t in (h, m, l)]
+            assert sum(Fraction(p) for p in pieces) == Fraction(v), v
+            # leading 24 bits, then pieces far below: |m| < 2^-23 |h|, |l| < 2^-46 |h|
+            assert abs(pieces[1]) < 2.0 ** -22 * abs(pieces[0])
+            assert abs(pieces[2]) < 2.0 ** -45 * abs(pieces[0])
+
+
+def _acc_cases(rng):
+    def rnd(lo=EMIN, hi=EMAX):
+        return rng.choice((-1, 1)) * rng.uniform(1, 2) * 2.0 ** rng.randint(lo, hi)
+    cases = []
+    for n in (1, 2, 7, 24, 100, 300):
+        for _ in range(60):
+            cases.append([(rnd(), rnd()) for _ in range(n)])
+            cases.append([(rng.gauss(0, 1), rng.gauss(0, 1e-3)) for _ in range(n)])
+    # cancellation: the last product cancels the others up to its own rounding
+    for n in (2, 7, 24, 70):
+        for _ in range(80):
+            pairs = [(rnd(-8, 8), rnd(-8, 8)) for _ in range(n - 1)]
+            part = sum(Fraction(a) * Fraction(x) for a, x in pairs)
+            x_last = rnd(-4, 4)
+            a_last = -float(part / Fraction(x_last))
+            pairs.append((a_last, x_last))
+            cases.append(pairs)
+    return [c for c in cases if all(EMIN <= _exp(a) <= EMAX and EMIN <= _exp(x) <= EMAX
+                                    for a, x in c if a != 0 and x != 0)
+            and all(a != 0 and x != 0 for a, x in c)]
+
+
+def test_accumulated_products_within_two_to_the_minus_60(harness):
+    cases = _acc_cases(random.Random(2))
+    lines = ["A %d %s\n" % (len(c), " ".join("%s %s" % (a.hex(), x.hex()) for a, x in c))
+             for c in cases]
+    out = harness(lines)
+    assert len(out) == len(cases)
+    worst = 0.0
+    cancelling = 0
+    for c, line in zip(cases, out):
+        ok, h, m, l, d0, d1 = line.split()
+        assert ok == "1"
+        exact = sum(Fraction(a) * Fraction(x) for a, x in c)
+        mag = sum(abs(Fraction(a) * Fraction(x)) for a, x in c)
+        got3 = sum(Fraction(float.fromhex(t)) for t in (h, m, l))
+        got2 = Fraction(float.fromhex(d0)) + Fraction(float.fromhex(d1))
+        err = max(abs(got3 - exact), abs(got2 - exact)) / mag
+        worst = max(worst, float(err))
+        if abs(exact) < mag * 2.0 ** -40:
+            cancelling += 1
+    assert worst <= 2.0 ** -60, math.log2(worst)
+    assert cancelling > 100  # the cancellation cases really cancel
