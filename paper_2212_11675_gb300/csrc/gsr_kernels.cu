@@ -9,20 +9,24 @@
 //
 // aprod 1 is row-parallel: lane l of a warp takes row 32 t + l of tile t, so
 // every plane read is a whole aligned 256-byte segment (no half-used cache
-// lines).  The star of a row (for its five astrometric unknowns) comes from a
-// per-tile table of first stars plus a short walk along star_ptr.
+// lines).  The star of a row (for its five astrometric unknowns) is the
+// tile's first star plus a stored 16-bit delta.  The FP64 pipe bounds this
+// kernel on GB300, so by default its instrumental and global products are
+// formed on the binary32 pipes from exact splits (gsr_split.cuh).
 //
-// aprod 2 is split by column section:
-//  - astrometric, instrumental, global: star-parallel pass.  Rows are grouped
-//    by star (§3), so G lanes own one star, accumulate its five sums in
-//    registers and write them without atomics.  Instrumental columns are
-//    privatised per block in shared memory when they fit; the global column
-//    is reduced per block.
-//  - attitude: a pass over a copy of the 12 attitude values sorted by the
-//    attitude offset.  A warp reduces all rows of one offset o into 12 sums
-//    S[o][a][j] (axis a, tap j); column a*D + k then receives
-//    sum_j S[k-j][a][j].  No atomics, and the summation order is fixed, so
-//    this part is deterministic.
+// aprod 2 runs by default as one launch over a shared work queue with three
+// kinds of units, none of which needs an atomic:
+//  - star units: rows are grouped by star (§3), so G lanes own one star and
+//    reduce its five astrometric sums in registers; the global column gets
+//    one partial per unit;
+//  - attitude segments: a copy of the 12 attitude values sorted by attitude
+//    offset lets one warp reduce all rows of offset o into 12 sums
+//    S[o][a][j] (axis a, tap j); column a*D + k receives sum_j S[k-j][a][j];
+//  - instrument units: a copy of the instrumental entries sorted by
+//    instrument, cut into row windows, summed per instrument and window.
+// The partial sums are added in a fixed order, so aprod 2 is deterministic.
+// The same passes also run as separate launches, and the instrumental sums
+// can instead use shared-memory privatisation or per-SM L2 replicas.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
