@@ -512,10 +512,14 @@ def main():
     value = iters_total / t_max
 
     # end to end through the C ABI with host buffers (H2D of b and D2H of x,
-    # se inside the timed region)
-    bh = b.cpu().numpy().copy()
-    xh = np.empty(sys_.n)
-    seh = np.empty(sys_.n)
+    # se inside the timed region), held in pinned (page-locked) host memory as
+    # a caller streaming right-hand sides would hold them; the tensors own the
+    # memory the NumPy views point into
+    b_pin = torch.empty(sys_.m, dtype=torch.float64, pin_memory=True)
+    b_pin.copy_(b)
+    x_pin = torch.empty(sys_.n, dtype=torch.float64, pin_memory=True)
+    se_pin = torch.empty(sys_.n, dtype=torch.float64, pin_memory=True)
+    bh, xh, seh = b_pin.numpy(), x_pin.numpy(), se_pin.numpy()
     solver.lsqr_solve(bh, itmax, 0.0, 0.0, x=xh, se=seh, stream=stream)
     t0 = time.perf_counter()
     e2e_iters = 0
