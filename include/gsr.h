@@ -155,7 +155,10 @@ int gsr_create(void **h, const gsr_dims *dims, const uint32_t *star_ptr,
 int gsr_destroy(void *h);
 
 /* aprod mode 1 (Alg. 1): y[m] += A x[n], A the original (unpreconditioned)
- * matrix.  x and y must not overlap. */
+ * matrix.  x and y must not overlap.  The products are FP64-accurate in
+ * every form of gsr_config.products: each row sum is within the FP64
+ * rounding bound of the exact sum (the split form's products within 2^-60
+ * of their magnitudes, the rest FP64 FMAs). */
 int gsr_aprod1(void *h, const double *x, double *y, void *stream);
 
 /* aprod mode 2 (Alg. 2): x[n] += A^T y[m], shared columns summed exactly
