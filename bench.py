@@ -45,8 +45,47 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 FMA peak of GB300: 1.25 TFLOP/s nominal (152 SMs, 2070 MHz).
-FP64_NOMINAL_TFLOPS = 1.25
+# sources of the row kernels; a capture's DRAM traffic applies only while
+# their hash is the one recorded beside it
+KERNEL_SOURCES = ("gsr_kernels.cu", "gsr_internal.cuh", "gsr_split.cuh", "gsr_reduce.cuh")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2212_11675_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel, workload):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summaries under profiles/: a line
+      traffic: <kernel> workload=<w> dram_bytes_per_launch=<B> source_sha256=<h>
+    counts only while <h> is the hash of the current kernel sources (None
+    otherwise, or when no capture of this kernel and workload is recorded)."""
+    import glob
+    import re
+    want = kernel_source_hash()
+    pat = re.compile(r"^traffic:\s+(\S+)\s+workload=(\S+)\s+dram_bytes_per_launch=(\S+)\s+"
+                     r"source_sha256=([0-9a-f]+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for ln in f:
+                m_ = pat.match(ln.strip().strip("`"))
+                if m_ and m_.group(1) == kernel and m_.group(2) == workload and m_.group(4) == want:
+                    return float(m_.group(3)), os.path.relpath(path, ROOT)
+    return None, None
+
+
+def fp64_fma_rate():
+    """FP64 FMAs per second of this GPU, measured now by the library's probe."""
+    import ctypes
+    from paper_2212_11675_gb300 import _lib
+    r = ctypes.c_double(0.0)
+    _lib.check(_lib.lib().gsr_fp64_fma_rate(ctypes.byref(r)), "gsr_fp64_fma_rate")
+    return r.value
 
 
 class Clocks:
@@ -554,28 +593,29 @@ def main():
     dom = "aprod2" if t_a2 >= t_a1 else "aprod1"
     t_dom, gbs_dom, tf_dom, byt = ((t_a2, gbs_a2, tf_a2, bytes_a2) if dom == "aprod2"
                                    else (t_a1, gbs_a1, tf_a1, bytes_a1))
-    # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-    # capture of the in-solve launches of the current kernels on the medium
-    # workload (dram__bytes.sum.per_second x duration; null for another
-    # workload, and to be nulled once that kernel changes)
-    traffic = {"aprod2": 1.9412e9, "aprod1": 1.5422e9}.get(dom) if args.workload == "medium" else None
-    f_hbm = gbs_dom / hbm
-    f_alu = tf_dom / FP64_NOMINAL_TFLOPS
-    if f_alu >= f_hbm:
-        roof = {"bound": "alu", "achieved": tf_dom, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": f_alu, "traffic": traffic}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs_dom, "peak": hbm, "unit": "GB/s", "frac": f_hbm,
-                "traffic": traffic}
-    roof.update({"kernel": dom, "peak_source": "FP64 nominal (recipe)" if roof["bound"] == "alu"
-                 else "%s HBM copy" % src,
-                 "kernels": {"aprod1": {"ms": t_a1 * 1e3, "GB/s": gbs_a1, "hbm_frac": gbs_a1 / hbm,
-                                        "fp64_TFLOP/s": tf_a1, "fp64_frac": tf_a1 / FP64_NOMINAL_TFLOPS,
-                                        "split_products": split1},
-                             "aprod2": {"ms": t_a2 * 1e3, "GB/s": gbs_a2, "hbm_frac": gbs_a2 / hbm,
-                                        "fp64_TFLOP/s": tf_a2, "fp64_frac": tf_a2 / FP64_NOMINAL_TFLOPS,
-                                        "split_products": split2}},
-                 "aprod_GB/s": (bytes_a1 + bytes_a2) / (t_a1 + t_a2) / 1e9})
+    # DRAM bytes (read + write) per launch of the dominant kernel from the
+    # committed ncu capture of the current kernel sources (null when the
+    # kernel changed since, or for a workload without a capture)
+    kname = {"aprod2": "k_aprod2_fused", "aprod1": "k_aprod1"}[dom]
+    traffic, traffic_src = captured_traffic(kname, args.workload)
+    fma_rate = fp64_fma_rate()
+    fp64_peak = 2.0 * fma_rate / 1e12  # TFLOP/s, measured in this run
+    roof = {"bound": "hbm", "achieved": gbs_dom, "peak": hbm, "unit": "GB/s",
+            "frac": gbs_dom / hbm, "traffic": traffic, "kernel": kname,
+            "peak_source": "%s HBM copy (MEASURED_PEAKS.json)" % src,
+            "traffic_source": traffic_src,
+            "algorithmic_bytes_per_launch": byt,
+            "fp64_pipe": {"achieved_TFLOP/s": tf_dom, "peak_TFLOP/s": fp64_peak,
+                          "frac": tf_dom / fp64_peak,
+                          "peak_source": "FP64 FMA chains on every SM, measured in this run"},
+            "kernels": {"aprod1": {"ms": t_a1 * 1e3, "GB/s": gbs_a1, "hbm_frac": gbs_a1 / hbm,
+                                   "fp64_TFLOP/s": tf_a1, "fp64_frac": tf_a1 / fp64_peak,
+                                   "split_products": split1},
+                        "aprod2": {"ms": t_a2 * 1e3, "GB/s": gbs_a2, "hbm_frac": gbs_a2 / hbm,
+                                   "fp64_TFLOP/s": tf_a2, "fp64_frac": tf_a2 / fp64_peak,
+                                   "split_products": split2}},
+            "aprod_GB/s": (bytes_a1 + bytes_a2) / (t_a1 + t_a2) / 1e9,
+            "aprod_hbm_frac": (bytes_a1 + bytes_a2) / (t_a1 + t_a2) / 1e9 / hbm}
 
     mixed = None
     batched = None

@@ -48,7 +48,8 @@ extern "C" {
 #define GSR_ERR_INDEX (-2)       /* structure out of range (star_ptr, attoff, instr) */
 #define GSR_ERR_OOM (-3)         /* device or host allocation failed */
 #define GSR_ERR_CUDA (-4)        /* a CUDA runtime call failed */
-#define GSR_ERR_TIMEOUT (-5)     /* a bounded device wait expired */
+/* (-5) is unused: no entry point waits on the device with a time limit (the
+ * solve loops are conditional CUDA graph nodes, not spin-waits) */
 #define GSR_ERR_NONFINITE (-6)   /* NaN or Inf in the input or in the recurrences */
 #define GSR_ERR_UNSUPPORTED (-7) /* configuration not supported by this build */
 
@@ -192,22 +193,28 @@ int gsr_lsqr_solve(void *h, const double *b, int itmax, double atol,
  * not allocate device memory at call time (another component owns the
  * device-memory budget through its own pool, or a cudaMalloc would
  * synchronise the device where the caller cannot afford it).
- *  - x and y must be device pointers (host vectors would need staging
- *    memory): otherwise GSR_ERR_ARG.  ynorm may be a device pointer or a host
- *    pointer; with a host pointer the call synchronises the stream.
+ *  - x and y must be device pointers on the handle's device (host vectors
+ *    would need staging memory; another device's memory would be read over
+ *    the peer link): otherwise GSR_ERR_ARG.  ynorm may be device memory of
+ *    the handle's device or host memory; with a host pointer the call copies
+ *    the norm back and synchronises the stream, so that form cannot be
+ *    recorded into a stream capture.
  *  - Scratch: one file-scope device array of 36 KiB (a state slot, one
- *    8-byte partial sum per thread block, a ticket counter), held by every
- *    GPU that loads the library until the process exits.  The kernel never
- *    uses more than 4096 blocks, whatever the system size; a launch that
- *    would need more partial sums than the array holds is rejected with
- *    GSR_ERR_ARG before anything runs.
- *  - The first call on a device looks up the array's device address (with
- *    the handle's device made current for the call); make that first call
- *    before any stream capture that might include later calls.
+ *    8-byte partial sum per thread block, a ticket counter), held on every
+ *    GPU where a handle has been created until the process exits.  The
+ *    kernel never uses more than 4096 blocks, whatever the system size; a
+ *    launch that would need more partial sums than the array holds is
+ *    rejected with GSR_ERR_ARG before anything runs.
+ *  - Set-up: gsr_create (which allocates anyway) looks up the array's device
+ *    address on the handle's device and loads the code that uses it, so a
+ *    call of this entry point does no set-up of its own, loads no module
+ *    and allocates nothing.
+ *  - cy reaches the device as a kernel argument (no host-to-device copy).
  *  - All calls share the array and it keeps the last call's contents (the
- *    counter is cleared at the start of every call).  Calls whose work
- *    overlaps on the GPU (different streams, or different handles at the
- *    same time) race on it: order them on one stream.
+ *    coefficient slot and the counter are written at the start of every
+ *    call, on the caller's stream).  Calls whose work overlaps on the GPU
+ *    (different streams, or different handles at the same time) race on
+ *    it: order them on one stream.
  *  - No cudaMalloc, cudaFree or other allocating routine is called.
  */
 int gsr_aprod1_norm_noalloc(void *h, const double *x, double *y, double cy,
@@ -344,6 +351,16 @@ int gsr_set_batch_tiling(void *h, int kt, int lanes);
  * instrumental path), GSR_ERR_CUDA.
  */
 int gsr_set_aprod2_fused(void *h, int fused);
+
+/*
+ * Measured FP64 fused multiply-add throughput of the current device, in FMAs
+ * per second (*fma_per_s), for the roofline of the FP64 row kernels: one
+ * launch of independent FMA chains on every SM, timed with CUDA events
+ * (about a millisecond on a GB300; synchronises the device).  The paper has
+ * no counterpart; it is a measurement helper.  Errors: GSR_ERR_ARG,
+ * GSR_ERR_CUDA.
+ */
+int gsr_fp64_fma_rate(double *fma_per_s);
 
 /* Text of the last CUDA failure seen by this host thread ("" if none). */
 const char *gsr_last_error(void);

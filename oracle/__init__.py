@@ -37,9 +37,9 @@ def lib():
         L.or_aprod2_f32.argtypes = sysargs + [_P, _P]
         L.or_colnorms.argtypes = sysargs + [_P]
         L.or_precondition.argtypes = sysargs + [_P, _P]
-        L.or_lsqr.argtypes = sysargs + [_P, _I, _D, _D, _D, _P, _P, _P, _P]
+        L.or_lsqr.argtypes = sysargs + [_P, _I, _D, _D, _D, _P, _P, _P, _P, ctypes.c_int]
         L.or_lsqr.restype = ctypes.c_int
-        L.or_pc_lsqr.argtypes = sysargs + [_P, _I, _D, _D, _D, _P, _P, _P, _P, _P]
+        L.or_pc_lsqr.argtypes = sysargs + [_P, _I, _D, _D, _D, _P, _P, _P, _P, _P, ctypes.c_int]
         L.or_pc_lsqr.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -110,8 +110,11 @@ def precondition(sys):
     return p, scaled
 
 
-def lsqr(sys, b, itmax, atol=1e-12, btol=1e-12, conlim=1e8, values=None, trace=False):
-    """Plain LSQR on the given values (no preconditioning). Returns dict."""
+def lsqr(sys, b, itmax, atol=1e-12, btol=1e-12, conlim=1e8, values=None, trace=False,
+         run_to_itmax=False):
+    """Plain LSQR on the given values (no preconditioning). Returns dict.
+    run_to_itmax: iterate to itmax whatever the stopping rules say (they are
+    reported for the last iteration)."""
     keep, a = _sysargs(sys, values)
     b = np.ascontiguousarray(b, dtype=np.float64)
     z = np.empty(sys.n)
@@ -119,7 +122,7 @@ def lsqr(sys, b, itmax, atol=1e-12, btol=1e-12, conlim=1e8, values=None, trace=F
     st = np.zeros(8)
     tr = np.full(max(int(itmax), 1), np.nan) if trace else None
     rc = lib().or_lsqr(*a, _ptr(b), int(itmax), atol, btol, conlim, _ptr(z), _ptr(var), _ptr(st),
-                       _ptr(tr) if trace else None)
+                       _ptr(tr) if trace else None, 1 if run_to_itmax else 0)
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     out = {"z": z, "var": var, **{k: st[i] for i, k in enumerate(STAT_NAMES)}}
@@ -129,8 +132,10 @@ def lsqr(sys, b, itmax, atol=1e-12, btol=1e-12, conlim=1e8, values=None, trace=F
     return out
 
 
-def pc_lsqr(sys, b, itmax, atol=1e-12, btol=1e-12, conlim=1e8, trace=False):
-    """Preconditioned LSQR of the flowchart: returns x, se, p and the stopping estimates."""
+def pc_lsqr(sys, b, itmax, atol=1e-12, btol=1e-12, conlim=1e8, trace=False, run_to_itmax=False):
+    """Preconditioned LSQR of the flowchart: returns x, se, p and the stopping
+    estimates.  run_to_itmax: iterate to itmax whatever the stopping rules say
+    (they are reported for the last iteration)."""
     keep, a = _sysargs(sys)
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.empty(sys.n)
@@ -139,7 +144,7 @@ def pc_lsqr(sys, b, itmax, atol=1e-12, btol=1e-12, conlim=1e8, trace=False):
     st = np.zeros(8)
     tr = np.full(max(int(itmax), 1), np.nan) if trace else None
     rc = lib().or_pc_lsqr(*a, _ptr(b), int(itmax), atol, btol, conlim, _ptr(x), _ptr(se), _ptr(p),
-                          _ptr(st), _ptr(tr) if trace else None)
+                          _ptr(st), _ptr(tr) if trace else None, 1 if run_to_itmax else 0)
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     out = {"x": x, "se": se, "p": p, **{k: st[i] for i, k in enumerate(STAT_NAMES)}}

@@ -246,13 +246,17 @@ enum { ST_ISTOP, ST_ITN, ST_RNORM, ST_ARNORM, ST_ANORM, ST_ACOND, ST_XNORM, ST_B
  * used as is (pass the preconditioned values for PC-LSQR).
  * Outputs: z[n] the solution, var[n] the sum of (w_i/rho_i)^2, stats[8].
  * trace_rnorm (optional, itmax entries): rnorm estimate after each iteration.
+ * run_to_itmax: nonzero runs exactly itmax iterations (unless x = 0 is exact):
+ * the stopping rules are still evaluated every iteration, but only the last
+ * iteration's verdict is reported in istop.  The arithmetic is unchanged;
+ * this serves comparisons at a fixed iteration count.
  */
 int or_lsqr(int64_t S, int64_t D, int64_t I,
             const uint32_t *star_ptr, const uint32_t *attoff,
             const uint16_t *instr, const double *values,
             const double *b, int64_t itmax, double atol, double btol,
             double conlim, double *z, double *var, double *stats,
-            double *trace_rnorm)
+            double *trace_rnorm, int run_to_itmax)
 {
     const int64_t m = star_ptr[S];
     const int64_t n = or_n_unknowns(S, D, I);
@@ -357,6 +361,8 @@ int or_lsqr(int64_t S, int64_t D, int64_t I,
             if (test3 <= ctol) istop = 3;
             if (test2 <= atol) istop = 2;
             if (test1 <= rtol) istop = 1;
+            if (run_to_itmax && itn < itmax)
+                istop = 0;
             if (istop != 0)
                 break;
         }
@@ -383,7 +389,7 @@ int or_pc_lsqr(int64_t S, int64_t D, int64_t I,
                const uint16_t *instr, const double *values,
                const double *b, int64_t itmax, double atol, double btol,
                double conlim, double *x, double *se, double *p,
-               double *stats, double *trace_rnorm)
+               double *stats, double *trace_rnorm, int run_to_itmax)
 {
     const int64_t m = star_ptr[S];
     const int64_t n = or_n_unknowns(S, D, I);
@@ -396,7 +402,7 @@ int or_pc_lsqr(int64_t S, int64_t D, int64_t I,
     }
     or_precondition(S, D, I, star_ptr, attoff, instr, values, p, scaled);
     int rc = or_lsqr(S, D, I, star_ptr, attoff, instr, scaled, b, itmax, atol,
-                     btol, conlim, z, var, stats, trace_rnorm);
+                     btol, conlim, z, var, stats, trace_rnorm, run_to_itmax);
     if (rc == 0) {
         const double dof = (m > n) ? (double)(m - n) : 1.0;
         const double t = stats[ST_RNORM] / sqrt(dof);

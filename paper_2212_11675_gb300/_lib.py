@@ -17,7 +17,6 @@ GSR_ERR_ARG = -1
 GSR_ERR_INDEX = -2
 GSR_ERR_OOM = -3
 GSR_ERR_CUDA = -4
-GSR_ERR_TIMEOUT = -5
 GSR_ERR_NONFINITE = -6
 GSR_ERR_UNSUPPORTED = -7
 
@@ -32,7 +31,7 @@ EXPORTS = (
     "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32", "gsr_mixed_solve",
     "gsr_set_values", "gsr_normal_solve", "gsr_lsq_backward", "gsr_batched_solve",
     "gsr_batched_products", "gsr_set_batch_tiling", "gsr_set_aprod2_fused",
-    "gsr_product_forms",
+    "gsr_product_forms", "gsr_fp64_fma_rate",
 )
 
 
@@ -125,6 +124,7 @@ def lib():
             L.gsr_set_batch_tiling.argtypes = [P, I, I]
             L.gsr_set_aprod2_fused.argtypes = [P, I]
             L.gsr_product_forms.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+            L.gsr_fp64_fma_rate.argtypes = [ctypes.POINTER(D)]
             L.gsr_last_error.restype = ctypes.c_char_p
             L.gsr_strerror.argtypes = [I]
             L.gsr_strerror.restype = ctypes.c_char_p
@@ -134,7 +134,8 @@ def lib():
                          "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32",
                          "gsr_mixed_solve", "gsr_set_values", "gsr_normal_solve",
                          "gsr_lsq_backward", "gsr_batched_solve", "gsr_batched_products",
-                         "gsr_set_batch_tiling", "gsr_set_aprod2_fused", "gsr_product_forms"):
+                         "gsr_set_batch_tiling", "gsr_set_aprod2_fused", "gsr_product_forms",
+                         "gsr_fp64_fma_rate"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib

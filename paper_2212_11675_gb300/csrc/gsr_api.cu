@@ -51,7 +51,6 @@ extern "C" const char *gsr_strerror(int code)
     case GSR_ERR_INDEX: return "matrix structure out of range";
     case GSR_ERR_OOM: return "out of memory";
     case GSR_ERR_CUDA: return "CUDA runtime error";
-    case GSR_ERR_TIMEOUT: return "device wait timed out";
     case GSR_ERR_NONFINITE: return "non-finite value";
     case GSR_ERR_UNSUPPORTED: return "unsupported configuration";
     default: return "unknown error";
@@ -513,6 +512,9 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     }
     TRY(dalloc(h, &h->d_gpart, ngp));
 
+    // scratch of gsr_aprod1_norm_noalloc: resolved here, where allocating is
+    // allowed, so that entry point never loads a module or allocates
+    TRY(noalloc_prepare(h->device));
     cudaError_t e = build_solve_graph(h);
     if (e != cudaSuccess)
         return cuda_fail(e, "build_solve_graph");

@@ -327,6 +327,8 @@ cudaError_t enqueue_iteration(const gsr_handle_t *h, cudaStream_t s,
                               cudaGraphConditionalHandle loop, int in_graph);
 cudaError_t enqueue_epilogue(const gsr_handle_t *h, cudaStream_t s);
 cudaError_t launch_precond_finish(const gsr_handle_t *h, double *p, cudaStream_t st);
+// gsr_noalloc.cu: scratch address of gsr_aprod1_norm_noalloc on device dev
+int noalloc_prepare(int dev);
 
 enum Aprod2Mode { kA2Accumulate = 0, kA2Overwrite = 1, kA2Squares = 2 };
 

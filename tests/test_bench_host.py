@@ -60,3 +60,22 @@ def test_reference_arm_line():
     assert line["impl"] == "reference" and line["unit"] == "iter/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
+
+
+def test_captured_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic is read from a committed capture summary
+    only while the kernel sources hash to the value recorded beside it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.kernel_source_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "cap.md").write_text(
+        "notes\n`traffic: k_aprod2_fused workload=medium dram_bytes_per_launch=1.5e9 "
+        "source_sha256=%s`\ntraffic: k_aprod1 workload=medium dram_bytes_per_launch=2e9 "
+        "source_sha256=0000000000000000\n" % h)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    assert bench.captured_traffic("k_aprod2_fused", "medium") == (1.5e9, "profiles/cap.md")
+    assert bench.captured_traffic("k_aprod2_fused", "tiny") == (None, None)
+    assert bench.captured_traffic("k_aprod1", "medium") == (None, None)  # stale hash

@@ -162,6 +162,48 @@ def test_lsqr_stopping_rules_match_scipy():
     assert r["itn"] == ref[2]
 
 
+def test_lsqr_machine_precision_rules_match_scipy():
+    """Rules 4 and 5 (S1 and S2 with the tolerance at machine precision) fire
+    as in SciPy: with atol = btol = 0 and no condition limit, a consistent
+    system stops on rule 4 and an inconsistent one on rule 5, within a few
+    iterations of SciPy (the last iterations are rounding-dominated).  Rule 6
+    (the condition estimate beyond 1/eps) is not pinned: on these shapes
+    rule 5 fires first in both implementations."""
+    scipy_lsqr = pytest.importorskip("scipy.sparse.linalg").lsqr
+    sys = small(30, 12, 8, seed=3)
+    A = dense(sys)
+    rng = np.random.default_rng(1)
+    b = A @ rng.standard_normal(sys.n)
+    r = oracle.lsqr(sys, b, 2000, atol=0.0, btol=0.0, conlim=0.0)
+    ref = scipy_lsqr(A, b, atol=0.0, btol=0.0, conlim=0.0, iter_lim=2000)
+    assert r["istop"] == ref[1] == 4
+    assert abs(r["itn"] - ref[2]) <= 5
+    b = b + 1e-3 * rng.standard_normal(sys.m)
+    r = oracle.lsqr(sys, b, 2000, atol=0.0, btol=0.0, conlim=0.0)
+    ref = scipy_lsqr(A, b, atol=0.0, btol=0.0, conlim=0.0, iter_lim=2000)
+    assert r["istop"] == ref[1] == 5
+    assert abs(r["itn"] - ref[2]) <= 5
+
+
+def test_run_to_itmax_changes_no_arithmetic():
+    """run_to_itmax only keeps the loop going: up to the iteration where a
+    rule fires, the iterates are bit-identical to a run that stops there, and
+    past it they equal a run with every rule switched off."""
+    sys = small(30, 12, 8)
+    _, b = _rhs(sys)
+    stop = oracle.pc_lsqr(sys, b, 1000, atol=1e-6, btol=0.0, conlim=0.0)
+    assert stop["istop"] == 2 and stop["itn"] < 200
+    k = stop["itn"]
+    same = oracle.pc_lsqr(sys, b, k, atol=1e-6, btol=0.0, conlim=0.0, run_to_itmax=True)
+    np.testing.assert_array_equal(same["x"], stop["x"])
+    assert same["itn"] == k and same["istop"] == 2
+    longer = oracle.pc_lsqr(sys, b, k + 30, atol=1e-6, btol=0.0, conlim=0.0, run_to_itmax=True)
+    free = oracle.pc_lsqr(sys, b, k + 30, atol=0.0, btol=0.0, conlim=0.0, run_to_itmax=True)
+    assert longer["itn"] == free["itn"] == k + 30
+    np.testing.assert_array_equal(longer["x"], free["x"])
+    np.testing.assert_array_equal(longer["se"], free["se"])
+
+
 def test_pc_lsqr_matches_lapack_lstsq():
     sys = small(30, 12, 8)
     A = dense(sys)
