@@ -64,24 +64,29 @@ extern "C" {
                                 is deterministic */
 
 /* How the FP64 row kernels form their products; every choice is
- * FP64-accurate. */
+ * FP64-accurate.  A split product is formed on the binary32 pipes from exact
+ * three-piece binary32 splits of both operands, with error-free products and
+ * sums, within 2^-60 of the sum of the magnitudes of the products it
+ * accumulates (below the rounding of one FP64 FMA).  Operands whose exponent
+ * is outside [-30, 30] (zero entries excepted) send their row (aprod 1),
+ * block (aprod 1's x), star group or instrument unit (aprod 2) to native FP64
+ * products.  gsr_product_forms() tells which forms a handle runs. */
 #define GSR_PRODUCTS_AUTO 0   /* library choice: aprod 1's split form where it
-                                 applies (I <= 3072), native products otherwise */
+                                 applies (I <= 3072); native products
+                                 otherwise and in aprod 2 */
 #define GSR_PRODUCTS_NATIVE 1 /* every product on the FP64 pipe */
-#define GSR_PRODUCTS_SPLIT 2  /* products formed on the binary32 pipes from exact
-                                 three-piece binary32 splits of both operands,
-                                 with error-free products and sums, within 2^-60
-                                 of the sum of their magnitudes (below the
-                                 rounding of one FP64 FMA): aprod 1's 6
-                                 instrumental and global products of each row
-                                 (needs I <= 3072, GSR_ERR_UNSUPPORTED
-                                 otherwise) and the astrometric and global
-                                 products of aprod 2's single-launch pass.
-                                 Operands whose exponent is outside [-30, 30]
-                                 (zero x or y entries excepted) send their row
-                                 (aprod 1), block (aprod 1's x) or star group
-                                 (aprod 2) to native FP64 products.
-                                 gsr_product_forms() tells which apply */
+#define GSR_PRODUCTS_SPLIT 2  /* every split form: GSR_SPLIT_APROD1 |
+                                 GSR_SPLIT_APROD2_STARS | GSR_SPLIT_APROD2_INSTR */
+#define GSR_PRODUCTS_MASK 0x100 /* GSR_PRODUCTS_MASK | a set of the bits below:
+                                   exactly the split forms named */
+#define GSR_SPLIT_APROD1 1        /* aprod 1: the 6 instrumental and the global
+                                     product of each row (needs I <= 3072;
+                                     GSR_ERR_UNSUPPORTED at creation otherwise) */
+#define GSR_SPLIT_APROD2_STARS 2  /* aprod 2's single-launch pass: the
+                                     astrometric and global products of its
+                                     star units */
+#define GSR_SPLIT_APROD2_INSTR 4  /* aprod 2's single-launch pass: the products
+                                     of its instrument units */
 
 /* Storage and arithmetic of the matrix values. */
 #define GSR_PREC_FP64 0  /* IEEE double values, native FP64 arithmetic */
@@ -262,11 +267,11 @@ int gsr_mixed_solve(void *h, const double *b, int max_outer, int max_inner,
 
 /*
  * Which FP64 products of the handle run on the binary32 pipes from exact
- * splits (GSR_PRODUCTS_SPLIT form): *aprod1_split_on = 1 when aprod 1 forms
- * its instrumental and global products that way, *aprod2_split_on = 1 when
- * aprod 2's single-launch pass forms its astrometric and global products
- * that way; 0 for native FP64 products.  Host only, no CUDA call.  Errors:
- * GSR_ERR_ARG.
+ * splits: *aprod1_split_on = 1 when aprod 1 forms its instrumental and
+ * global products that way (0: native FP64); *aprod2_split_on is a set of
+ * bits for aprod 2's single-launch pass: 1 its star units' astrometric and
+ * global products, 2 its instrument units' products (0: native FP64
+ * everywhere).  Host only, no CUDA call.  Errors: GSR_ERR_ARG.
  */
 int gsr_product_forms(void *h, int *aprod1_split_on, int *aprod2_split_on);
 

@@ -2,6 +2,7 @@
 // validation of the Gaia system), the two products, the preconditioner and
 // the whole PC-LSQR solve.  No torch types cross this boundary.
 #include <cuda_runtime.h>
+#include <stdlib.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -501,8 +502,8 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
         const int64_t nsu32 = (h->sys.S + 3) / 4;
         if (nsu32 > nsu)
             nsu = nsu32;
-        if (nsu > ((int64_t)1 << 30))
-            h->a2_fused = 0;  // one global partial per star unit: keep the buffer bounded
+        if (nsu > ((int64_t)1 << 30) || a2_queue(h, h->lanes).total >= ((int64_t)1 << 32))
+            h->a2_fused = 0;  // bounded partials buffer; 32-bit unit indices
         else if (nsu > ngp)
             ngp = (int)nsu;
         TRY(dalloc(h, &h->d_a2ctr, 1));
@@ -569,9 +570,13 @@ extern "C" int gsr_create(void **out, const gsr_dims *d, const uint32_t *star_pt
         return GSR_ERR_ARG;
     if (c.instr_mode == GSR_INSTR_SMEM && d->n_instr > 6144)
         return GSR_ERR_UNSUPPORTED;
-    if (c.products < GSR_PRODUCTS_AUTO || c.products > GSR_PRODUCTS_SPLIT)
+    if ((c.products < GSR_PRODUCTS_AUTO || c.products > GSR_PRODUCTS_SPLIT) &&
+        (c.products & ~7) != GSR_PRODUCTS_MASK)
         return GSR_ERR_ARG;
-    if (c.products == GSR_PRODUCTS_SPLIT && d->n_instr > 3072)
+    // an explicit request for aprod 1's split form needs the split
+    // instrumental x in shared memory
+    if (c.products != GSR_PRODUCTS_AUTO && (split_request(c) & GSR_SPLIT_APROD1) &&
+        d->n_instr > 3072)
         return GSR_ERR_UNSUPPORTED;
     gsr_handle_t *h = new (std::nothrow) gsr_handle_t();
     if (!h)
@@ -840,7 +845,7 @@ extern "C" int gsr_product_forms(void *hv, int *aprod1_split_on, int *aprod2_spl
     if (!h || !aprod1_split_on || !aprod2_split_on)
         return GSR_ERR_ARG;
     *aprod1_split_on = aprod1_split(h) ? 1 : 0;
-    *aprod2_split_on = aprod2_split_active(h) ? 1 : 0;
+    *aprod2_split_on = aprod2_split_active(h);
     return GSR_OK;
 }
 

@@ -290,8 +290,9 @@ cudaError_t launch_tile_star(const gsr_handle_t *h, cudaStream_t st);
 cudaError_t launch_gather_att(const gsr_handle_t *h, cudaStream_t st);
 int aprod1_grid(const gsr_handle_t *h);
 bool aprod1_split(const gsr_handle_t *h);
-bool aprod2_split(const gsr_handle_t *h);
-bool aprod2_split_active(const gsr_handle_t *h);
+int split_request(const gsr_config &cfg);
+int aprod2_split(const gsr_handle_t *h);
+int aprod2_split_active(const gsr_handle_t *h);
 bool instr_in_smem(const gsr_handle_t *h);
 cudaError_t launch_att_combine(const gsr_handle_t *h, double *out, int nb_att, int nb_ins,
                                double *rep, int nrep, const double *gpart, int ngpart,

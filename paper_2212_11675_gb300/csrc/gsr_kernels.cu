@@ -380,6 +380,63 @@ __device__ __forceinline__ double acc3_to_double(const Acc3 &c)
     return d0 + d1;
 }
 
+// One instrument unit (entries e0 .. e1-1 of the instrument-sorted copy,
+// one instrument in one row window) with its products on the binary32 pipes:
+// every value and every gathered y is split exactly into three binary32
+// pieces (gsr_split.cuh) and the products are accumulated on three binary32
+// levels, two accumulators per lane (four gathers of y in flight), then
+// reduced over the warp with exact level sums.  The result is within about
+// 2^-60 of the sum of the |products| (below the rounding of one FP64 FMA).
+// Returns false, with nothing written, when an operand of the unit is outside
+// the split range (a zero excepted): the caller then sums the unit with
+// native FP64 products.  The total is valid in every lane.
+__device__ __forceinline__ bool instr_unit_split(uint32_t e0, uint32_t e1,
+                                                 const uint32_t *__restrict__ irow,
+                                                 const double *__restrict__ ival,
+                                                 const double *__restrict__ y, double &tot)
+{
+    const int lane = threadIdx.x & 31;
+    Acc3 c[2] = {Acc3{0.f, 0.f, 0.f}, Acc3{0.f, 0.f, 0.f}};
+    uint32_t rng = 0;
+    uint32_t e = e0 + lane;
+    for (; e + 96 < e1; e += 128) {
+        double v[4], yv[4];
+        uint32_t r[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            v[u] = __ldcs(ival + e + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            r[u] = __ldcs(irow + e + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            yv[u] = __ldg(y + r[u]);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            float a1, a2, a3, b1, b2, b3;
+            rng = max(rng, split3z(v[u], a1, a2, a3));
+            rng = max(rng, split3z(yv[u], b1, b2, b3));
+            acc3_fma(c[u & 1], a1, a2, a3, b1, b2, b3);
+        }
+    }
+    for (int u = 0; e < e1; e += 32, u++) {
+        float a1, a2, a3, b1, b2, b3;
+        rng = max(rng, split3z(__ldcs(ival + e), a1, a2, a3));
+        rng = max(rng, split3z(__ldg(y + __ldcs(irow + e)), b1, b2, b3));
+        acc3_fma(c[u & 1], a1, a2, a3, b1, b2, b3);
+    }
+    if (__any_sync(0xffffffffu, rng >= kSplitRangeSpan))
+        return false;
+    acc3_add(c[0], c[1].h, c[1].m, c[1].l);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const Acc3 send = c[0];
+        acc3_add_shfl(c[0], send, off);
+    }
+    tot = acc3_to_double(c[0]);
+    return true;
+}
+
 // Star-group part of the single-launch aprod 2 with the astrometric and
 // global products on the binary32 pipes (exact splits of the values and of
 // y, gsr_split.cuh): the five astrometric sums of a star and this lane's
@@ -699,18 +756,24 @@ k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
 // device counter, so the roles balance themselves; the combine kernel
 // resets the counter.  Which warp computes a unit does not change its sums:
 // the global column gets one partial per star unit, gpart[unit].
+// SPL: which units form their products on the binary32 pipes from exact
+// splits (kSplitStars: star units, kSplitInstr: instrument units); the
+// others, and every unit of the preconditioner's squares, use native FP64.
 // ---------------------------------------------------------------------------
-template <int G, int MODE, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 4)  // 64 registers: no spills in either form
+constexpr int kSplitStars = 1;
+constexpr int kSplitInstr = 2;
+
+template <int G, int MODE, int SPL>
+__global__ void __launch_bounds__(kThreads, 4)  // 64 registers: no spills in any form
 k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out,
                double *__restrict__ S, const uint32_t *__restrict__ cseg,
                const uint32_t *__restrict__ irow, const double *__restrict__ ival,
                double *__restrict__ part, int nwin, double *__restrict__ gpart, A2Queue q)
 {
-    static_assert(!SPLIT || MODE != kA2Squares, "the preconditioner keeps native products");
+    static_assert(SPL == 0 || MODE != kA2Squares, "the preconditioner keeps native products");
     constexpr bool SQ = MODE == kA2Squares;
     const int lane = threadIdx.x & 31;
-    const int L = q.ns + q.na + q.ni;
+    const uint32_t L = (uint32_t)(q.ns + q.na + q.ni);
     for (;;) {
         unsigned long long u = 0;
         if (lane == 0)
@@ -718,8 +781,9 @@ k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out
         u = __shfl_sync(0xffffffffu, u, 0);
         if ((int64_t)u >= q.total)
             break;
-        const int64_t c = (int64_t)u / L;
-        const int slot = (int)((int64_t)u - c * L);
+        // q.total < 2^32 (checked at creation): 32-bit unit decode
+        const int64_t c = (uint32_t)u / L;
+        const int slot = (int)((uint32_t)u - (uint32_t)c * L);
         if (slot < q.ns) {
             const int64_t i = c * q.ns + slot;
             if (i < q.nstar_units) {
@@ -730,7 +794,7 @@ k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out
                 for (int k = 0; k < q.star_k; k++) {
                     const int64_t grp = i * q.star_k + k;
                     if (grp < q.nstar_groups) {
-                        if constexpr (SPLIT)
+                        if constexpr ((SPL & kSplitStars) != 0)
                             g += stars_body_split<G, MODE>(A, y, out, grp, q.nstar_groups);
                         else
                             g += stars_body<G, MODE, kIpSorted>(A, y, out, nullptr, 1, nullptr,
@@ -747,8 +811,17 @@ k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out
                 att_body<SQ>(A, y, S, i, A.nseg);
         } else {
             const int64_t i = c * q.ni + (slot - q.ns - q.na);
-            if (i < q.ninstr_units)
-                instr_body<SQ>(A, cseg, irow, ival, y, part, nwin, i, q.ninstr_units);
+            if (i < q.ninstr_units) {
+                bool done = false;
+                if constexpr ((SPL & kSplitInstr) != 0) {
+                    double tot;
+                    done = instr_unit_split(cseg[i], cseg[i + A.I], irow, ival, y, tot);
+                    if (done && lane == 0)
+                        part[i] = tot;  // unit i = window q, instrument f: part[q I + f]
+                }
+                if (!done)  // native FP64 products (an operand outside the split range)
+                    instr_body<SQ>(A, cseg, irow, ival, y, part, nwin, i, q.ninstr_units);
+            }
         }
     }
 }
@@ -832,9 +905,24 @@ k_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ out,
 // many instruments (48 KB per block; three blocks per SM still fit)
 constexpr int64_t kSplitInstrMax = 3072;
 
+// the products formed on the binary32 pipes, as GSR_SPLIT_* bits
+int split_request(const gsr_config &cfg)
+{
+    const int p = cfg.products;
+    if (p == GSR_PRODUCTS_NATIVE)
+        return 0;
+    if (p == GSR_PRODUCTS_SPLIT)
+        return GSR_SPLIT_APROD1 | GSR_SPLIT_APROD2_STARS | GSR_SPLIT_APROD2_INSTR;
+    if ((p & ~7) == GSR_PRODUCTS_MASK)
+        return p & 7;
+    // library choice, measured on the medium workload: aprod 1's instrumental
+    // and global products only (see aprod2_split for aprod 2's forms)
+    return GSR_SPLIT_APROD1;
+}
+
 bool aprod1_split(const gsr_handle_t *h)
 {
-    return h->cfg.products != GSR_PRODUCTS_NATIVE && h->sys.I <= kSplitInstrMax;
+    return (split_request(h->cfg) & GSR_SPLIT_APROD1) && h->sys.I <= kSplitInstrMax;
 }
 
 template <int MODE>
@@ -993,39 +1081,50 @@ A2Queue a2_queue(const gsr_handle_t *h, int G, int64_t ninstr_units)
             if (p > periods)
                 periods = p;
         }
-    q.total = periods * (q.ns + q.na + q.ni);
+    q.total = periods * (q.ns + q.na + q.ni);  // below 2^32: checked at creation
     return q;
 }
 
-// the products of aprod 2 (not the preconditioner's squares) take the split
-// star pass only when asked for: measured on the medium workload it was
-// slower (0.411 against 0.388 ms per launch), the star units being a quarter
-// of the pass's FP64 work and its attitude and instrument units sharing the SMs
-bool aprod2_split(const gsr_handle_t *h)
+// the kSplit* units of the single-launch aprod 2 that form their products on
+// the binary32 pipes (never the preconditioner's squares); only an explicit
+// request splits them.  Measured on the medium workload (ncu, one launch):
+//  - split star units were slower (0.411 against 0.388 ms; a quarter of the
+//    pass's FP64 work, and the attitude and instrument units sharing the SMs
+//    lost issue slots to them);
+//  - split instrument units cut the FP64 instructions from 6.54 M to 5.17 M
+//    warp-instructions and the FP64 pipe from 93 % to 76 % active, but the
+//    launch stayed at 370 us: it then waits on memory (the y gathers and 1.93
+//    GB of DRAM reads), and the whole solve was about 1 % slower.
+int aprod2_split(const gsr_handle_t *h)
 {
-    return h->cfg.products == GSR_PRODUCTS_SPLIT;
+    const int r = split_request(h->cfg);
+    return ((r & GSR_SPLIT_APROD2_STARS) ? kSplitStars : 0) |
+           ((r & GSR_SPLIT_APROD2_INSTR) ? kSplitInstr : 0);
 }
 
-bool aprod2_split_active(const gsr_handle_t *h)
+int aprod2_split_active(const gsr_handle_t *h)
 {
-    return h->ipath == kIpSorted && h->a2_fused && aprod2_split(h);
+    return (h->ipath == kIpSorted && h->a2_fused) ? aprod2_split(h) : 0;
 }
 
 template <int G, int MODE>
 static void fused_launch(const gsr_handle_t *h, const double *y, double *out, cudaStream_t st)
 {
     const A2Queue q = a2_queue(h, G);
+#define GSR_FUSED(SPL)                                                                          \
+    k_aprod2_fused<G, MODE, SPL><<<h->grid_fused, kThreads, 0, st>>>(                           \
+        h->sys, y, out, h->d_attS, h->d_cseg, h->d_irow, h->d_ival, h->d_ipart, h->isplit, \
+        h->d_gpart, q)
     if constexpr (MODE != kA2Squares) {
-        if (aprod2_split(h)) {
-            k_aprod2_fused<G, MODE, true><<<h->grid_fused, kThreads, 0, st>>>(
-                h->sys, y, out, h->d_attS, h->d_cseg, h->d_irow, h->d_ival, h->d_ipart,
-                h->isplit, h->d_gpart, q);
-            return;
+        switch (aprod2_split(h)) {
+        case kSplitStars: GSR_FUSED(kSplitStars); return;
+        case kSplitInstr: GSR_FUSED(kSplitInstr); return;
+        case kSplitStars | kSplitInstr: GSR_FUSED(kSplitStars | kSplitInstr); return;
+        default: break;
         }
     }
-    k_aprod2_fused<G, MODE, false><<<h->grid_fused, kThreads, 0, st>>>(
-        h->sys, y, out, h->d_attS, h->d_cseg, h->d_irow, h->d_ival, h->d_ipart, h->isplit,
-        h->d_gpart, q);
+    GSR_FUSED(0);
+#undef GSR_FUSED
 }
 
 template <int MODE>
@@ -1355,11 +1454,20 @@ static int a2_occupancy(const gsr_handle_t *h)
 template <int G>
 static cudaError_t fused_occupancy(const gsr_handle_t *h, int *occ)
 {
-    return aprod2_split(h)
-               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                     occ, k_aprod2_fused<G, kA2Overwrite, true>, kThreads, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                     occ, k_aprod2_fused<G, kA2Overwrite, false>, kThreads, 0);
+    switch (aprod2_split(h)) {
+    case kSplitStars:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, k_aprod2_fused<G, kA2Overwrite, kSplitStars>, kThreads, 0);
+    case kSplitInstr:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, k_aprod2_fused<G, kA2Overwrite, kSplitInstr>, kThreads, 0);
+    case kSplitStars | kSplitInstr:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, k_aprod2_fused<G, kA2Overwrite, kSplitStars | kSplitInstr>, kThreads, 0);
+    default:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, k_aprod2_fused<G, kA2Overwrite, 0>, kThreads, 0);
+    }
 }
 
 int aprod2_fused_grid(const gsr_handle_t *h)

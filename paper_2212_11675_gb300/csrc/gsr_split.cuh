@@ -72,6 +72,19 @@ __device__ __forceinline__ void split3(uint32_t hi, uint32_t lo, float &h, float
     l = __fmaf_rn(__uint_as_float(0x4b000000u | (lo & 0x3fu)), s3, -c3);
 }
 
+// split3 of a binary64 d given as a value: zero splits into zeros (and is in
+// range); returns split3_range of d (>= kSplitRangeSpan: out of range)
+__device__ __forceinline__ uint32_t split3z(double d, float &a1, float &a2, float &a3)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    split3(hi, lo, a1, a2, a3);
+    if (((hi & 0x7fffffffu) | lo) == 0u) {
+        a1 = a2 = a3 = 0.f;
+        return 0u;
+    }
+    return split3_range(hi);
+}
+
 // Knuth's TwoSum: returns s = fl(a + b) and sets e with s + e = a + b exactly
 __device__ __forceinline__ float two_sum(float a, float b, float &e)
 {

@@ -196,11 +196,12 @@ class Solver:
 
     def product_forms(self):
         """(aprod1_split, aprod2_split): which FP64 products run on the binary32
-        pipes from exact splits (GSR_PRODUCTS_SPLIT form)."""
+        pipes from exact splits: aprod1_split a bool, aprod2_split a set of bits
+        (1 star units, 2 instrument units of the single-launch aprod 2)."""
         a1, a2 = ctypes.c_int(), ctypes.c_int()
         check(lib().gsr_product_forms(self._h, ctypes.byref(a1), ctypes.byref(a2)),
               "gsr_product_forms")
-        return bool(a1.value), bool(a2.value)
+        return bool(a1.value), int(a2.value)
 
     def set_batch_tiling(self, kt, lanes):
         """Column tile (1, 2, 4, 8) and lanes per star (8, 16, 32) of the batched kernels."""

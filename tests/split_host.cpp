@@ -6,6 +6,7 @@
 //
 // stdin, one request per line:
 //   S a               -> "h m l" pieces of split3(a), then split3_range ok (0/1)
+//   Z a               -> the same from split3z(a) (zero in range, zero pieces)
 //   A n a0 x0 ... -> n products accumulated with acc3_fma: "ok h m l d0 d1"
 // numbers in C hex-float notation.
 #include <cmath>
@@ -44,6 +45,18 @@ static inline double __hiloint2double(int hi, int lo)
     memcpy(&d, &v, 8);
     return d;
 }
+static inline int __double2hiint(double d)
+{
+    uint64_t b;
+    memcpy(&b, &d, 8);
+    return (int)(uint32_t)(b >> 32);
+}
+static inline int __double2loint(double d)
+{
+    uint64_t b;
+    memcpy(&b, &d, 8);
+    return (int)(uint32_t)b;
+}
 
 #include "gsr_split.cuh"
 
@@ -71,6 +84,13 @@ int main()
             split3(hi, lo, h, m, l);
             printf("%a %a %a %d\n", (double)h, (double)m, (double)l,
                    split3_range(hi) < kSplitRangeSpan ? 1 : 0);
+        } else if (op == 'Z') {
+            double a;
+            if (scanf("%la", &a) != 1)
+                return 2;
+            float h, m, l;
+            const uint32_t r = split3z(a, h, m, l);
+            printf("%a %a %a %d\n", (double)h, (double)m, (double)l, r < kSplitRangeSpan ? 1 : 0);
         } else if (op == 'A') {
             int n;
             if (scanf("%d", &n) != 1)

@@ -1,5 +1,6 @@
-"""The split product forms (GSR_PRODUCTS_SPLIT; aprod 1's is the default
-where I <= 3072) against exact rational arithmetic: the split products are
+"""The split product forms (GSR_PRODUCTS_SPLIT and the GSR_PRODUCTS_MASK
+choices; aprod 1's is the default where I <= 3072) against exact rational
+arithmetic: the split products are
 accumulated to within about 2^-60 of the sum of their magnitudes, so a row
 (or a star's column sum) made only of them stays accurate under heavy
 cancellation, where a chain of FP64 FMAs loses up to 2^-53 of that sum per
@@ -212,6 +213,75 @@ def test_split_star_sums_out_of_range_fall_back():
         assert np.all(_err(g, ex) <= 30 * U * mag), case
 
 
+INSTR_ONLY = _lib.GSR_PRODUCTS_MASK | _lib.GSR_SPLIT_APROD2_INSTR
+
+
+def _instrument_entries(sys):
+    """(row, slot) pairs of every instrument, in row order."""
+    out = [[] for _ in range(sys.n_instr)]
+    for i in range(sys.m):
+        for j in range(6):
+            out[int(sys.instr[i, j])].append((i, j))
+    return out
+
+
+@pytest.mark.parametrize("products", [INSTR_ONLY, _lib.GSR_PRODUCTS_SPLIT])
+def test_split_instrument_sums_exact_under_cancellation(products):
+    # aprod 2's instrumental sums: in every instrument the last entry's value
+    # cancels the instrument's other products (about 2^41 each), so the
+    # exact column sum is a rounding residual; each instrument holds a few
+    # hundred entries (the unit's four-entry loop and its tail)
+    sys = small(40, 12, 9, obs=9, seed=21)
+    rng = np.random.default_rng(21)
+    vals = sys.values.copy()
+    vals[:, 17:23] = rng.uniform(1.0, 2.0, size=(sys.m, 6)) * 2.0 ** 20
+    y = rng.uniform(1.0, 2.0, size=sys.m) * 2.0 ** 20 * np.where(np.arange(sys.m) % 2 == 0, 1, -1)
+    for ent in _instrument_entries(sys):
+        part = sum(Fraction(float(vals[i, 17 + j])) * Fraction(float(y[i])) for i, j in ent[:-1])
+        i, j = ent[-1]
+        vals[i, 17 + j] = -float(part / Fraction(float(y[i])))
+    sys = gen.GaiaSystem(sys.n_stars, sys.n_dfa, sys.n_instr, sys.star_ptr, sys.attoff,
+                         sys.instr, vals)
+    x0 = np.zeros(sys.n)
+    ex, mag = _exact_t(sys, y, x0)
+    exf = np.array([float(e) for e in ex])
+    ins = 5 * sys.n_stars + 3 * sys.n_dfa + np.arange(sys.n_instr)
+    assert min(len(e) for e in _instrument_entries(sys)) > 128
+    assert np.median(mag[ins] / np.maximum(np.abs(exf[ins]), 1e-300)) > 1e6
+    g = _aprod2(sys, y, x0, products)
+    err = _err(g, ex)
+    assert np.all(err[ins] <= 3 * U * np.abs(exf[ins]) + 2.0 ** -60 * mag[ins])
+    assert np.all(err <= 30 * U * mag)
+    gn = _aprod2(sys, y, x0, _lib.GSR_PRODUCTS_NATIVE)
+    errn = _err(gn, ex)
+    assert np.all(errn <= 30 * U * mag)
+    assert np.max(errn[ins] / np.maximum(np.abs(exf[ins]), 1e-300)) > 1e-12
+
+
+def test_split_instrument_sums_out_of_range_fall_back():
+    # an operand outside the split range sends its instrument unit to native
+    # FP64 products; zero values and zero y split exactly
+    sys = small(60, 20, 13, obs=12, seed=22)
+    rng = np.random.default_rng(23)
+    vals = sys.values.copy()
+    vals[5, 18] = 1e-13   # instrumental value below the split range
+    vals[40, 21] = 5e11   # above it
+    vals[41, 17] = 0.0    # zero value
+    sys = gen.GaiaSystem(sys.n_stars, sys.n_dfa, sys.n_instr, sys.star_ptr, sys.attoff,
+                         sys.instr, vals)
+    x0 = rng.standard_normal(sys.n)
+    for case in range(3):
+        y = rng.standard_normal(sys.m)
+        if case == 1:
+            y[100] = 1e-16  # y below the range: six units fall back
+        if case == 2:
+            y[::7] = 0.0    # zero y splits exactly
+        ex, mag = _exact_t(sys, y, x0)
+        for products in (INSTR_ONLY, _lib.GSR_PRODUCTS_SPLIT):
+            g = _aprod2(sys, y, x0, products)
+            assert np.all(_err(g, ex) <= 30 * U * mag), (case, products)
+
+
 @pytest.mark.parametrize("lanes", [4, 8, 16, 32])
 def test_split_star_pass_every_lane_count(lanes):
     # the split star pass of aprod 2 (explicit GSR_PRODUCTS_SPLIT) with 4 lanes
@@ -224,13 +294,17 @@ def test_product_forms_report_what_runs():
     from paper_2212_11675_gb300.solver import Solver
     tiny = gen.make("tiny")
     with Solver(tiny) as s:  # default: split aprod 1, native aprod 2
-        assert s.product_forms() == (True, False)
+        assert s.product_forms() == (True, 0)
     with Solver(tiny, products=_lib.GSR_PRODUCTS_NATIVE) as s:
-        assert s.product_forms() == (False, False)
+        assert s.product_forms() == (False, 0)
     with Solver(tiny, products=_lib.GSR_PRODUCTS_SPLIT) as s:
-        assert s.product_forms() == (True, True)
+        assert s.product_forms() == (True, 3)
+    with Solver(tiny, products=INSTR_ONLY) as s:
+        assert s.product_forms() == (False, 2)
+    with Solver(tiny, products=_lib.GSR_PRODUCTS_MASK | _lib.GSR_SPLIT_APROD2_STARS) as s:
+        assert s.product_forms() == (False, 1)
     with Solver(tiny, products=_lib.GSR_PRODUCTS_SPLIT, instr_mode=_lib.GSR_INSTR_SMEM) as s:
-        assert s.product_forms() == (True, False)  # no single-launch aprod 2 on this path
+        assert s.product_forms() == (True, 0)  # no single-launch aprod 2 on this path
     # more instruments than the split x fits in shared memory: native aprod 1
     with Solver(small(300, 50, 7000, seed=9)) as s:
         assert s.product_forms()[0] is False

@@ -111,3 +111,20 @@ def test_accumulated_products_within_two_to_the_minus_60(harness):
             cancelling += 1
     assert worst <= 2.0 ** -60, math.log2(worst)
     assert cancelling > 100  # the cancellation cases really cancel
+
+
+def test_split3z_takes_zero_and_agrees_with_split3(harness):
+    """split3z, the value-argument form the instrument units use: a zero of
+    either sign splits into zero pieces and counts as in range; every other
+    value gives split3's pieces and range verdict."""
+    rng = random.Random(3)
+    vals = [0.0, -0.0, 1.0, -1.5, 2.0 ** EMIN, 2.0 ** (EMIN - 1), 2.0 ** (EMAX + 1)]
+    vals += [rng.gauss(0, 1) * 2.0 ** rng.randint(-40, 40) for _ in range(500)]
+    zs = harness(["Z %s\n" % float(v).hex() for v in vals])
+    ss = harness(_split_lines(vals))
+    for v, z, s in zip(vals, zs, ss):
+        if v == 0.0:
+            h, m, l, ok = z.split()
+            assert float.fromhex(h) == float.fromhex(m) == float.fromhex(l) == 0.0 and ok == "1"
+        else:
+            assert z == s, v
