@@ -89,7 +89,7 @@ k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ld
 #pragma unroll
         for (int c = 0; c < KT; c++)
             h[c] = l[c] = 0.f;
-        const float *v = A.val32 + r;
+        const float *v = A.val32 + tidx<kNPar>(0, r);  // plane k at v + 32 k
 #pragma unroll
         for (int k = 0; k < kNPar; k++) {
             int64_t col;
@@ -101,7 +101,7 @@ k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ld
                 col = A.ins0 + instr_b(rc, k - kNAstro - kNAtt);
             else
                 col = A.glb0;
-            const float a = __ldcs(v + k * mp);
+            const float a = __ldcs(v + 32 * k);
             float xv[KT];
             load_cols<KT>(X + col * ldk + c0, xv);
 #pragma unroll
@@ -165,17 +165,17 @@ k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ld
             for (int c = 0; c < KT; c++)
                 ah[k][c] = al[k][c] = 0.f;
         for (uint32_t r = r0 + lane; r < r1; r += G) {
-            const float *v = A.val32 + r;
+            const float *v = A.val32 + tidx<kNPar>(0, r);
             float yv[KT];
             load_cols<KT>(Y + (int64_t)r * ldk + c0, yv);
 #pragma unroll
             for (int k = 0; k < kNAstro; k++) {
-                const float a = __ldcs(v + k * mp);
+                const float a = __ldcs(v + 32 * k);
 #pragma unroll
                 for (int c = 0; c < KT; c++)
                     df_acc(ah[k][c], al[k][c], __fmul_rn(a, yv[c]));
             }
-            const float ag = __ldcs(v + 23 * mp);
+            const float ag = __ldcs(v + 32 * 23);
 #pragma unroll
             for (int c = 0; c < KT; c++)
                 df_acc(gh[c], gl[c], __fmul_rn(ag, yv[c]));
@@ -241,7 +241,7 @@ k_b_att(SysView A, const float *__restrict__ Y, double *__restrict__ S, int ldk,
             load_cols<KT>(Y + (int64_t)__ldcs(A.perm + e) * ldk + c0, yv);
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const float v = __ldcs(A.tval32 + (4 * a + j) * mp + e);
+                const float v = __ldcs(A.tval32 + tidx<kNAtt>(4 * a + j, e));
 #pragma unroll
                 for (int c = 0; c < KT; c++)
                     df_acc(h[j * KT + c], l[j * KT + c], __fmul_rn(v, yv[c]));

@@ -108,11 +108,11 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
         if (r < A.m) {
             const uint32_t s = star_of_row(A, t, r);
             const uint4 rc = __ldcs(A.rec + r);
-            const double *v = A.val + r;
+            const double *v = A.val + tidx<kNPar>(0, r);  // plane k at v + 32 k
             double vk[kNPar];
 #pragma unroll
             for (int k = 0; k < kNPar; k++)
-                vk[k] = __ldcs(v + k * mp);
+                vk[k] = __ldcs(v + 32 * k);
             // two independent partial sums (astrometric + global +
             // instrumental, attitude) keep the FP64 pipe fed with one merge
             // (four sums were 4% slower: two more FP64 adds per row)
@@ -269,15 +269,15 @@ __device__ __forceinline__ double stars_body(const SysView &A, const double *__r
             // the sorted path leaves the instrumental nonzeros to its own pass
             constexpr bool INS = IP != kIpSorted;
             const uint4 rc = INS ? __ldcs(A.rec + r) : make_uint4(0, 0, 0, 0);
-            const double *v = A.val + r;
+            const double *v = A.val + tidx<kNPar>(0, r);
             double va[kNAstro], vi[kNInstr], vg;
 #pragma unroll
             for (int k = 0; k < kNAstro; k++)
-                va[k] = __ldcs(v + k * mp);
+                va[k] = __ldcs(v + 32 * k);
 #pragma unroll
             for (int j = 0; j < kNInstr; j++)
-                vi[j] = INS ? __ldcs(v + (17 + j) * mp) : 0.0;
-            vg = __ldcs(v + 23 * mp);
+                vi[j] = INS ? __ldcs(v + 32 * (17 + j)) : 0.0;
+            vg = __ldcs(v + 32 * 23);
             double yi;
             if (MODE == kA2Squares) {
                 yi = 1.0;
@@ -467,11 +467,11 @@ __device__ __forceinline__ double stars_body_split(const SysView &A, const doubl
             c[k] = Acc3{0.f, 0.f, 0.f};
         uint32_t rng = 0;
         for (uint32_t r = r0 + lane; r < r1; r += G) {
-            const double *v = A.val + r;
+            const double *v = A.val + tidx<kNPar>(0, r);
             double va[kNAstro + 1];
 #pragma unroll
             for (int k = 0; k <= kNAstro; k++)
-                va[k] = __ldcs(v + (k < kNAstro ? k : 23) * mp);
+                va[k] = __ldcs(v + 32 * (k < kNAstro ? k : 23));
             const double yi = __ldcs(y + r);
             const uint32_t yhi = (uint32_t)__double2hiint(yi), ylo = (uint32_t)__double2loint(yi);
             float y1, y2, y3;
@@ -674,7 +674,7 @@ __global__ void k_gather_instr64(SysView A, const uint32_t *__restrict__ code,
          e += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = code[e];
         const uint32_t row = c / kNInstr, slot = c - row * kNInstr;
-        out[e] = A.val[(int64_t)(kNAstro + kNAtt + slot) * A.mp + row];
+        out[e] = A.val[tidx<kNPar>(kNAstro + kNAtt + slot, row)];
     }
 }
 
@@ -706,7 +706,7 @@ __device__ __forceinline__ void att_body(const SysView &A, const double *__restr
             const double yi = SQ ? 1.0 : __ldg(y + __ldcs(A.perm + e));
 #pragma unroll
             for (int k = 0; k < kNAtt; k++) {
-                double v = __ldcs(A.tval + k * mp + e);
+                double v = __ldcs(A.tval + tidx<kNAtt>(k, e));
                 if (SQ)
                     v *= v;
                 acc[k] = fma(v, yi, acc[k]);
@@ -1228,7 +1228,7 @@ k_planes(const double *__restrict__ rowmajor, double *__restrict__ val, int64_t 
     for (int t = threadIdx.x; t < 64 * kNPar; t += blockDim.x) {
         const int k = t / 64, r = t % 64;
         if (r < nr)
-            val[k * mp + row0 + b0 + r] = tile[r * kNPar + k];
+            val[tidx<kNPar>(k, row0 + b0 + r)] = tile[r * kNPar + k];
     }
 }
 
@@ -1312,7 +1312,7 @@ __global__ void k_gather_att(SysView A, double *__restrict__ tval)
         const int64_t r = A.perm[e];
 #pragma unroll
         for (int k = 0; k < kNAtt; k++)
-            tval[k * A.mp + e] = A.val[(kNAstro + k) * A.mp + r];
+            tval[tidx<kNAtt>(k, e)] = A.val[tidx<kNPar>(kNAstro + k, r)];
     }
 }
 
@@ -1327,14 +1327,14 @@ __global__ void k_set_plane(SysView A, int k, const double *__restrict__ v, doub
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.m;
          i += (int64_t)gridDim.x * blockDim.x)
-        val[k * A.mp + i] = v[i];
+        val[tidx<kNPar>(k, i)] = v[i];
 }
 
 __global__ void k_regather_att_plane(SysView A, int k, double *__restrict__ tval)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A.m;
          e += (int64_t)gridDim.x * blockDim.x)
-        tval[(k - kNAstro) * A.mp + e] = A.val[k * A.mp + A.perm[e]];
+        tval[tidx<kNAtt>(k - kNAstro, e)] = A.val[tidx<kNPar>(k, A.perm[e])];
 }
 
 cudaError_t launch_set_plane(const gsr_handle_t *h, int k, const double *v, cudaStream_t st)
@@ -1385,7 +1385,7 @@ __global__ void k_validate(SysView A, int *err, int check_values)
                 e |= 4;
         if (check_values)
             for (int k = 0; k < kNPar; k++)
-                if (!isfinite(A.val[k * A.mp + i]))
+                if (!isfinite(A.val[tidx<kNPar>(k, i)]))
                     e |= 8;
     }
     if (e)

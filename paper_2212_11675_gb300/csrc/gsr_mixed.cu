@@ -72,10 +72,10 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, const float4 *__restrict_
             if (ok[u]) {
                 st[u] = star_of_row(A, t, r);
                 rc[u] = __ldcs(A.rec + r);
-                const float *v = A.val32 + r;
+                const float *v = A.val32 + tidx<kNPar>(0, r);  // plane k at v + 32 k
 #pragma unroll
                 for (int k = 0; k < kNPar; k++)
-                    vk[u][k] = __ldcs(v + k * mp);
+                    vk[u][k] = __ldcs(v + 32 * k);
             }
         }
 #pragma unroll
@@ -163,23 +163,23 @@ __device__ __forceinline__ double stars_body_f32(const SysView &A, const float *
         for (int k = 0; k < kNAstro; k++)
             ah[k] = al[k] = 0.f;
         for (uint32_t r = r0 + lane; r < r1; r += G) {
-            const float *v = A.val32 + r;
+            const float *v = A.val32 + tidx<kNPar>(0, r);
             const float yi = __ldcs(y32 + r);
 #pragma unroll
             for (int k = 0; k < kNAstro; k++)
-                df_acc(ah[k], al[k], __fmul_rn(__ldcs(v + k * mp), yi));
+                df_acc(ah[k], al[k], __fmul_rn(__ldcs(v + 32 * k), yi));
             if (INS) {
                 const uint4 rc = __ldcs(A.rec + r);
 #pragma unroll
                 for (int j = 0; j < kNInstr; j++) {
-                    const float pr = __fmul_rn(__ldcs(v + (17 + j) * mp), yi);
+                    const float pr = __fmul_rn(__ldcs(v + 32 * (17 + j)), yi);
                     if (IP == kIpSmem)
                         atomicAdd(&s_ins[instr_at32(rc, j)], f2d(pr));
                     else
                         atomicAdd(myrep + instr_at32(rc, j), f2d(pr));
                 }
             }
-            df_acc(gh, gl, __fmul_rn(__ldcs(v + 23 * mp), yi));
+            df_acc(gh, gl, __fmul_rn(__ldcs(v + 32 * 23), yi));
         }
         // the star's five sums over its G lanes, in double-float
 #pragma unroll
@@ -264,8 +264,8 @@ __device__ __forceinline__ void att_body_f32(const SysView &A, const float *__re
             float va[kNAtt], vb[kNAtt];
 #pragma unroll
             for (int k = 0; k < kNAtt; k++) {
-                va[k] = __ldcs(A.tval32 + k * mp + e);
-                vb[k] = __ldcs(A.tval32 + k * mp + e + 32);
+                va[k] = __ldcs(A.tval32 + tidx<kNAtt>(k, e));
+                vb[k] = __ldcs(A.tval32 + tidx<kNAtt>(k, e + 32));
             }
             const float ya = __ldg(y32 + ra), yb = __ldg(y32 + rb);
 #pragma unroll
@@ -278,7 +278,7 @@ __device__ __forceinline__ void att_body_f32(const SysView &A, const float *__re
             const float yi = __ldg(y32 + __ldcs(A.perm + e));
 #pragma unroll
             for (int k = 0; k < kNAtt; k++)
-                df_acc(h[k], l[k], __fmul_rn(__ldcs(A.tval32 + k * mp + e), yi));
+                df_acc(h[k], l[k], __fmul_rn(__ldcs(A.tval32 + tidx<kNAtt>(k, e)), yi));
         }
         // reduce-scatter over the warp in double-float (FP32 pipe): after
         // the butterfly, lane pair (2k, 2k+1) holds sum k
@@ -1055,14 +1055,24 @@ cudaError_t run_cg64(gsr_handle_t *h, cudaStream_t st, int max_iter)
     return e;
 }
 
+// binary32 copy of plane k of K tiled planes (k_to_f32 over one plane)
+template <int K>
+__global__ void k_plane_to_f32(const double *__restrict__ a, float *__restrict__ b, int k, int64_t m)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = tidx<K>(k, i);
+        b[j] = (float)a[j];
+    }
+}
+
 // binary32 copies of plane k after it changed
 cudaError_t launch_f32_plane(const gsr_handle_t *h, int k, cudaStream_t st)
 {
-    const int64_t mp = h->sys.mp;
-    k_to_f32<<<h->nsm * 8, kThreads, 0, st>>>(h->d_val + k * mp, h->d_val32 + k * mp, h->sys.m);
+    k_plane_to_f32<kNPar><<<h->nsm * 8, kThreads, 0, st>>>(h->d_val, h->d_val32, k, h->sys.m);
     if (k >= kNAstro && k < kNAstro + kNAtt)
-        k_to_f32<<<h->nsm * 8, kThreads, 0, st>>>(h->d_tval + (k - kNAstro) * mp,
-                                                   h->d_tval32 + (k - kNAstro) * mp, h->sys.m);
+        k_plane_to_f32<kNAtt><<<h->nsm * 8, kThreads, 0, st>>>(h->d_tval, h->d_tval32, k - kNAstro,
+                                                              h->sys.m);
     return cudaGetLastError();
 }
 
