@@ -568,21 +568,30 @@ def main():
     e2e = {"value": ws * e2e_iters / e2e_t, "unit": "iter/s",
            "h2d_bytes_per_step": int(bh.nbytes), "d2h_bytes_per_step": int(xh.nbytes + seh.nbytes)}
 
-    # roofline of the two row kernels, each timed alone through its entry point
+    # roofline of the row kernels as they run inside a solve: the launches of
+    # 20 LSQR iterations timed with CUDA events on the solve's stream (aprod 1
+    # in its LSQR form with ||U||, the single-launch aprod 2 whose partial sums
+    # the vector pass combines, the vector pass); each product is also timed
+    # alone through its entry point (y += A x, x += A^T y with its combine),
+    # for reference
     m, n = sys_.m, sys_.n
+    ins = solver.time_iteration(b, iters=20, stream=stream)
+    t_a1, t_a2, t_vec = ins["aprod1"] * 1e-3, ins["aprod2"] * 1e-3, ins["vector_pass"] * 1e-3
     yv = torch.zeros(m, dtype=torch.float64, device=dev)
     xv = torch.zeros(n, dtype=torch.float64, device=dev)
     vin = torch.randn(n, dtype=torch.float64, device=dev)
     uin = torch.randn(m, dtype=torch.float64, device=dev)
     reps = 20
-    t_a1 = time_kernel(lambda: solver.aprod1(vin, yv, stream=stream), stream, reps, torch)
-    t_a2 = time_kernel(lambda: solver.aprod2(uin, xv, stream=stream), stream, reps, torch)
+    api_a1 = time_kernel(lambda: solver.aprod1(vin, yv, stream=stream), stream, reps, torch)
+    api_a2 = time_kernel(lambda: solver.aprod2(uin, xv, stream=stream), stream, reps, torch)
     hbm, src = peaks()
     # algorithmic bytes per launch: 24 values x 8 B + 16 B index record per row,
     # y read+write (aprod 1) or read (aprod 2), 4 B star pointer per star,
-    # x gathered / written once per unknown
+    # x gathered / written once per unknown; the vector pass: 11 n-vectors
+    # (p, q, v, w, z, var read; w, z, var, v, p o v written)
     bytes_a1 = m * (24 * 8 + 16 + 16) + 4 * sys_.n_stars + 8 * n
     bytes_a2 = m * (24 * 8 + 16 + 8) + 4 * sys_.n_stars + 16 * n
+    bytes_vec = 11 * 8 * n
     # FLOPs on the FP64 pipe: one FMA per nonzero, less the products formed on
     # the binary32 pipes from exact splits (7 per row in aprod 1; in aprod 2,
     # 6 per row in the star units, 6 in the instrument units)
@@ -605,16 +614,19 @@ def main():
             "frac": gbs_dom / hbm, "traffic": traffic, "kernel": kname,
             "peak_source": "%s HBM copy (MEASURED_PEAKS.json)" % src,
             "traffic_source": traffic_src,
+            "timing": "in-solve launches (CUDA events, 20 LSQR iterations, host-launched)",
             "algorithmic_bytes_per_launch": byt,
             "fp64_pipe": {"achieved_TFLOP/s": tf_dom, "peak_TFLOP/s": fp64_peak,
                           "frac": tf_dom / fp64_peak,
                           "peak_source": "FP64 FMA chains on every SM, measured in this run"},
             "kernels": {"aprod1": {"ms": t_a1 * 1e3, "GB/s": gbs_a1, "hbm_frac": gbs_a1 / hbm,
                                    "fp64_TFLOP/s": tf_a1, "fp64_frac": tf_a1 / fp64_peak,
-                                   "split_products": split1},
+                                   "split_products": split1, "api_call_ms": api_a1 * 1e3},
                         "aprod2": {"ms": t_a2 * 1e3, "GB/s": gbs_a2, "hbm_frac": gbs_a2 / hbm,
                                    "fp64_TFLOP/s": tf_a2, "fp64_frac": tf_a2 / fp64_peak,
-                                   "split_products": split2}},
+                                   "split_products": split2, "api_call_ms": api_a2 * 1e3},
+                        "vector_pass": {"ms": t_vec * 1e3, "GB/s": bytes_vec / t_vec / 1e9,
+                                        "hbm_frac": bytes_vec / t_vec / 1e9 / hbm}},
             "aprod_GB/s": (bytes_a1 + bytes_a2) / (t_a1 + t_a2) / 1e9,
             "aprod_hbm_frac": (bytes_a1 + bytes_a2) / (t_a1 + t_a2) / 1e9 / hbm}
 

@@ -367,6 +367,19 @@ int gsr_set_aprod2_fused(void *h, int fused);
  */
 int gsr_fp64_fma_rate(double *fma_per_s);
 
+/*
+ * Durations of the three launches of an LSQR iteration as they run inside a
+ * solve, for the roofline of the row kernels: the preconditioner and the
+ * start of a solve of b[m] (host or device), then `iters` (1..256)
+ * iterations launched from the host with CUDA events between aprod 1 (the
+ * LSQR form y = A x + cy y with ||y||), aprod 2 and the vector pass.
+ * ms3[0..2] receive their average durations in milliseconds.  The handle's
+ * solve buffers are left mid-solve (the next solve starts afresh); no
+ * solution is returned.  The paper has no counterpart; it is a measurement
+ * helper.  Synchronises the stream.  Errors: GSR_ERR_ARG, GSR_ERR_CUDA.
+ */
+int gsr_time_iteration(void *h, const double *b, int iters, double *ms3, void *stream);
+
 /* Text of the last CUDA failure seen by this host thread ("" if none). */
 const char *gsr_last_error(void);
 

@@ -2,7 +2,6 @@
 // validation of the Gaia system), the two products, the preconditioner and
 // the whole PC-LSQR solve.  No torch types cross this boundary.
 #include <cuda_runtime.h>
-#include <stdlib.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -484,6 +483,9 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     if (gv > (int64_t)h->nsm * 2) gv = (int64_t)h->nsm * 2;
     if (gv > kMaxPartials) gv = kMaxPartials;
     h->grid_vec = (int)(gv < 1 ? 1 : gv);
+    h->grid_lsqr_vec = lsqr_vec_grid(h);
+    if (h->grid_lsqr_vec <= 0)
+        return cuda_fail(cudaGetLastError(), "vector pass occupancy");
     if (h->ipath == kIpReplicas || (h->cfg.precision == GSR_PREC_MIXED && !instr_in_smem(h))) {
         h->nrep = h->nsm;
         TRY(dalloc(h, &h->d_irep, (int64_t)h->nrep * I));
@@ -740,6 +742,62 @@ extern "C" int gsr_lsqr_solve(void *hv, const double *b, int itmax, double atol,
         out->bnorm = s.bnorm;
     }
     return s.nonfinite ? GSR_ERR_NONFINITE : GSR_OK;
+}
+
+extern "C" int gsr_time_iteration(void *hv, const double *b, int iters, double *ms3, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !b || !ms3 || iters < 1 || iters > 256)
+        return GSR_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *db, *dx;
+    TRY(stage(h, &h->d_bstage, h->sys.m, b, &db, true, st));
+    if (!h->d_xstage)
+        TRY(dalloc(h, &h->d_xstage, h->sys.n));
+    dx = h->d_xstage;
+    SolveArgs *a = h->h_args;
+    a->b = db;
+    a->x = dx;
+    a->se = nullptr;
+    a->itmax = iters;
+    a->force_itmax = 1;
+    a->atol = a->btol = 0.0;
+    a->ctol = 0.0;
+    a->isdof = 1.0 / sqrt((h->sys.m > h->sys.n) ? (double)(h->sys.m - h->sys.n) : 1.0);
+    CK(cudaMemcpyAsync(h->d_args, a, sizeof(SolveArgs), cudaMemcpyHostToDevice, st));
+    std::vector<cudaEvent_t> ev((size_t)3 * iters + 1, nullptr);
+    int rc = GSR_OK;
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            rc = GSR_ERR_CUDA;
+        }
+    cudaError_t e = cudaSuccess;
+    if (rc == GSR_OK)
+        e = enqueue_prologue(h, st, 0, 0);
+    if (rc == GSR_OK && e == cudaSuccess)
+        e = cudaEventRecord(ev[0], st);
+    for (int it = 0; rc == GSR_OK && e == cudaSuccess && it < iters; it++)
+        e = enqueue_iteration_timed(h, st, ev.data() + 3 * it);
+    if (rc == GSR_OK && e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    double sum[3] = {0.0, 0.0, 0.0};
+    for (int it = 0; rc == GSR_OK && e == cudaSuccess && it < iters; it++)
+        for (int k = 0; k < 3 && e == cudaSuccess; k++) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[3 * it + k], ev[3 * it + k + 1]);
+            sum[k] += ms;
+        }
+    for (auto &x : ev)
+        if (x)
+            cudaEventDestroy(x);
+    if (rc != GSR_OK)
+        return rc;
+    if (e != cudaSuccess)
+        return cuda_fail(e, "gsr_time_iteration");
+    for (int k = 0; k < 3; k++)
+        ms3[k] = sum[k] / iters;
+    return GSR_OK;
 }
 
 extern "C" int gsr_aprod1_f32(void *hv, const double *x, double *y, void *stream)

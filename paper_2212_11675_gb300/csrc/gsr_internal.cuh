@@ -85,7 +85,10 @@ __device__ __forceinline__ double q_from_parts(const SysView &A, const A2Parts &
 {
     double t = 0.0;
     if (j < A.ins0) {
-        const int64_t c = j - A.att0, a = c / A.D, k = c - a * A.D;
+        // axis a and knot k of attitude column c by two comparisons (a 64-bit
+        // division is a long instruction sequence on the GPU)
+        const int64_t c = j - A.att0;
+        const int64_t a = (c >= A.D) + (c >= 2 * A.D), k = c - a * A.D;
 #pragma unroll
         for (int jj = 0; jj < 4; jj++) {
             const int64_t o = k - jj;
@@ -268,6 +271,7 @@ struct gsr_handle_t {
     cudaGraphExec_t solve_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
     int grid_rows = 0, grid_rows2 = 0, grid_vec = 0, grid_att = 0, grid_ins = 0;
+    int grid_lsqr_vec = 0;              // the LSQR vector pass: every resident block
 };
 
 namespace gsr {
@@ -341,7 +345,9 @@ cudaError_t enqueue_prologue(const gsr_handle_t *h, cudaStream_t s,
 cudaError_t enqueue_iteration(const gsr_handle_t *h, cudaStream_t s,
                               cudaGraphConditionalHandle loop, int in_graph);
 cudaError_t enqueue_epilogue(const gsr_handle_t *h, cudaStream_t s);
+cudaError_t enqueue_iteration_timed(const gsr_handle_t *h, cudaStream_t s, const cudaEvent_t *ev);
 cudaError_t launch_precond_finish(const gsr_handle_t *h, double *p, cudaStream_t st);
+int lsqr_vec_grid(const gsr_handle_t *h);
 // gsr_noalloc.cu: scratch address of gsr_aprod1_norm_noalloc on device dev
 int noalloc_prepare(int dev);
 

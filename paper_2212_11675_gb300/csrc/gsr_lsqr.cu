@@ -222,6 +222,7 @@ k_vec(const SysView A, const double *__restrict__ p, double *__restrict__ q, dou
     const bool upd = bn > 0.0;
     const double k1 = ia * ib, k2 = -bn * ia;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
     for (int64_t j = gtid(); j < n; j += gstride()) {
         const double pj = p[j];
         double qj;
@@ -253,9 +254,10 @@ k_vec(const SysView A, const double *__restrict__ p, double *__restrict__ q, dou
         acc[0] = fma(vn, vn, acc[0]);
     }
     if (INL) {  // this block's fixed slice of the global-column partials
-        const int64_t per = (P.ngpart + gridDim.x - 1) / gridDim.x;
-        const int64_t b0 = blockIdx.x * per, b1 = min((int64_t)P.ngpart, b0 + per);
-        for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+        const uint32_t per = ((uint32_t)P.ngpart + gridDim.x - 1) / gridDim.x;
+        const uint32_t b0 = blockIdx.x * per;
+        const uint32_t b1 = min((uint32_t)P.ngpart, b0 + per);
+        for (uint32_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
             acc[3] += P.gpart[b];
     }
     if (grid_reduce<4>(acc, partial, counter)) {
@@ -280,6 +282,25 @@ k_vec(const SysView A, const double *__restrict__ p, double *__restrict__ q, dou
             lsqr_scalars(st, args, vn2, acc[1], acc[2], loop, in_graph);
         }
     }
+}
+
+// blocks of the LSQR vector pass: two per SM (measured on the medium
+// workload, in the solve: 32.9 us against 33.4 us with three and 37.2 us
+// with one; more blocks add per-block reductions), no more than the vector
+// needs
+int lsqr_vec_grid(const gsr_handle_t *h)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vec<true>, kThreads, 0) != cudaSuccess ||
+        occ < 1)
+        return -1;
+    if (occ > 2)
+        occ = 2;
+    int64_t g = (int64_t)h->nsm * occ;
+    const int64_t need = (h->sys.n + kThreads - 1) / kThreads;
+    if (g > need) g = need;
+    if (g > kMaxPartials) g = kMaxPartials;
+    return (int)(g < 1 ? 1 : g);
 }
 
 // x = p o z, se = p o sqrt(var) * rnorm / sqrt(dof)
@@ -354,7 +375,7 @@ cudaError_t find_graph_leaf(cudaGraph_t g, cudaGraphNode_t *leaf)
 // q = A^T U (overwrite) and the vector pass; with the single-launch aprod 2
 // the vector pass combines its partial sums itself
 static cudaError_t a2_and_vec(const gsr_handle_t *h, cudaStream_t s, cudaGraphConditionalHandle loop,
-                              int in_graph, int first)
+                              int in_graph, int first, cudaEvent_t mid = nullptr)
 {
     double *part = h->d_partial + kRedV * kPartialsPerKind;
     unsigned *cnt = h->d_counter + kRedV;
@@ -365,11 +386,18 @@ static cudaError_t a2_and_vec(const gsr_handle_t *h, cudaStream_t s, cudaGraphCo
         cudaError_t e = launch_aprod2(h, h->d_u, h->d_q, kA2Overwrite, s);
         if (e != cudaSuccess)
             return e;
-        k_vec<false><<<h->grid_vec, kThreads, 0, s>>>(h->sys, h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w,
+        if (mid && (e = cudaEventRecord(mid, s)) != cudaSuccess)
+            return e;
+        k_vec<false><<<h->grid_lsqr_vec, kThreads, 0, s>>>(h->sys, h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w,
                                                       h->d_z, h->d_var, h->d_state, h->d_args, part,
                                                       cnt, loop, in_graph, first, P);
     } else {
-        k_vec<true><<<h->grid_vec, kThreads, 0, s>>>(h->sys, h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w,
+        if (mid) {
+            cudaError_t e = cudaEventRecord(mid, s);
+            if (e != cudaSuccess)
+                return e;
+        }
+        k_vec<true><<<h->grid_lsqr_vec, kThreads, 0, s>>>(h->sys, h->d_p, h->d_q, h->d_v, h->d_vp, h->d_w,
                                                      h->d_z, h->d_var, h->d_state, h->d_args, part,
                                                      cnt, loop, in_graph, first, P);
     }
@@ -400,6 +428,21 @@ cudaError_t enqueue_iteration(const gsr_handle_t *h, cudaStream_t s,
     if (e != cudaSuccess)
         return e;
     return a2_and_vec(h, s, loop, in_graph, 0);
+}
+
+// One iteration launched from the host with events between its launches:
+// ev[0] before aprod 1, ev[1] after it, ev[2] after aprod 2, ev[3] after the
+// vector pass (ev[0] may be the previous iteration's ev[3]).
+cudaError_t enqueue_iteration_timed(const gsr_handle_t *h, cudaStream_t s, const cudaEvent_t *ev)
+{
+    cudaError_t e = launch_aprod1(h, h->d_vp, h->d_u, 1, s);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess)
+        e = a2_and_vec(h, s, 0, 0, 0, ev[2]);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(ev[3], s);
+    return e;
 }
 
 cudaError_t enqueue_epilogue(const gsr_handle_t *h, cudaStream_t s)

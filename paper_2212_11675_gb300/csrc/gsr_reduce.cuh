@@ -22,11 +22,51 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Four sums over the block by reduce-scatter: in each warp the first two
+// exchanges halve the set of values a lane carries (2 + 1 adds), the last
+// three add whole lanes (3 adds), so lane group g = lane / 8 ends with the
+// warp's total of value g; warp 0 then adds the per-warp totals the same way.
+// 9 FP64 adds per lane instead of 20 + 3 for four separate butterflies (FP64
+// adds are expensive on this part).  Fixed order: deterministic.
+__device__ __forceinline__ void block_sum4(double (&v)[4])
+{
+    constexpr int NW = kThreads / 32;
+    static_assert(NW == 8, "one lane per (value, warp) in warp 0");
+    __shared__ double sh[4][NW];
+    __shared__ double res[4];
+    const int lane = threadIdx.x & 31;
+    const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+    // xor 16: keep values {0,1} (lower half) or {2,3} (upper half)
+    double a0 = (up16 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, up16 ? v[0] : v[2], 16);
+    double a1 = (up16 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, up16 ? v[1] : v[3], 16);
+    // xor 8: keep one of the two
+    double t = (up8 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, up8 ? a0 : a1, 8);
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1)
+        t += __shfl_xor_sync(0xffffffffu, t, off);
+    if ((lane & 7) == 0)
+        sh[lane >> 3][threadIdx.x >> 5] = t;  // value lane / 8 of this warp
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double u = sh[lane >> 3][lane & 7];
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1)
+            u += __shfl_xor_sync(0xffffffffu, u, off);
+        if ((lane & 7) == 0)
+            res[lane >> 3] = u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        v[k] = res[k];
+    __syncthreads();
+}
+
 // Sum over the block; the result is valid in every thread.  Deterministic.
 // Warps reduce their lanes; only warp 0 then adds the per-warp partials (FP64
 // adds are expensive on this part, so no other thread repeats them).
 template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K])
+__device__ __forceinline__ void block_sum_generic(double (&v)[K])
 {
     constexpr int NW = kThreads / 32;
     __shared__ double sh[K][NW];
@@ -55,6 +95,15 @@ __device__ __forceinline__ void block_sum(double (&v)[K])
     for (int k = 0; k < K; k++)
         v[k] = res[k];
     __syncthreads();
+}
+
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K])
+{
+    if constexpr (K == 4)
+        block_sum4(v);
+    else
+        block_sum_generic<K>(v);
 }
 
 template <int K>

@@ -203,6 +203,16 @@ class Solver:
               "gsr_product_forms")
         return bool(a1.value), int(a2.value)
 
+    def time_iteration(self, b, iters=20, stream=None):
+        """Average durations (ms) of aprod 1, aprod 2 and the vector pass of an
+        LSQR iteration as they run inside a solve of b (CUDA events)."""
+        _check_vec(b, self.m, "b")
+        out = np.zeros(3)
+        check(lib().gsr_time_iteration(self._h, _ptr(b)[0], int(iters),
+                                       out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+              "gsr_time_iteration")
+        return {"aprod1": float(out[0]), "aprod2": float(out[1]), "vector_pass": float(out[2])}
+
     def set_batch_tiling(self, kt, lanes):
         """Column tile (1, 2, 4, 8) and lanes per star (8, 16, 32) of the batched kernels."""
         check(lib().gsr_set_batch_tiling(self._h, int(kt), int(lanes)), "gsr_set_batch_tiling")

@@ -317,3 +317,18 @@ def test_errors_are_reported_not_faulted():
         # the handle stays usable after a reported error
         x, _, res = s.lsqr_solve(torch.ones(sys.m, dtype=torch.float64, device=DEV), 5, 0.0, 0.0)
         assert res["itn"] == 5 and torch.isfinite(x).all().item()
+
+
+def test_time_iteration_leaves_solves_intact():
+    """gsr_time_iteration (the benchmark's in-solve kernel timing) returns
+    positive durations, and a solve after it is bit-identical to one before."""
+    sys = gen.make("tiny")
+    b = _rhs(sys, 3)
+    with _solver(sys) as s:
+        bd = torch.tensor(b, device=DEV)
+        x0 = s.lsqr_solve(bd, 30, 0.0, 0.0)[0].cpu().numpy()
+        t = s.time_iteration(bd, iters=5)
+        assert set(t) == {"aprod1", "aprod2", "vector_pass"}
+        assert all(v > 0.0 for v in t.values())
+        x1 = s.lsqr_solve(bd, 30, 0.0, 0.0)[0].cpu().numpy()
+    np.testing.assert_array_equal(x0, x1)
