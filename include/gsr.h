@@ -380,6 +380,17 @@ int gsr_fp64_fma_rate(double *fma_per_s);
  */
 int gsr_time_iteration(void *h, const double *b, int iters, double *ms3, void *stream);
 
+/*
+ * dst[0..n) += src[0..n) on the current device: the reduction step of the
+ * row-block sharded products (paper §4, Fig. 2: after aprod 2 every block of
+ * whole stars holds a partial sum of the 3 D + I + 1 replicated attitude,
+ * instrumental and global columns, summed over the blocks).  When several
+ * blocks share one GPU the partials are added block after block in a fixed
+ * order with this call.  Both pointers must be device (or managed) memory
+ * of the current device; n >= 0.  Errors: GSR_ERR_ARG, GSR_ERR_CUDA.
+ */
+int gsr_vector_add(double *dst, const double *src, int64_t n, void *stream);
+
 /* Text of the last CUDA failure seen by this host thread ("" if none). */
 const char *gsr_last_error(void);
 

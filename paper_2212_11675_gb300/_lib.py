@@ -33,7 +33,7 @@ EXPORTS = (
     "gsr_aprod1_norm_noalloc", "gsr_aprod1_f32", "gsr_aprod2_f32", "gsr_mixed_solve",
     "gsr_set_values", "gsr_normal_solve", "gsr_lsq_backward", "gsr_batched_solve",
     "gsr_batched_products", "gsr_set_batch_tiling", "gsr_set_aprod2_fused",
-    "gsr_product_forms", "gsr_fp64_fma_rate", "gsr_time_iteration",
+    "gsr_product_forms", "gsr_fp64_fma_rate", "gsr_time_iteration", "gsr_vector_add",
 )
 
 
@@ -128,6 +128,7 @@ def lib():
             L.gsr_product_forms.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
             L.gsr_fp64_fma_rate.argtypes = [ctypes.POINTER(D)]
             L.gsr_time_iteration.argtypes = [P, P, I, P, P]
+            L.gsr_vector_add.argtypes = [P, P, I64, P]
             L.gsr_last_error.restype = ctypes.c_char_p
             L.gsr_strerror.argtypes = [I]
             L.gsr_strerror.restype = ctypes.c_char_p
@@ -138,7 +139,7 @@ def lib():
                          "gsr_mixed_solve", "gsr_set_values", "gsr_normal_solve",
                          "gsr_lsq_backward", "gsr_batched_solve", "gsr_batched_products",
                          "gsr_set_batch_tiling", "gsr_set_aprod2_fused", "gsr_product_forms",
-                         "gsr_fp64_fma_rate", "gsr_time_iteration"):
+                         "gsr_fp64_fma_rate", "gsr_time_iteration", "gsr_vector_add"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib
