@@ -39,6 +39,33 @@ namespace gsr {
 
 constexpr int64_t kSmemInstrMax = 6144;  // instrument columns kept in shared memory (48 KB)
 
+// c += the Acc3 value that lane (lane ^ off) sends
+__device__ __forceinline__ void acc3_add_shfl(Acc3 &c, const Acc3 &send, int off)
+{
+    acc3_add(c, __shfl_xor_sync(0xffffffffu, send.h, off), __shfl_xor_sync(0xffffffffu, send.m, off),
+             __shfl_xor_sync(0xffffffffu, send.l, off));
+}
+
+// Exact reduce-scatter steps on the binary32 pipes for FP64 partial sums
+// (FP64 adds are the bottleneck of the row kernels on this part):
+// split_range_ok(d) tells whether d splits exactly (zero, or exponent in the
+// split window), acc3_pair(a, b) is a + b as a three-level accumulator.
+__device__ __forceinline__ bool split_range_ok(double d)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    return ((hi & 0x7fffffffu) | lo) == 0u || split3_range(hi) < kSplitRangeSpan;
+}
+
+__device__ __forceinline__ Acc3 acc3_pair(double a, double b)
+{
+    Acc3 c;
+    float h, m, l;
+    split3z(a, c.h, c.m, c.l);
+    split3z(b, h, m, l);
+    acc3_add(c, h, m, l);
+    return c;
+}
+
 __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
 {
     const uint32_t w = (j < 2) ? rc.y : ((j < 4) ? rc.z : rc.w);
@@ -100,7 +127,6 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t ntiles = (A.m + 31) >> 5;
     const double cy = (MODE == 1) ? st->cy : 1.0;
-    const int64_t mp = A.mp;
     double nrm = 0.0;
 
     for (int64_t t = warp; t < ntiles; t += nwarps) {
@@ -310,29 +336,65 @@ __device__ __forceinline__ double stars_body(const SysView &A, const double *__r
         if constexpr (G >= 8) {
             // reduce-scatter: the first three exchanges halve a padded set of
             // 8 sums (4 + 2 + 1 adds), the remaining ones add whole lanes;
-            // lane l then holds sum number kidx of the star
-            double r8[8] = {a0, a1, a2, a3, a4, 0.0, 0.0, 0.0};
+            // lane l then holds sum number kidx of the star.  The adds run on
+            // the binary32 pipes on exact three-piece splits (one binary64
+            // add at the end), in binary64 when a sum of the warp is outside
+            // the split window.
+            const bool in_range = split_range_ok(a0) && split_range_ok(a1) && split_range_ok(a2) &&
+                                  split_range_ok(a3) && split_range_ok(a4);
+            double tot;
+            if (__all_sync(0xffffffffu, in_range)) {
+                const double a[5] = {a0, a1, a2, a3, a4};
+                Acc3 r4[4];
+                const bool up = (lane & (G / 2)) != 0;
 #pragma unroll
-            for (int hw = 4, off = G / 2; hw >= 1; hw >>= 1, off >>= 1) {
-                const bool upper = (lane & off) != 0;
-#pragma unroll
-                for (int k = 0; k < hw; k++) {
-                    const double send = upper ? r8[k] : r8[k + hw];
-                    const double keep = upper ? r8[k + hw] : r8[k];
-                    r8[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                for (int k = 0; k < 4; k++) {  // sums k and k + 4 (zero beyond the 5th)
+                    const double p = a[k], q = (k == 0) ? a[4] : 0.0;
+                    const double recv = __shfl_xor_sync(0xffffffffu, up ? p : q, G / 2);
+                    r4[k] = acc3_pair(up ? q : p, recv);
                 }
-            }
 #pragma unroll
-            for (int off = G / 16; off > 0; off >>= 1)
-                r8[0] += __shfl_xor_sync(0xffffffffu, r8[0], off);
+                for (int hw = 2, off = G / 4; hw >= 1; hw >>= 1, off >>= 1) {
+                    const bool upper = (lane & off) != 0;
+#pragma unroll
+                    for (int k = 0; k < hw; k++) {
+                        const Acc3 send = upper ? r4[k] : r4[k + hw];
+                        Acc3 keep = upper ? r4[k + hw] : r4[k];
+                        acc3_add_shfl(keep, send, off);
+                        r4[k] = keep;
+                    }
+                }
+#pragma unroll
+                for (int off = G / 16; off > 0; off >>= 1) {
+                    const Acc3 send = r4[0];
+                    acc3_add_shfl(r4[0], send, off);
+                }
+                tot = acc3_to_double(r4[0]);
+            } else {
+                double r8[8] = {a0, a1, a2, a3, a4, 0.0, 0.0, 0.0};
+#pragma unroll
+                for (int hw = 4, off = G / 2; hw >= 1; hw >>= 1, off >>= 1) {
+                    const bool upper = (lane & off) != 0;
+#pragma unroll
+                    for (int k = 0; k < hw; k++) {
+                        const double send = upper ? r8[k] : r8[k + hw];
+                        const double keep = upper ? r8[k + hw] : r8[k];
+                        r8[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                    }
+                }
+#pragma unroll
+                for (int off = G / 16; off > 0; off >>= 1)
+                    r8[0] += __shfl_xor_sync(0xffffffffu, r8[0], off);
+                tot = r8[0];
+            }
             const int kidx = ((lane & (G / 2)) ? 4 : 0) | ((lane & (G / 4)) ? 2 : 0) |
                              ((lane & (G / 8)) ? 1 : 0);
             if (s < A.S && (lane & (G / 8 - 1)) == 0 && kidx < kNAstro) {
                 double *xs = out + kNAstro * s + kidx;
                 if (MODE == kA2Accumulate)
-                    *xs += r8[0];
+                    *xs += tot;
                 else
-                    *xs = r8[0];
+                    *xs = tot;
             }
         } else {
 #pragma unroll
@@ -354,30 +416,6 @@ __device__ __forceinline__ double stars_body(const SysView &A, const double *__r
         }
     }
     return gacc;
-}
-
-// c += the Acc3 value (h, m, l) of another lane: both exact levels by TwoSum,
-// the third rounded
-__device__ __forceinline__ void acc3_add(Acc3 &c, float h, float m, float l)
-{
-    float t, u1, u2;
-    c.h = two_sum(c.h, h, t);
-    c.m = two_sum(c.m, m, u1);
-    c.m = two_sum(c.m, t, u2);
-    c.l = __fadd_rn(__fadd_rn(c.l, l), __fadd_rn(u1, u2));
-}
-
-__device__ __forceinline__ void acc3_add_shfl(Acc3 &c, const Acc3 &send, int off)
-{
-    acc3_add(c, __shfl_xor_sync(0xffffffffu, send.h, off), __shfl_xor_sync(0xffffffffu, send.m, off),
-             __shfl_xor_sync(0xffffffffu, send.l, off));
-}
-
-__device__ __forceinline__ double acc3_to_double(const Acc3 &c)
-{
-    double d0, d1;
-    acc3_parts(c, d0, d1);
-    return d0 + d1;
 }
 
 // One instrument unit (entries e0 .. e1-1 of the instrument-sorted copy,
@@ -713,22 +751,58 @@ __device__ __forceinline__ void att_body(const SysView &A, const double *__restr
             }
         }
         // reduce-scatter over the warp: after the butterfly, lane pair
-        // (2k, 2k+1) holds the total of sum k (16 adds per lane, not 60)
-        double r16[16];
+        // (2k, 2k+1) holds the total of sum k (16 adds per lane, not 60).
+        // The adds run on the binary32 pipes on exact three-piece splits of
+        // the partial sums (one binary64 add at the end instead of 16), and
+        // in binary64 when a partial sum of the warp is outside the split
+        // window.
+        bool in_range = true;
 #pragma unroll
-        for (int k = 0; k < 16; k++)
-            r16[k] = k < kNAtt ? acc[k] : 0.0;
+        for (int k = 0; k < kNAtt; k++)
+            in_range &= split_range_ok(acc[k]);
+        double tot;
+        if (__all_sync(0xffffffffu, in_range)) {
+            // first exchange (xor 16) from the binary64 partials: sums k and
+            // k + 8 (zero beyond the 12th) become one three-level value
+            Acc3 r8[8];
+            const bool up16 = (lane & 16) != 0;
 #pragma unroll
-        for (int half = 8; half >= 1; half >>= 1) {
-            const bool upper = (lane & (2 * half)) != 0;  // keeps the upper half
-#pragma unroll
-            for (int k = 0; k < half; k++) {
-                const double send = upper ? r16[k] : r16[k + half];
-                const double keep = upper ? r16[k + half] : r16[k];
-                r16[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * half);
+            for (int k = 0; k < 8; k++) {
+                const double a = acc[k], b = (k + 8 < kNAtt) ? acc[k + 8] : 0.0;
+                const double recv = __shfl_xor_sync(0xffffffffu, up16 ? a : b, 16);
+                r8[k] = acc3_pair(up16 ? b : a, recv);
             }
+#pragma unroll
+            for (int half = 4; half >= 1; half >>= 1) {
+                const bool upper = (lane & (2 * half)) != 0;
+#pragma unroll
+                for (int k = 0; k < half; k++) {
+                    const Acc3 send = upper ? r8[k] : r8[k + half];
+                    Acc3 keep = upper ? r8[k + half] : r8[k];
+                    acc3_add_shfl(keep, send, 2 * half);
+                    r8[k] = keep;
+                }
+            }
+            const Acc3 send = r8[0];
+            acc3_add_shfl(r8[0], send, 1);
+            tot = acc3_to_double(r8[0]);
+        } else {
+            double r16[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++)
+                r16[k] = k < kNAtt ? acc[k] : 0.0;
+#pragma unroll
+            for (int half = 8; half >= 1; half >>= 1) {
+                const bool upper = (lane & (2 * half)) != 0;  // keeps the upper half
+#pragma unroll
+                for (int k = 0; k < half; k++) {
+                    const double send = upper ? r16[k] : r16[k + half];
+                    const double keep = upper ? r16[k + half] : r16[k];
+                    r16[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * half);
+                }
+            }
+            tot = r16[0] + __shfl_xor_sync(0xffffffffu, r16[0], 1);
         }
-        const double tot = r16[0] + __shfl_xor_sync(0xffffffffu, r16[0], 1);
         const int k_of_lane = lane >> 1;  // bits 4..1 of the lane pick the sum
         if ((lane & 1) == 0 && k_of_lane < kNAtt)
             S[o * kNAtt + k_of_lane] = tot;

@@ -119,6 +119,17 @@ __device__ __forceinline__ void acc3_fma(Acc3 &c, float a1, float a2, float a3, 
     c.l = __fadd_rn(c.l, __fadd_rn(__fadd_rn(q, u1), __fadd_rn(__fadd_rn(u2, u3), u4)));
 }
 
+// c += (h, m, l), another three-level value: both exact levels by TwoSum,
+// the third rounded
+__device__ __forceinline__ void acc3_add(Acc3 &c, float h, float m, float l)
+{
+    float t, u1, u2;
+    c.h = two_sum(c.h, h, t);
+    c.m = two_sum(c.m, m, u1);
+    c.m = two_sum(c.m, t, u2);
+    c.l = __fadd_rn(__fadd_rn(c.l, l), __fadd_rn(u1, u2));
+}
+
 // exact binary32 -> binary64 of a normal or zero binary32 by bit operations
 // (binary32 subnormals, below 2^-126 in magnitude, become signed zero)
 __device__ __forceinline__ double f2d_bits(float f)
@@ -139,6 +150,14 @@ __device__ __forceinline__ void acc3_parts(const Acc3 &c, double &d0, double &d1
 {
     d0 = f2d_bits(c.h);
     d1 = f2d_bits(c.m) + f2d_bits(c.l);
+}
+
+// the accumulated value in binary64 (two binary64 additions)
+__device__ __forceinline__ double acc3_to_double(const Acc3 &c)
+{
+    double d0, d1;
+    acc3_parts(c, d0, d1);
+    return d0 + d1;
 }
 
 }  // namespace gsr
