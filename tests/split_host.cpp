@@ -7,6 +7,8 @@
 // stdin, one request per line:
 //   S a               -> "h m l" pieces of split3(a), then split3_range ok (0/1)
 //   Z a               -> the same from split3z(a) (zero in range, zero pieces)
+//   R n a0 ... a{n-1} -> the values summed by acc3_add on their split3z
+//                        pieces: "ok sum" (acc3_to_double)
 //   A n a0 x0 ... -> n products accumulated with acc3_fma: "ok h m l d0 d1"
 // numbers in C hex-float notation.
 #include <cmath>
@@ -91,6 +93,23 @@ int main()
             float h, m, l;
             const uint32_t r = split3z(a, h, m, l);
             printf("%a %a %a %d\n", (double)h, (double)m, (double)l, r < kSplitRangeSpan ? 1 : 0);
+        } else if (op == 'R') {
+            // n binary64 values summed as the reduce-scatter of the row
+            // kernels does: split3z pieces added with acc3_add
+            int n;
+            if (scanf("%d", &n) != 1)
+                return 2;
+            Acc3 c = {0.f, 0.f, 0.f};
+            int ok = 1;
+            for (int i = 0; i < n; i++) {
+                double a;
+                if (scanf("%la", &a) != 1)
+                    return 2;
+                float h, m, l;
+                ok &= split3z(a, h, m, l) < kSplitRangeSpan;
+                acc3_add(c, h, m, l);
+            }
+            printf("%d %a\n", ok, acc3_to_double(c));
         } else if (op == 'A') {
             int n;
             if (scanf("%d", &n) != 1)

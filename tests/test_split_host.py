@@ -128,3 +128,29 @@ def test_split3z_takes_zero_and_agrees_with_split3(harness):
             assert float.fromhex(h) == float.fromhex(m) == float.fromhex(l) == 0.0 and ok == "1"
         else:
             assert z == s, v
+
+
+def test_reduction_of_split_partials_is_exact(harness):
+    """The binary32 reduce-scatter of the row kernels: FP64 partial sums split
+    by split3z and added with acc3_add come out within two binary64 roundings
+    of the exact sum plus 2^-60 of the sum of magnitudes, also when the
+    partials cancel to 2^-40 of their size (where binary64 adds lose far
+    more)."""
+    rng = random.Random(7)
+    lines, cases = [], []
+    for trial in range(300):
+        n = rng.choice([2, 5, 8, 12, 16, 32])
+        vals = [rng.gauss(0, 1) * 2.0 ** rng.randint(-20, 20) for _ in range(n)]
+        if trial % 3 == 0:  # cancel: the last partial undoes the others but a tiny rest
+            s = sum(Fraction(v) for v in vals[:-1])
+            vals[-1] = float(-s) + float(s) * 2.0 ** -40 * rng.choice([-1, 1])
+        cases.append(vals)
+        lines.append("R %d %s\n" % (n, " ".join(float(v).hex() for v in vals)))
+    out = harness(lines)
+    for vals, line in zip(cases, out):
+        ok, got = line.split()
+        assert ok == "1"
+        exact = sum(Fraction(v) for v in vals)
+        mag = sum(abs(v) for v in vals)
+        err = abs(Fraction(float.fromhex(got)) - exact)
+        assert err <= 2 * 2.0 ** -53 * abs(exact) + 2.0 ** -60 * Fraction(mag), vals
