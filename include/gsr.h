@@ -68,9 +68,9 @@ extern "C" {
  * three-piece binary32 splits of both operands, with error-free products and
  * sums, within 2^-60 of the sum of the magnitudes of the products it
  * accumulates (below the rounding of one FP64 FMA).  Operands whose exponent
- * is outside [-30, 30] (zero entries excepted) send their row (aprod 1),
- * block (aprod 1's x), star group or instrument unit (aprod 2) to native FP64
- * products.  gsr_product_forms() tells which forms a handle runs. */
+ * is outside [-30, 30] (zero entries excepted) send the rows that use them
+ * (aprod 1), or their star group or instrument unit (aprod 2), to native
+ * FP64 products.  gsr_product_forms() tells which forms a handle runs. */
 #define GSR_PRODUCTS_AUTO 0   /* library choice: aprod 1's split form where it
                                  applies (I <= 3072); native products
                                  otherwise and in aprod 2 */

@@ -83,8 +83,9 @@ __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
 // three-piece splits of both operands (gsr_split.cuh: FP64-accurate, error
 // below 2^-60 of the sum of their magnitudes), which takes 6 of the 27
 // FP64-pipe operations of a row off the pipe that bounds this kernel; x is
-// staged as pieces, and a row (or a block, for x) with an operand outside
-// the split range takes the FP64 products instead.
+// staged as pieces, and a row with an operand outside the split range (a
+// value, an instrumental x it uses, or the global x) takes the FP64
+// products instead.
 // ---------------------------------------------------------------------------
 template <int MODE, bool SMEMX, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, SPLIT ? 3 : 5)  // measured best: 3 split, 5 native
@@ -96,27 +97,21 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
     float4 *s_x4 = reinterpret_cast<float4 *>(s_xi);
     const double xg = __ldg(x + A.glb0);
     float g1 = 0.f, g2 = 0.f, g3 = 0.f;
-    bool split_x = false;  // block-uniform: every split operand of x is in range
+    bool split_x = false;  // the global x splits (the same for every row)
     if (SPLIT) {
-        int bad = 0;
+        // the pieces of every instrumental x, and in the fourth float a flag
+        // for an entry outside the split range: a row that uses it takes
+        // native products (only those rows: a block-wide decision sent every
+        // row of the block to the FP64 pipe whenever one of the I entries of
+        // p o v was below 2^-30, which happened in a sizeable share of the
+        // LSQR iterations)
         for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x) {
-            const double xv = x[A.ins0 + f];
-            const uint32_t hi = (uint32_t)__double2hiint(xv), lo = (uint32_t)__double2loint(xv);
             float p1, p2, p3;
-            split3(hi, lo, p1, p2, p3);
-            if (((hi & 0x7fffffffu) | lo) == 0u)
-                p1 = p2 = p3 = 0.f;  // zero splits exactly
-            else if (split3_range(hi) >= kSplitRangeSpan)
-                bad = 1;
-            s_x4[f] = make_float4(p1, p2, p3, 0.f);
+            const bool ok = split3z(x[A.ins0 + f], p1, p2, p3) < kSplitRangeSpan;
+            s_x4[f] = make_float4(p1, p2, p3, ok ? 0.f : 1.f);
         }
-        const uint32_t ghi = (uint32_t)__double2hiint(xg), glo = (uint32_t)__double2loint(xg);
-        split3(ghi, glo, g1, g2, g3);
-        if (((ghi & 0x7fffffffu) | glo) == 0u)
-            g1 = g2 = g3 = 0.f;
-        else if (split3_range(ghi) >= kSplitRangeSpan)
-            bad = 1;
-        split_x = __syncthreads_or(bad) == 0;
+        split_x = split3z(xg, g1, g2, g3) < kSplitRangeSpan;
+        __syncthreads();
     } else if (SMEMX) {
         for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x)
             s_xi[f] = x[A.ins0 + f];
@@ -150,6 +145,7 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
                     // pipes; their sum h + (m + l) starts the FP64 chains
                     Acc3 c = {0.f, 0.f, 0.f};
                     uint32_t rng = 0;
+                    float flag = 0.f;  // > 0: an instrumental x of the row out of range
 #pragma unroll
                     for (int j = 0; j <= kNInstr; j++) {
                         const double a = vk[17 + j];
@@ -160,12 +156,13 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
                         split3(hi, lo, a1, a2, a3);
                         if (j < kNInstr) {
                             const float4 xp = s_x4[instr_at(rc, j)];
+                            flag += xp.w;
                             acc3_fma(c, a1, a2, a3, xp.x, xp.y, xp.z);
                         } else {
                             acc3_fma(c, a1, a2, a3, g1, g2, g3);
                         }
                     }
-                    if (rng < kSplitRangeSpan) {
+                    if (rng < kSplitRangeSpan && flag == 0.f) {
                         acc3_parts(c, s0, s1);
                         native = false;
                     }

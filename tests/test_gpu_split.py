@@ -114,15 +114,23 @@ def test_split_out_of_range_operands_fall_back():
     y0 = rng.standard_normal(sys.m)
     ins0 = 5 * sys.n_stars + 3 * sys.n_dfa
     x[ins0 + 2] = 0.0  # a zero instrumental x is split exactly
+    uses5 = (sys.instr == 5).any(axis=1)
+    assert uses5.any() and not uses5.all()
+    g0 = None
     for case in range(3):
         xc = x.copy()
         if case == 1:
-            xc[ins0 + 5] = 1e-14  # instrumental x out of range: native for every row
+            xc[ins0 + 5] = 1e-14  # instrumental x out of range: native for the rows using it
         if case == 2:
-            xc[-1] = 1e15         # global x out of range
+            xc[-1] = 1e15         # global x out of range: native for every row
         ex, mag = _exact(sys, xc, y0)
         g = _aprod1(sys, xc, y0, _lib.GSR_PRODUCTS_SPLIT)
         assert np.all(_err(g, ex) <= 27 * U * mag), case
+        if case == 0:
+            g0 = g
+        if case == 1:
+            # the other rows keep their split products: identical to case 0
+            np.testing.assert_array_equal(g[~uses5], g0[~uses5])
 
 
 def test_split_matches_native_on_a_generated_system():
