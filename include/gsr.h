@@ -48,8 +48,9 @@ extern "C" {
 #define GSR_ERR_INDEX (-2)       /* structure out of range (star_ptr, attoff, instr) */
 #define GSR_ERR_OOM (-3)         /* device or host allocation failed */
 #define GSR_ERR_CUDA (-4)        /* a CUDA runtime call failed */
-/* (-5) is unused: no entry point waits on the device with a time limit (the
- * solve loops are conditional CUDA graph nodes, not spin-waits) */
+#define GSR_ERR_TIMEOUT (-5)     /* a bounded device wait expired (the staged aprod 1
+                                    waited over a second for a bulk copy of a tile;
+                                    the results of that call are undefined) */
 #define GSR_ERR_NONFINITE (-6)   /* NaN or Inf in the input or in the recurrences */
 #define GSR_ERR_UNSUPPORTED (-7) /* configuration not supported by this build */
 
@@ -185,7 +186,8 @@ int gsr_precondition(void *h, double *p, void *stream);
  * The whole iteration runs on the device (one CUDA graph, no host
  * synchronisation until the end).  `out` receives the stopping estimates.
  * Errors: GSR_ERR_ARG, GSR_ERR_NONFINITE (a NaN/Inf in b or in the scalar
- * recurrences; x and se are then undefined), GSR_ERR_CUDA.
+ * recurrences; x and se are then undefined), GSR_ERR_TIMEOUT (a bounded wait
+ * of the staged aprod 1 expired; x and se are undefined), GSR_ERR_CUDA.
  */
 int gsr_lsqr_solve(void *h, const double *b, int itmax, double atol,
                    double btol, double *x, double *se, gsr_result *out,
@@ -356,6 +358,49 @@ int gsr_set_batch_tiling(void *h, int kt, int lanes);
  * instrumental path), GSR_ERR_CUDA.
  */
 int gsr_set_aprod2_fused(void *h, int fused);
+
+/*
+ * Form of the FP64 aprod 1 (Alg. 1; every y += A x of the handle: the
+ * entry point, the LSQR iteration, the FP64 steps of the mixed solve).
+ * staged = 0: every warp loads its rows' values, index records and star
+ * deltas from device memory into registers (the register form).  staged = 1
+ * (the default wherever it applies): one block of 18 warps per SM; each warp
+ * has the bulk-copy (TMA) engine stage its next 32-row tile (the 24 value
+ * planes, the records, the star deltas and, when y is read and 16-byte
+ * aligned, the tile's y) into a 7,040-byte stage in shared memory, one tile
+ * ahead of the tile it computes.  Both forms use the same
+ * per-row arithmetic (the split instrumental and global products), so their
+ * results are bitwise equal.  Available when the split products apply (I up
+ * to the split limit) and the stages fit the block's opt-in shared memory;
+ * GSR_ERR_UNSUPPORTED otherwise.  Every wait on a copy is bounded (one
+ * second); an expired wait sets a device flag that the solve entry points
+ * (gsr_lsqr_solve, gsr_mixed_solve, gsr_normal_solve, gsr_lsq_backward,
+ * gsr_batched_solve) and gsr_kernel_status report as GSR_ERR_TIMEOUT (and
+ * clear).  The handle's solve graphs
+ * are captured again.  gsr_aprod1_staging reads the current form.
+ * Errors: GSR_ERR_ARG, GSR_ERR_UNSUPPORTED, GSR_ERR_CUDA.
+ */
+int gsr_set_aprod1_staging(void *h, int staged);
+int gsr_aprod1_staging(void *h, int *staged);
+
+/*
+ * Synchronises stream and reports whether a bounded device wait of a kernel
+ * on this handle expired since the last check: GSR_ERR_TIMEOUT (the flag is
+ * cleared) or GSR_OK.  Errors: GSR_ERR_ARG, GSR_ERR_CUDA.
+ */
+int gsr_kernel_status(void *h, void *stream);
+
+/*
+ * Test hook for the bounded waits of the staged aprod 1: tile >= 0 makes
+ * every later launch on the handle announce tile's bulk copies to its
+ * barrier without issuing them, so the wait of the warp that owns the tile
+ * expires after one second (the tile's rows and the rest of that warp's
+ * rows are not computed; the launch still ends and the flag read by
+ * gsr_kernel_status is set).  No memory access is made out of bounds and no
+ * kernel is left waiting.  tile = -1 turns the hook off.  The solve graphs
+ * are captured again.  Errors: GSR_ERR_ARG, GSR_ERR_CUDA.
+ */
+int gsr_inject_missing_copy(void *h, int64_t tile);
 
 /*
  * Measured FP64 fused multiply-add throughput of the current device, in FMAs

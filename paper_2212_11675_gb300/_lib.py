@@ -17,6 +17,7 @@ GSR_ERR_ARG = -1
 GSR_ERR_INDEX = -2
 GSR_ERR_OOM = -3
 GSR_ERR_CUDA = -4
+GSR_ERR_TIMEOUT = -5
 GSR_ERR_NONFINITE = -6
 GSR_ERR_UNSUPPORTED = -7
 
@@ -34,6 +35,8 @@ EXPORTS = (
     "gsr_set_values", "gsr_normal_solve", "gsr_lsq_backward", "gsr_batched_solve",
     "gsr_batched_products", "gsr_set_batch_tiling", "gsr_set_aprod2_fused",
     "gsr_product_forms", "gsr_fp64_fma_rate", "gsr_time_iteration", "gsr_vector_add",
+    "gsr_set_aprod1_staging", "gsr_aprod1_staging", "gsr_kernel_status",
+    "gsr_inject_missing_copy",
 )
 
 
@@ -129,6 +132,10 @@ def lib():
             L.gsr_fp64_fma_rate.argtypes = [ctypes.POINTER(D)]
             L.gsr_time_iteration.argtypes = [P, P, I, P, P]
             L.gsr_vector_add.argtypes = [P, P, I64, P]
+            L.gsr_set_aprod1_staging.argtypes = [P, I]
+            L.gsr_aprod1_staging.argtypes = [P, ctypes.POINTER(I)]
+            L.gsr_kernel_status.argtypes = [P, P]
+            L.gsr_inject_missing_copy.argtypes = [P, I64]
             L.gsr_last_error.restype = ctypes.c_char_p
             L.gsr_strerror.argtypes = [I]
             L.gsr_strerror.restype = ctypes.c_char_p
@@ -139,7 +146,9 @@ def lib():
                          "gsr_mixed_solve", "gsr_set_values", "gsr_normal_solve",
                          "gsr_lsq_backward", "gsr_batched_solve", "gsr_batched_products",
                          "gsr_set_batch_tiling", "gsr_set_aprod2_fused", "gsr_product_forms",
-                         "gsr_fp64_fma_rate", "gsr_time_iteration", "gsr_vector_add"):
+                         "gsr_fp64_fma_rate", "gsr_time_iteration", "gsr_vector_add",
+                         "gsr_set_aprod1_staging", "gsr_aprod1_staging", "gsr_kernel_status",
+                         "gsr_inject_missing_copy"):
                 getattr(L, name).restype = I
             _lib = L
     return _lib

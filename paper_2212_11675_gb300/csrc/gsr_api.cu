@@ -53,6 +53,7 @@ extern "C" const char *gsr_strerror(int code)
     case GSR_ERR_CUDA: return "CUDA runtime error";
     case GSR_ERR_NONFINITE: return "non-finite value";
     case GSR_ERR_UNSUPPORTED: return "unsupported configuration";
+    case GSR_ERR_TIMEOUT: return "a bounded device wait expired";
     default: return "unknown error";
     }
 }
@@ -320,10 +321,12 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     const int64_t ntiles = (m + 31) / 32;
 
     TRY(dalloc(h, &h->d_star_ptr, S + 1));
-    TRY(dalloc(h, &h->d_rec, m));
+    // records and star deltas padded to whole 32-row tiles (zero), so a tile
+    // can be staged by one bulk copy
+    TRY(dalloc(h, &h->d_rec, mp));
     TRY(dalloc(h, &h->d_val, kNPar * mp));
     TRY(dalloc(h, &h->d_tile_star, ntiles));
-    TRY(dalloc(h, &h->d_sdelta, m));
+    TRY(dalloc(h, &h->d_sdelta, mp));
     TRY(dalloc(h, &h->d_sorder, S));
     TRY(dalloc(h, &h->d_tval, (int64_t)kNAtt * mp));
     TRY(dalloc(h, &h->d_perm, m));
@@ -342,8 +345,12 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     TRY(dalloc(h, &h->d_partial, (int64_t)kRedCount * kPartialsPerKind));
     TRY(dalloc(h, &h->d_counter, kRedCount));
     TRY(dalloc(h, &h->d_err, 1));
+    TRY(dalloc(h, &h->d_kerr, 1));
     CK(cudaMemset(h->d_counter, 0, kRedCount * sizeof(unsigned)));
     CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    CK(cudaMemset(h->d_kerr, 0, sizeof(int)));
+    CK(cudaMemset(h->d_rec, 0, (size_t)mp * sizeof(uint4)));
+    CK(cudaMemset(h->d_sdelta, 0, (size_t)mp * sizeof(uint16_t)));
     CK(cudaMemset(h->d_val, 0, (size_t)kNPar * mp * sizeof(double)));
     CK(cudaMallocHost((void **)&h->h_state, sizeof(SolveState)));
     CK(cudaMallocHost((void **)&h->h_args, sizeof(SolveArgs)));
@@ -473,6 +480,10 @@ static int create_impl(gsr_handle_t *h, const gsr_dims *d, const uint32_t *star_
     // measured at the medium size: 8 lanes per star with shared-memory
     // instrument sums or the sorted pass, 32 with replicas
     h->lanes = h->cfg.lanes_per_star ? h->cfg.lanes_per_star : (h->ipath == kIpReplicas ? 32 : 8);
+    // aprod 1 staged by the bulk-copy engine wherever it applies (measured
+    // faster in the solve on the medium workload: 0.305 against 0.328 ms)
+    CK(aprod1_tma_prepare(h));
+    h->a1_tma = h->a1_tma_avail;
     h->grid_rows = aprod1_grid(h);
     if (h->grid_rows <= 0)
         return cuda_fail(cudaGetLastError(), "aprod1 occupancy");
@@ -636,6 +647,30 @@ static int stage(gsr_handle_t *h, double **slot, int64_t count, const double *us
     return GSR_OK;
 }
 
+// GSR_ERR_TIMEOUT when a bounded wait of a kernel on this handle expired
+// since the last check (the flag is then cleared); synchronizes the stream
+static int take_kernel_status(gsr_handle_t *h, cudaStream_t st)
+{
+    int kerr = 0;
+    CK(cudaMemcpyAsync(&kerr, h->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (kerr == 0)
+        return GSR_OK;
+    CK(cudaMemsetAsync(h->d_kerr, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    snprintf(g_last_error, sizeof g_last_error, "%s",
+             "a bounded wait of the staged aprod 1 expired: a bulk copy did not complete");
+    return GSR_ERR_TIMEOUT;
+}
+
+extern "C" int gsr_kernel_status(void *hv, void *stream)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h)
+        return GSR_ERR_ARG;
+    return take_kernel_status(h, (cudaStream_t)stream);
+}
+
 extern "C" int gsr_aprod1(void *hv, const double *x, double *y, void *stream)
 {
     gsr_handle_t *h = (gsr_handle_t *)hv;
@@ -730,6 +765,7 @@ extern "C" int gsr_lsqr_solve(void *hv, const double *b, int itmax, double atol,
     if (se && dse != se)
         CK(cudaMemcpyAsync(se, dse, h->sys.n * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    TRY(take_kernel_status(h, st));
     const SolveState &s = *h->h_state;
     if (out) {
         out->istop = s.istop;
@@ -892,6 +928,7 @@ extern "C" int gsr_mixed_solve(void *hv, const double *b, int max_outer, int max
     }
     CK(cudaMemcpyAsync(x, h->d_xm, A.n * sizeof(double), cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
+    TRY(take_kernel_status(h, st));
     if (out)
         *out = res;
     return GSR_OK;
@@ -960,6 +997,7 @@ extern "C" int gsr_normal_solve(void *hv, const double *g, int max_iter, double 
     TRY(normal_solve_dev(h, dg, max_iter, tol, out, st));
     CK(cudaMemcpyAsync(q, h->d_xm, h->sys.n * sizeof(double), cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
+    TRY(take_kernel_status(h, st));
     return GSR_OK;
 }
 
@@ -1002,6 +1040,7 @@ extern "C" int gsr_lsq_backward(void *hv, const double *b, const double *x, cons
     if (dgb != grad_b)
         CK(cudaMemcpyAsync(grad_b, dgb, A.m * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    TRY(take_kernel_status(h, st));
     return GSR_OK;
 }
 
@@ -1101,6 +1140,71 @@ extern "C" int gsr_set_aprod2_fused(void *hv, int fused)
     if (e != cudaSuccess)
         return cuda_fail(e, "gsr_set_aprod2_fused");
     return GSR_OK;
+}
+
+// the captured graphs hold the old launches: capture them again
+static int recapture_graphs(gsr_handle_t *h, const char *what)
+{
+    if (h->solve_exec) {
+        cudaGraphExecDestroy(h->solve_exec);
+        h->solve_exec = nullptr;
+    }
+    if (h->cg64_exec) {
+        cudaGraphExecDestroy(h->cg64_exec);
+        h->cg64_exec = nullptr;
+    }
+    const bool mixed = h->cg_exec != nullptr;
+    if (h->cg_exec) {
+        cudaGraphExecDestroy(h->cg_exec);
+        h->cg_exec = nullptr;
+    }
+    cudaError_t e = build_solve_graph(h);
+    if (e == cudaSuccess)
+        e = build_cg64_graph(h);
+    if (e == cudaSuccess && mixed)
+        e = build_cg_graph(h);
+    if (e != cudaSuccess)
+        return cuda_fail(e, what);
+    return GSR_OK;
+}
+
+extern "C" int gsr_set_aprod1_staging(void *hv, int staged)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || (staged != 0 && staged != 1))
+        return GSR_ERR_ARG;
+    if (staged && !h->a1_tma_avail)
+        return GSR_ERR_UNSUPPORTED;
+    if (h->a1_tma == staged)
+        return GSR_OK;
+    const int old_tma = h->a1_tma, old_grid = h->grid_rows;
+    h->a1_tma = staged;
+    const int g = aprod1_grid(h);
+    if (g <= 0 || g > kMaxPartials) {
+        h->a1_tma = old_tma;
+        h->grid_rows = old_grid;
+        return cuda_fail(cudaGetLastError(), "gsr_set_aprod1_staging");
+    }
+    h->grid_rows = g;
+    return recapture_graphs(h, "gsr_set_aprod1_staging");
+}
+
+extern "C" int gsr_aprod1_staging(void *hv, int *staged)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || !staged)
+        return GSR_ERR_ARG;
+    *staged = h->a1_tma;
+    return GSR_OK;
+}
+
+extern "C" int gsr_inject_missing_copy(void *hv, int64_t tile)
+{
+    gsr_handle_t *h = (gsr_handle_t *)hv;
+    if (!h || tile < -1)
+        return GSR_ERR_ARG;
+    h->drop_tile = tile;
+    return recapture_graphs(h, "gsr_inject_missing_copy");
 }
 
 extern "C" int gsr_set_batch_tiling(void *hv, int kt, int lanes)
@@ -1236,6 +1340,7 @@ extern "C" int gsr_batched_solve(void *hv, int k, const double *B, int max_outer
     }
     CK(cudaMemcpyAsync(X, h->d_bXcm, A.n * k * sizeof(double), cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
+    TRY(take_kernel_status(h, st));
     if (out)
         for (int c = 0; c < k; c++)
             out[c] = res[c];

@@ -272,6 +272,11 @@ struct gsr_handle_t {
     cudaStream_t cap_stream = nullptr;
     int grid_rows = 0, grid_rows2 = 0, grid_vec = 0, grid_att = 0, grid_ins = 0;
     int grid_lsqr_vec = 0;              // the LSQR vector pass: every resident block
+    // aprod 1 with its tiles staged by the bulk-copy engine (k_aprod1_tma)
+    int a1_tma = 0;                     // 1: the staged form runs
+    int a1_tma_avail = 0;               // 1: the staged form applies on this device
+    int *d_kerr = nullptr;              // set by a kernel whose bounded wait expired
+    int64_t drop_tile = -1;             // test hook: the tile whose bulk copy is not issued
 };
 
 namespace gsr {
@@ -307,6 +312,9 @@ cudaError_t launch_pack_rec(const gsr_handle_t *h, const uint32_t *attoff,
 cudaError_t launch_tile_star(const gsr_handle_t *h, cudaStream_t st);
 cudaError_t launch_gather_att(const gsr_handle_t *h, cudaStream_t st);
 int aprod1_grid(const gsr_handle_t *h);
+// the staged aprod 1 for this handle: its shared memory (0: does not apply)
+size_t aprod1_tma_smem(const gsr_handle_t *h);
+cudaError_t aprod1_tma_prepare(gsr_handle_t *h);
 bool aprod1_split(const gsr_handle_t *h);
 int split_request(const gsr_config &cfg);
 int aprod2_split(const gsr_handle_t *h);

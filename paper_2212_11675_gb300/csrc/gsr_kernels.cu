@@ -72,6 +72,117 @@ __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
     return (j & 1) ? (w >> 16) : (w & 0xffffu);
 }
 
+// A x of one row (vk: its 24 values, rc: its record, s: its star): two
+// independent partial sums (astrometric + global + instrumental, attitude)
+// keep the FP64 pipe fed with one merge (four sums were 4% slower: two more
+// FP64 adds per row).  SPLIT: the instrumental and global products on the
+// binary32 pipes (x pieces s_x4 in shared memory, global pieces g1..g3).
+template <bool SMEMX, bool SPLIT>
+__device__ __forceinline__ double row_sum(const SysView &A, const double *__restrict__ x,
+                                          const double (&vk)[kNPar], const uint4 &rc, uint32_t s,
+                                          const float4 *s_x4, const double *s_xi, bool split_x,
+                                          double xg, float g1, float g2, float g3)
+{
+    double s0, s1;
+    if constexpr (SPLIT) {
+        bool native = true;
+        if (split_x) {
+            // instrumental and global products on the binary32
+            // pipes; their sum h + (m + l) starts the FP64 chains
+            Acc3 c = {0.f, 0.f, 0.f};
+            uint32_t rng = 0;
+            float flag = 0.f;  // > 0: an instrumental x of the row out of range
+#pragma unroll
+            for (int j = 0; j <= kNInstr; j++) {
+                const double a = vk[17 + j];
+                const uint32_t hi = (uint32_t)__double2hiint(a);
+                const uint32_t lo = (uint32_t)__double2loint(a);
+                rng = max(rng, split3_range(hi));
+                float a1, a2, a3;
+                split3(hi, lo, a1, a2, a3);
+                if (j < kNInstr) {
+                    const float4 xp = s_x4[instr_at(rc, j)];
+                    flag += xp.w;
+                    acc3_fma(c, a1, a2, a3, xp.x, xp.y, xp.z);
+                } else {
+                    acc3_fma(c, a1, a2, a3, g1, g2, g3);
+                }
+            }
+            if (rng < kSplitRangeSpan && flag == 0.f) {
+                acc3_parts(c, s0, s1);
+                native = false;
+            }
+        }
+        if (native) {  // an operand outside the split range
+            s0 = vk[23] * xg;
+#pragma unroll
+            for (int j = 0; j < kNInstr; j++)
+                s0 = fma(vk[17 + j], __ldg(x + A.ins0 + instr_at(rc, j)), s0);
+            s1 = 0.0;
+        }
+        const double *xs = x + (int64_t)kNAstro * s;
+#pragma unroll
+        for (int k = 0; k < kNAstro; k++)
+            s0 = fma(vk[k], __ldg(xs + k), s0);
+        const double *xa = x + A.att0 + rc.x;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                s1 = fma(vk[5 + 4 * a + j], __ldg(xa + a * A.D + j), s1);
+    } else {
+        const double *xs = x + (int64_t)kNAstro * s;
+        s0 = vk[0] * __ldg(xs);
+#pragma unroll
+        for (int k = 1; k < kNAstro; k++)
+            s0 = fma(vk[k], __ldg(xs + k), s0);
+        const double *xa = x + A.att0 + rc.x;
+        s1 = vk[5] * __ldg(xa);
+#pragma unroll
+        for (int j = 1; j < 4; j++)
+            s1 = fma(vk[5 + j], __ldg(xa + j), s1);
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            s1 = fma(vk[9 + j], __ldg(xa + A.D + j), s1);
+        s0 = fma(vk[23], xg, s0);
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            s1 = fma(vk[13 + j], __ldg(xa + 2 * A.D + j), s1);
+#pragma unroll
+        for (int j = 0; j < kNInstr; j++) {
+            const uint32_t f = instr_at(rc, j);
+            s0 = fma(vk[17 + j], SMEMX ? s_xi[f] : __ldg(x + A.ins0 + f), s0);
+        }
+    }
+    return s0 + s1;
+}
+
+// Last block of the LSQR form of aprod 1, with unorm2 = ||U_{i+1}||^2:
+// beta_{i+1} = ||U_{i+1}|| / alpha_i and the rotation that eliminates it; the
+// two independent square roots and reciprocals run in two warps
+__device__ __forceinline__ void lsqr_beta_rotation(SolveState *st, double unorm2)
+{
+    __shared__ double sq[2];
+    const double rhobar = st->rhobar;
+    const double ia = st->ia;
+    if (threadIdx.x == 0) {
+        const double un = sqrt(unorm2);
+        st->beta_new = un;
+        const double beta = un * ia;
+        sq[0] = beta;
+        st->bnext = beta;
+        st->ib = (beta > 0.0) ? 1.0 / beta : 0.0;
+    }
+    if (threadIdx.x == 32) {
+        const double irho = 1.0 / sqrt(rhobar * rhobar + unorm2 * ia * ia);
+        sq[1] = irho;
+        st->irho = irho;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        st->t1 = rhobar * sq[1] * st->phibar * sq[1];
+}
+
 // ---------------------------------------------------------------------------
 // aprod 1, row-parallel.  MODE 0: y += A x.  MODE 1 (LSQR): y = A x + cy y
 // with cy from the solve state, ||y|| into state->beta_new and, for the
@@ -134,81 +245,8 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
 #pragma unroll
             for (int k = 0; k < kNPar; k++)
                 vk[k] = __ldcs(v + 32 * k);
-            // two independent partial sums (astrometric + global +
-            // instrumental, attitude) keep the FP64 pipe fed with one merge
-            // (four sums were 4% slower: two more FP64 adds per row)
-            double s0, s1;
-            if constexpr (SPLIT) {
-                bool native = true;
-                if (split_x) {
-                    // instrumental and global products on the binary32
-                    // pipes; their sum h + (m + l) starts the FP64 chains
-                    Acc3 c = {0.f, 0.f, 0.f};
-                    uint32_t rng = 0;
-                    float flag = 0.f;  // > 0: an instrumental x of the row out of range
-#pragma unroll
-                    for (int j = 0; j <= kNInstr; j++) {
-                        const double a = vk[17 + j];
-                        const uint32_t hi = (uint32_t)__double2hiint(a);
-                        const uint32_t lo = (uint32_t)__double2loint(a);
-                        rng = max(rng, split3_range(hi));
-                        float a1, a2, a3;
-                        split3(hi, lo, a1, a2, a3);
-                        if (j < kNInstr) {
-                            const float4 xp = s_x4[instr_at(rc, j)];
-                            flag += xp.w;
-                            acc3_fma(c, a1, a2, a3, xp.x, xp.y, xp.z);
-                        } else {
-                            acc3_fma(c, a1, a2, a3, g1, g2, g3);
-                        }
-                    }
-                    if (rng < kSplitRangeSpan && flag == 0.f) {
-                        acc3_parts(c, s0, s1);
-                        native = false;
-                    }
-                }
-                if (native) {  // an operand outside the split range
-                    s0 = vk[23] * xg;
-#pragma unroll
-                    for (int j = 0; j < kNInstr; j++)
-                        s0 = fma(vk[17 + j], __ldg(x + A.ins0 + instr_at(rc, j)), s0);
-                    s1 = 0.0;
-                }
-                const double *xs = x + (int64_t)kNAstro * s;
-#pragma unroll
-                for (int k = 0; k < kNAstro; k++)
-                    s0 = fma(vk[k], __ldg(xs + k), s0);
-                const double *xa = x + A.att0 + rc.x;
-#pragma unroll
-                for (int a = 0; a < 3; a++)
-#pragma unroll
-                    for (int j = 0; j < 4; j++)
-                        s1 = fma(vk[5 + 4 * a + j], __ldg(xa + a * A.D + j), s1);
-            } else {
-                const double *xs = x + (int64_t)kNAstro * s;
-                s0 = vk[0] * __ldg(xs);
-#pragma unroll
-                for (int k = 1; k < kNAstro; k++)
-                    s0 = fma(vk[k], __ldg(xs + k), s0);
-                const double *xa = x + A.att0 + rc.x;
-                s1 = vk[5] * __ldg(xa);
-#pragma unroll
-                for (int j = 1; j < 4; j++)
-                    s1 = fma(vk[5 + j], __ldg(xa + j), s1);
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    s1 = fma(vk[9 + j], __ldg(xa + A.D + j), s1);
-                s0 = fma(vk[23], xg, s0);
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    s1 = fma(vk[13 + j], __ldg(xa + 2 * A.D + j), s1);
-#pragma unroll
-                for (int j = 0; j < kNInstr; j++) {
-                    const uint32_t f = instr_at(rc, j);
-                    s0 = fma(vk[17 + j], SMEMX ? s_xi[f] : __ldg(x + A.ins0 + f), s0);
-                }
-            }
-            const double sum = s0 + s1;
+            const double sum = row_sum<SMEMX, SPLIT>(A, x, vk, rc, s, s_x4, s_xi, split_x, xg, g1,
+                                                     g2, g3);
             double yn;
             if (MODE == 1) {
                 yn = fma(cy, y[r], sum);
@@ -231,30 +269,234 @@ k_aprod1(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveS
     }
     if (MODE == 1) {
         double v1[1] = {nrm};
-        if (grid_reduce<1>(v1, partial, counter)) {
-            // beta_{i+1} = ||U_{i+1}|| / alpha_i and the rotation that
-            // eliminates it; the two independent square roots and
-            // reciprocals run in two warps
-            __shared__ double sq[2];
-            const double rhobar = st->rhobar;
-            const double ia = st->ia;
-            if (threadIdx.x == 0) {
-                const double un = sqrt(v1[0]);
-                st->beta_new = un;
-                const double beta = un * ia;
-                sq[0] = beta;
-                st->bnext = beta;
-                st->ib = (beta > 0.0) ? 1.0 / beta : 0.0;
+        if (grid_reduce<1>(v1, partial, counter))
+            lsqr_beta_rotation(st, v1[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// aprod 1 with its tiles staged by the bulk-copy (TMA) engine.  In the tiled
+// layout the 24 value planes of a 32-row tile are one contiguous 6 KB block,
+// its 32 index records 512 B, its star deltas 64 B and its y 256 B: one lane
+// of a warp stages them with four cp.async.bulk copies that complete on an
+// mbarrier.  A warp reads its stage into registers, hands the stage back to
+// the copy engine for its next tile, and then computes, so its x gathers
+// (which need the records) and its y update start as soon as a tile begins
+// and no load of the row stream is in flight in its registers.  One block of
+// kTmaWarps warps per SM (the largest count whose stages, x pieces and
+// registers fit); the rows use the same arithmetic as k_aprod1 (row_sum), so
+// y is bitwise equal to the register form's.  The ring of stages per warp is
+// written for kTmaStages stages.
+// Every wait on an mbarrier is bounded (one second of %globaltimer): when it
+// expires the warp sets *kerr, waits (bounded again) for its other copies in
+// flight, stops staging and still joins the grid reduction, so the launch
+// ends and the host reports GSR_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kTileValBytes = 32 * kNPar * sizeof(double);     // 6144
+constexpr uint32_t kTileRecBytes = 32 * sizeof(uint4);              // 512
+constexpr uint32_t kTileDeltaBytes = 32 * sizeof(uint16_t);         // 64
+constexpr uint32_t kTileBytes = kTileValBytes + kTileRecBytes + kTileDeltaBytes;
+constexpr uint32_t kTileYBytes = 32 * sizeof(double);               // 256
+constexpr uint32_t kStageBytes = (kTileBytes + kTileYBytes + 127) / 128 * 128;  // 7040
+constexpr uint64_t kWaitNs = 1000000000ull;                         // 1 s
+
+// block shape of the staged form, measured on the medium workload (in-solve
+// aprod 1, ms): 18 warps with one stage each and y staged 0.305; 20 warps
+// 0.308; 16 warps 0.321; 22 warps (80 registers, spills) 0.339; 12 warps
+// with two stages and no y 0.373; 24 warps with one stage and no y 0.399;
+// the register form 0.328.  More stages per warp cost warps (shared memory),
+// and one tile ahead already covers the copy latency: a warp spends about
+// 5 us on a tile.
+constexpr int kTmaWarps = 18;
+constexpr int kTmaThreads = 32 * kTmaWarps;
+constexpr int kTmaStages = 1;
+
+constexpr size_t tma_smem_bytes(int64_t I)
+{
+    return ((size_t)I * sizeof(float4) + 127) / 128 * 128 +
+           (size_t)kTmaWarps * kTmaStages * (kStageBytes + sizeof(uint64_t));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// true when the mbarrier at bar completed the phase with this parity within
+// kWaitNs
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t done = 0;
+    uint64_t t0 = 0;
+    for (int it = 0; !done; it++) {
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+                     "selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done)
+            break;
+        if (it == 0)
+            t0 = global_ns();
+        else if (global_ns() - t0 > kWaitNs)
+            return false;
+    }
+    return true;
+}
+
+// lane 0 of the warp: stage tile t (values, records, star deltas) into the
+// stage at sbase, completing on the mbarrier bar.  drop: a test hook, the
+// tile whose copies are announced to the barrier but never issued (its wait
+// then expires); -1 in every other launch.
+__device__ __forceinline__ void tma_stage_tile(const SysView &A, int64_t t, uint32_t sbase,
+                                               uint32_t bar, int64_t drop, const double *ys)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(kTileBytes + (ys ? kTileYBytes : 0u)) : "memory");
+    if (t == drop)
+        return;
+    if (ys)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(sbase + kTileBytes), "l"(ys + t * 32), "r"(kTileYBytes), "r"(bar)
+                     : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(sbase), "l"(A.val + t * 32 * kNPar), "r"(kTileValBytes), "r"(bar) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(sbase + kTileValBytes), "l"(A.rec + t * 32), "r"(kTileRecBytes), "r"(bar)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(sbase + kTileValBytes + kTileRecBytes), "l"(A.sdelta + t * 32),
+                 "r"(kTileDeltaBytes), "r"(bar) : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+k_aprod1_tma(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveState *st,
+             double *partial, unsigned *counter, CgState *cg, int *kerr, int64_t drop)
+{
+    constexpr int NW = kTmaWarps, NS = kTmaStages;
+    // y staged with its tile: a whole tile of a 16-byte aligned y that the
+    // launch reads (the ragged last tile loads its y directly)
+    const bool ys_ok = MODE != 2 && ((uintptr_t)y & 15u) == 0;
+    const int64_t full_tiles = A.m >> 5;
+    extern __shared__ __align__(128) unsigned char smem[];
+    // [x pieces: I float4, rounded to 128 B][NW x NS stages][NW x NS mbarriers]
+    float4 *s_x4 = reinterpret_cast<float4 *>(smem);
+    const uint32_t xbytes = ((uint32_t)A.I * 16u + 127u) / 128u * 128u;
+    unsigned char *stages = smem + xbytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stages + NW * NS * kStageBytes);
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const double xg = __ldg(x + A.glb0);
+    float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+    for (int64_t f = threadIdx.x; f < A.I; f += blockDim.x) {
+        float p1, p2, p3;
+        const bool ok = split3z(x[A.ins0 + f], p1, p2, p3) < kSplitRangeSpan;
+        s_x4[f] = make_float4(p1, p2, p3, ok ? 0.f : 1.f);
+    }
+    const bool split_x = split3z(xg, g1, g2, g3) < kSplitRangeSpan;
+    // stage j of this warp at sb0 + j kStageBytes, its barrier at bar0 + 8 j
+    const uint32_t bar0 = smem_addr(bars + NS * wib);
+    unsigned char *my = stages + (size_t)wib * NS * kStageBytes;
+    const uint32_t sb0 = smem_addr(my);
+    if (lane == 0) {
+        for (int j = 0; j < NS; j++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * j) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();  // x pieces and barriers ready
+
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t ntiles = (A.m + 31) >> 5;
+    const double cy = (MODE == 1) ? st->cy : 1.0;
+    double nrm = 0.0;
+
+    if (lane == 0)
+        for (int j = 0; j < NS; j++)
+            if (warp + j * nwarps < ntiles)
+                tma_stage_tile(A, warp + j * nwarps, sb0 + j * kStageBytes, bar0 + 8 * j, drop,
+                               (ys_ok && warp + j * nwarps < full_tiles) ? y : nullptr);
+    uint32_t phase = 0;  // bit j: parity of the phase stage j completes next
+    int s = 0;
+    for (int64_t t = warp; t < ntiles; t += nwarps, s = (s + 1 == NS) ? 0 : s + 1) {
+        const uint32_t bar = bar0 + 8 * s;
+        // every lane waits (the wait makes the copy's bytes visible to it);
+        // the verdict is made warp-uniform, so no lane goes on alone
+        if (!__all_sync(0xffffffffu, mbar_wait(bar, (phase >> s) & 1u))) {
+            // the copy did not arrive: report, let this warp's other copies
+            // in flight land before the block may exit, stop
+            if (lane == 0)
+                atomicExch(kerr, 1);
+            for (int j = 1; j < NS; j++) {
+                const int sj = (s + j) % NS;
+                if (t + j * nwarps < ntiles)
+                    mbar_wait(bar0 + 8 * sj, (phase >> sj) & 1u);
             }
-            if (threadIdx.x == 32) {
-                const double irho = 1.0 / sqrt(rhobar * rhobar + v1[0] * ia * ia);
-                sq[1] = irho;
-                st->irho = irho;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0)
-                st->t1 = rhobar * sq[1] * st->phibar * sq[1];
+            break;
         }
+        phase ^= 1u << s;
+        const unsigned char *sp = my + (size_t)s * kStageBytes;
+        const double *sval = reinterpret_cast<const double *>(sp);
+        const uint4 *srec = reinterpret_cast<const uint4 *>(sp + kTileValBytes);
+        const uint16_t *sdel = reinterpret_cast<const uint16_t *>(sp + kTileValBytes + kTileRecBytes);
+        const int64_t r = (t << 5) + lane;
+        double vk[kNPar];
+#pragma unroll
+        for (int k = 0; k < kNPar; k++)
+            vk[k] = sval[32 * k + lane];
+        const uint4 rc = srec[lane];
+        const uint16_t d = sdel[lane];
+        double yo = 0.0;  // y of the row, when staged
+        const bool yst = ys_ok && t < full_tiles;
+        if (yst)
+            yo = reinterpret_cast<const double *>(sp + kTileBytes)[lane];
+        __syncwarp();
+        // every lane has its row: the stage can take the tile NS steps ahead
+        // while this one is computed (the proxy fence orders the warp's reads
+        // of the stage before the copy engine's writes)
+        if (lane == 0 && t + NS * nwarps < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_stage_tile(A, t + NS * nwarps, sb0 + s * kStageBytes, bar, drop,
+                           (ys_ok && t + NS * nwarps < full_tiles) ? y : nullptr);
+        }
+        if (r < A.m) {
+            uint32_t st_ = __ldg(A.tile_star + t) + d;
+            if (d == 0xffffu)
+                while ((int64_t)A.star_ptr[st_ + 1] <= r)
+                    ++st_;
+            const double sum = row_sum<true, true>(A, x, vk, rc, st_, s_x4, nullptr, split_x, xg,
+                                                   g1, g2, g3);
+            double yn;
+            if (MODE == 1) {
+                yn = fma(cy, yst ? yo : y[r], sum);
+                nrm = fma(yn, yn, nrm);
+            } else if (MODE == 2) {
+                yn = sum;
+                nrm = fma(yn, yn, nrm);
+            } else {
+                yn = (yst ? yo : y[r]) + sum;
+            }
+            y[r] = yn;
+        }
+    }
+    if (MODE == 2) {
+        double v1[1] = {nrm};
+        if (grid_reduce<1, 32 * NW>(v1, partial, counter) && threadIdx.x == 0) {
+            cg->xi = v1[0];
+            cg->alpha = (v1[0] > 0.0) ? cg->gamma / v1[0] : 0.0;
+        }
+    }
+    if (MODE == 1) {
+        double v1[1] = {nrm};
+        if (grid_reduce<1, 32 * NW>(v1, partial, counter))
+            lsqr_beta_rotation(st, v1[0]);
     }
 }
 
@@ -996,13 +1238,47 @@ bool aprod1_split(const gsr_handle_t *h)
     return (split_request(h->cfg) & GSR_SPLIT_APROD1) && h->sys.I <= kSplitInstrMax;
 }
 
+// the staged form of aprod 1: its shared memory, 0 when the split products
+// do not apply
+size_t aprod1_tma_smem(const gsr_handle_t *h)
+{
+    return aprod1_split(h) ? tma_smem_bytes(h->sys.I) : 0;
+}
+
+// the staged form needs the split products and its stages in the opt-in
+// shared memory of a block: h->a1_tma_avail when both hold
+cudaError_t aprod1_tma_prepare(gsr_handle_t *h)
+{
+    h->a1_tma_avail = 0;
+    const size_t need = aprod1_tma_smem(h);
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                           h->device);
+    if (e != cudaSuccess || need == 0 || need > (size_t)optin)
+        return e;
+    e = cudaFuncSetAttribute(k_aprod1_tma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)need);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_aprod1_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)need);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_aprod1_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)need);
+    if (e == cudaSuccess)
+        h->a1_tma_avail = 1;
+    return e;
+}
+
 template <int MODE>
 static cudaError_t a1_launch(const gsr_handle_t *h, const double *x, double *y,
                              SolveState *st_slot, double *partial, unsigned *counter,
                              cudaStream_t st, CgState *cg = nullptr)
 {
     const bool smem = h->sys.I <= kSmemInstrMax;
-    if (aprod1_split(h))
+    if (h->a1_tma)
+        k_aprod1_tma<MODE><<<h->grid_rows, kTmaThreads, aprod1_tma_smem(h), st>>>(
+            h->sys, x, y, st_slot, partial, counter, cg, h->d_kerr, h->drop_tile);
+    else if (aprod1_split(h))
         k_aprod1<MODE, true, true><<<h->grid_rows, kThreads, (size_t)h->sys.I * sizeof(float4),
                                      st>>>(h->sys, x, y, st_slot, partial, counter, cg);
     else if (smem)
@@ -1487,7 +1763,10 @@ int aprod1_grid(const gsr_handle_t *h)
     const bool smem = h->sys.I <= kSmemInstrMax;
     int occ = 0;
     cudaError_t e;
-    if (aprod1_split(h))
+    if (h->a1_tma)  // one block per SM
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1_tma<1>, kTmaThreads,
+                                                          aprod1_tma_smem(h));
+    else if (aprod1_split(h))
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1<1, true, true>, kThreads,
                                                           (size_t)h->sys.I * sizeof(float4));
     else if (smem)

@@ -65,10 +65,12 @@ __device__ __forceinline__ void block_sum4(double (&v)[4])
 // Sum over the block; the result is valid in every thread.  Deterministic.
 // Warps reduce their lanes; only warp 0 then adds the per-warp partials (FP64
 // adds are expensive on this part, so no other thread repeats them).
-template <int K>
+template <int K, int NT = kThreads>
 __device__ __forceinline__ void block_sum_generic(double (&v)[K])
 {
-    constexpr int NW = kThreads / 32;
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
+    constexpr int NW = NT / 32;
+    constexpr int P = NW <= 1 ? 1 : NW <= 2 ? 2 : NW <= 4 ? 4 : NW <= 8 ? 8 : NW <= 16 ? 16 : 32;
     __shared__ double sh[K][NW];
     __shared__ double res[K];
     const int lane = threadIdx.x & 31;
@@ -84,7 +86,7 @@ __device__ __forceinline__ void block_sum_generic(double (&v)[K])
         for (int k = 0; k < K; k++) {
             double t = (lane < NW) ? sh[k][lane] : 0.0;
 #pragma unroll
-            for (int off = NW / 2; off > 0; off >>= 1)
+            for (int off = P / 2; off > 0; off >>= 1)
                 t += __shfl_xor_sync(0xffffffffu, t, off);
             if (lane == 0)
                 res[k] = t;
@@ -97,20 +99,21 @@ __device__ __forceinline__ void block_sum_generic(double (&v)[K])
     __syncthreads();
 }
 
-template <int K>
+// NT: the block size the kernel is launched with
+template <int K, int NT = kThreads>
 __device__ __forceinline__ void block_sum(double (&v)[K])
 {
-    if constexpr (K == 4)
+    if constexpr (K == 4 && NT == kThreads)
         block_sum4(v);
     else
-        block_sum_generic<K>(v);
+        block_sum_generic<K, NT>(v);
 }
 
-template <int K>
+template <int K, int NT = kThreads>
 __device__ bool grid_reduce(double (&v)[K], double *partial, unsigned *counter)
 {
     __shared__ bool am_last;
-    block_sum<K>(v);
+    block_sum<K, NT>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < K; k++)
@@ -130,7 +133,7 @@ __device__ bool grid_reduce(double (&v)[K], double *partial, unsigned *counter)
             t += __ldcg(partial + k * kMaxPartials + b);
         v[k] = t;
     }
-    block_sum<K>(v);
+    block_sum<K, NT>(v);
     if (threadIdx.x == 0)
         *counter = 0u;
     return true;

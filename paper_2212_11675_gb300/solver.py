@@ -194,6 +194,26 @@ class Solver:
         queue (True, the default) or as separate passes (False)."""
         check(lib().gsr_set_aprod2_fused(self._h, 1 if fused else 0), "gsr_set_aprod2_fused")
 
+    def set_aprod1_staging(self, staged):
+        """FP64 aprod 1 with its tiles staged in shared memory by the bulk-copy
+        engine (True) or loaded into registers (False); bitwise-equal results."""
+        check(lib().gsr_set_aprod1_staging(self._h, 1 if staged else 0),
+              "gsr_set_aprod1_staging")
+
+    def aprod1_staging(self):
+        v = ctypes.c_int()
+        check(lib().gsr_aprod1_staging(self._h, ctypes.byref(v)), "gsr_aprod1_staging")
+        return bool(v.value)
+
+    def kernel_status(self, stream=None):
+        """Raw status of the bounded device waits since the last check
+        (GSR_OK or GSR_ERR_TIMEOUT; the flag is cleared)."""
+        return lib().gsr_kernel_status(self._h, _stream(stream))
+
+    def inject_missing_copy(self, tile):
+        """Test hook: tile's bulk copies are never issued (-1: off)."""
+        check(lib().gsr_inject_missing_copy(self._h, int(tile)), "gsr_inject_missing_copy")
+
     def product_forms(self):
         """(aprod1_split, aprod2_split): which FP64 products run on the binary32
         pipes from exact splits: aprod1_split a bool, aprod2_split a set of bits
