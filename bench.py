@@ -630,10 +630,12 @@ def main():
     bytes_vec = 11 * 8 * n
     # FLOPs on the FP64 pipe: one FMA per nonzero, less the products formed on
     # the binary32 pipes from exact splits (7 per row in aprod 1; in aprod 2,
-    # 6 per row in the star units, 6 in the instrument units)
+    # 6 per row in the star units, 6 in the instrument units, 4 or 8 in the
+    # attitude units)
     split1, split2 = solver.product_forms()
     flops_a1 = 2 * (24 - (7 if split1 else 0)) * m
-    flops_a2 = 2 * (24 - (6 if split2 & 1 else 0) - (6 if split2 & 2 else 0)) * m
+    flops_a2 = 2 * (24 - (6 if split2 & 1 else 0) - (6 if split2 & 2 else 0)
+                    - (4 if split2 & 4 else 0) - (8 if split2 & 8 else 0)) * m
     gbs_a1, gbs_a2 = bytes_a1 / t_a1 / 1e9, bytes_a2 / t_a2 / 1e9
     tf_a1, tf_a2 = flops_a1 / t_a1 / 1e12, flops_a2 / t_a2 / 1e12
     dom = "aprod2" if t_a2 >= t_a1 else "aprod1"

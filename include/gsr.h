@@ -88,6 +88,16 @@ extern "C" {
                                      star units */
 #define GSR_SPLIT_APROD2_INSTR 4  /* aprod 2's single-launch pass: the products
                                      of its instrument units */
+#define GSR_SPLIT_APROD2_ATT 8    /* aprod 2's single-launch pass: in its
+                                     attitude units, the 4 products of axis 2
+                                     (the other 8 stay native) */
+#define GSR_SPLIT_APROD2_ATT2 16  /* as GSR_SPLIT_APROD2_ATT for axes 1 and 2
+                                     (8 of the 12 products).  The attitude
+                                     bits exclude each other and
+                                     GSR_SPLIT_APROD2_STARS, and ATT2 excludes
+                                     GSR_SPLIT_APROD2_INSTR (no kernel
+                                     combines them: GSR_ERR_UNSUPPORTED at
+                                     creation; both attitude bits: GSR_ERR_ARG) */
 
 /* Storage and arithmetic of the matrix values. */
 #define GSR_PREC_FP64 0  /* IEEE double values, native FP64 arithmetic */
@@ -272,8 +282,10 @@ int gsr_mixed_solve(void *h, const double *b, int max_outer, int max_inner,
  * splits: *aprod1_split_on = 1 when aprod 1 forms its instrumental and
  * global products that way (0: native FP64); *aprod2_split_on is a set of
  * bits for aprod 2's single-launch pass: 1 its star units' astrometric and
- * global products, 2 its instrument units' products (0: native FP64
- * everywhere).  Host only, no CUDA call.  Errors: GSR_ERR_ARG.
+ * global products, 2 its instrument units' products, 4 the axis-2 products
+ * of its attitude units, 8 the axis-1 and axis-2 products of its attitude
+ * units (0: native FP64 everywhere).  Host only, no CUDA call.  Errors:
+ * GSR_ERR_ARG.
  */
 int gsr_product_forms(void *h, int *aprod1_split_on, int *aprod2_split_on);
 

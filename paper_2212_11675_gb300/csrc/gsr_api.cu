@@ -584,8 +584,17 @@ extern "C" int gsr_create(void **out, const gsr_dims *d, const uint32_t *star_pt
     if (c.instr_mode == GSR_INSTR_SMEM && d->n_instr > 6144)
         return GSR_ERR_UNSUPPORTED;
     if ((c.products < GSR_PRODUCTS_AUTO || c.products > GSR_PRODUCTS_SPLIT) &&
-        (c.products & ~7) != GSR_PRODUCTS_MASK)
+        (c.products & ~31) != GSR_PRODUCTS_MASK)
         return GSR_ERR_ARG;
+    if ((c.products & ~31) == GSR_PRODUCTS_MASK) {
+        const int r = c.products & 31;
+        if ((r & GSR_SPLIT_APROD2_ATT) && (r & GSR_SPLIT_APROD2_ATT2))
+            return GSR_ERR_ARG;
+        if ((r & (GSR_SPLIT_APROD2_ATT | GSR_SPLIT_APROD2_ATT2)) && (r & GSR_SPLIT_APROD2_STARS))
+            return GSR_ERR_UNSUPPORTED;  // no kernel combines these forms
+        if ((r & GSR_SPLIT_APROD2_ATT2) && (r & GSR_SPLIT_APROD2_INSTR))
+            return GSR_ERR_UNSUPPORTED;
+    }
     // an explicit request for aprod 1's split form needs the split
     // instrumental x in shared memory
     if (c.products != GSR_PRODUCTS_AUTO && (split_request(c) & GSR_SPLIT_APROD1) &&

@@ -118,10 +118,9 @@ struct SolveState {
     // on this part, so no other thread recomputes them)
     double bnext;              // beta_{i+1} = ||U_{i+1}|| / alpha_i
     double ib;                 // 1/beta_{i+1} (0 if beta_{i+1} = 0)
-    double t1;                 // phi/rho of the pending rotation
+    double t1;                 // phi of the pending rotation
     double irho;               // 1/rho of the pending rotation
     double ia;                 // 1/alpha (1 if alpha = 0)
-    double t2;                 // -theta/rho for the w update
     int itn, istop, done, nonfinite;
 };
 

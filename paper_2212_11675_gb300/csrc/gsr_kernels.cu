@@ -48,12 +48,13 @@ __device__ __forceinline__ void acc3_add_shfl(Acc3 &c, const Acc3 &send, int off
 
 // Exact reduce-scatter steps on the binary32 pipes for FP64 partial sums
 // (FP64 adds are the bottleneck of the row kernels on this part):
-// split_range_ok(d) tells whether d splits exactly (zero, or exponent in the
-// split window), acc3_pair(a, b) is a + b as a three-level accumulator.
-__device__ __forceinline__ bool split_range_ok(double d)
+// split_sum_ok(d) tells whether a partial sum d splits exactly for addition
+// (zero, or exponent in the reduction window [kSumEMin, kSumEMax]),
+// acc3_pair(a, b) is a + b as a three-level accumulator.
+__device__ __forceinline__ bool split_sum_ok(double d)
 {
     const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
-    return ((hi & 0x7fffffffu) | lo) == 0u || split3_range(hi) < kSplitRangeSpan;
+    return ((hi & 0x7fffffffu) | lo) == 0u || split3_sum_range(hi) < kSumRangeSpan;
 }
 
 __device__ __forceinline__ Acc3 acc3_pair(double a, double b)
@@ -64,6 +65,45 @@ __device__ __forceinline__ Acc3 acc3_pair(double a, double b)
     split3z(b, h, m, l);
     acc3_add(c, h, m, l);
     return c;
+}
+
+// Warp sum of the K binary64 values of every lane, valid in every lane: on
+// the binary32 pipes from exact three-piece splits (two binary64 adds at the
+// end) when every value of the warp is in the reduction window, else by binary64
+// adds ((v0 + v1) + (v2 + v3) per lane, then a butterfly).
+template <int K>
+__device__ __forceinline__ double warp_sum_split(const double (&v)[K])
+{
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        ok &= split_sum_ok(v[k]);
+    if (__all_sync(0xffffffffu, ok)) {
+        Acc3 c;
+        split3z(v[0], c.h, c.m, c.l);
+#pragma unroll
+        for (int k = 1; k < K; k++) {
+            float h, m, l;
+            split3z(v[k], h, m, l);
+            acc3_add(c, h, m, l);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const Acc3 send = c;
+            acc3_add_shfl(c, send, off);
+        }
+        return acc3_to_double(c);
+    }
+    double t;
+    if constexpr (K == 4)
+        t = (v[0] + v[1]) + (v[2] + v[3]);
+    else {
+        t = v[0];
+#pragma unroll
+        for (int k = 1; k < K; k++)
+            t += v[k];
+    }
+    return warp_sum(t);
 }
 
 __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
@@ -180,7 +220,7 @@ __device__ __forceinline__ void lsqr_beta_rotation(SolveState *st, double unorm2
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        st->t1 = rhobar * sq[1] * st->phibar * sq[1];
+        st->t1 = rhobar * sq[1] * st->phibar;  // phi = c phibar, c = rhobar / rho
 }
 
 // ---------------------------------------------------------------------------
@@ -518,7 +558,6 @@ __device__ __forceinline__ double stars_body(const SysView &A, const double *__r
     constexpr int GPW = 32 / G;
     const int lane = threadIdx.x & (G - 1);
     const int gw = (threadIdx.x & 31) / G;
-    const int64_t mp = A.mp;
     double gacc = 0.0;
     for (int64_t s0 = warp * GPW; s0 < A.S; s0 += nwarps * GPW) {
         // the GPW stars of a warp have similar row counts (stars taken in
@@ -578,9 +617,9 @@ __device__ __forceinline__ double stars_body(const SysView &A, const double *__r
             // lane l then holds sum number kidx of the star.  The adds run on
             // the binary32 pipes on exact three-piece splits (one binary64
             // add at the end), in binary64 when a sum of the warp is outside
-            // the split window.
-            const bool in_range = split_range_ok(a0) && split_range_ok(a1) && split_range_ok(a2) &&
-                                  split_range_ok(a3) && split_range_ok(a4);
+            // the reduction window.
+            const bool in_range = split_sum_ok(a0) && split_sum_ok(a1) && split_sum_ok(a2) &&
+                                  split_sum_ok(a3) && split_sum_ok(a4);
             double tot;
             if (__all_sync(0xffffffffu, in_range)) {
                 const double a[5] = {a0, a1, a2, a3, a4};
@@ -729,7 +768,6 @@ __device__ __forceinline__ double stars_body_split(const SysView &A, const doubl
     constexpr int GPW = 32 / G;
     const int lane = threadIdx.x & (G - 1);
     const int gw = (threadIdx.x & 31) / G;
-    const int64_t mp = A.mp;
     double gacc = 0.0;
     for (int64_t s0 = warp * GPW; s0 < A.S; s0 += nwarps * GPW) {
         const int64_t s = (s0 + gw < A.S) ? (int64_t)A.sorder[s0 + gw] : A.S;
@@ -925,7 +963,7 @@ __device__ __forceinline__ void instr_body(const SysView &A, const uint32_t *__r
             const double v = __ldcs(ival + e);
             acc[u & 3] = fma(v, SQ ? v : __ldg(y + __ldcs(irow + e)), acc[u & 3]);
         }
-        const double t = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        const double t = warp_sum_split<4>(acc);
         if (lane == 0)
             part[(size_t)q * I + f] = t;
     }
@@ -972,7 +1010,6 @@ __device__ __forceinline__ void att_body(const SysView &A, const double *__restr
                                          double *__restrict__ S, int64_t warp, int64_t nwarps)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t mp = A.mp;
     for (int64_t o = warp; o < A.nseg; o += nwarps) {
         const uint32_t e0 = A.seg[o], e1 = A.seg[o + 1];
         double acc[kNAtt];
@@ -993,12 +1030,12 @@ __device__ __forceinline__ void att_body(const SysView &A, const double *__restr
         // (2k, 2k+1) holds the total of sum k (16 adds per lane, not 60).
         // The adds run on the binary32 pipes on exact three-piece splits of
         // the partial sums (one binary64 add at the end instead of 16), and
-        // in binary64 when a partial sum of the warp is outside the split
-        // window.
+        // in binary64 when a partial sum of the warp is outside the
+        // reduction window.
         bool in_range = true;
 #pragma unroll
         for (int k = 0; k < kNAtt; k++)
-            in_range &= split_range_ok(acc[k]);
+            in_range &= split_sum_ok(acc[k]);
         double tot;
         if (__all_sync(0xffffffffu, in_range)) {
             // first exchange (xor 16) from the binary64 partials: sums k and
@@ -1048,6 +1085,104 @@ __device__ __forceinline__ void att_body(const SysView &A, const double *__restr
     }
 }
 
+// Partial sum j (0..11) of an attitude unit as an exact three-level value:
+// a native binary64 partial (j < NN, split exactly: in range by the caller's
+// check) or a three-level accumulator of the split taps (j >= NN).
+template <int NN, int NAS>
+__device__ __forceinline__ Acc3 att_part(const double (&acc)[NN], const Acc3 (&c)[NAS], int j)
+{
+    Acc3 r;
+    if (j < NN)
+        split3z(acc[j < NN ? j : 0], r.h, r.m, r.l);
+    else
+        r = c[j >= NN ? j - NN : 0];
+    return r;
+}
+
+// One attitude unit (offset o) with the products of its last NAS taps on the
+// binary32 pipes (NAS = 4: axis 2; NAS = 8: axes 1 and 2): y and those
+// values are split exactly into three binary32 pieces (gsr_split.cuh) and
+// accumulated on three levels, within about 2^-60 of the sum of the
+// |products|; the other taps keep FP64 FMAs.  The 12 sums are reduced over
+// the warp on exact three-level values in the reduce-scatter order of
+// att_body (lane pair (2k, 2k+1) ends with sum k; one binary64 add at the
+// end).  Returns false, with nothing written, when an operand is outside the
+// split range (zeros excepted) or a native partial sum outside the
+// reduction window: the caller then sums the unit with native products.
+template <int NAS>
+__device__ __forceinline__ bool att_unit_split(const SysView &A, const double *__restrict__ y,
+                                               double *__restrict__ S, int64_t o)
+{
+    constexpr int NN = kNAtt - NAS;
+    static_assert(NAS > 0 && NAS <= 8, "the split taps pair with native ones at xor 16");
+    const int lane = threadIdx.x & 31;
+    const uint32_t e0 = A.seg[o], e1 = A.seg[o + 1];
+    double acc[NN];
+    Acc3 c[NAS];
+#pragma unroll
+    for (int k = 0; k < NN; k++)
+        acc[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < NAS; k++)
+        c[k] = Acc3{0.f, 0.f, 0.f};
+    uint32_t rng = 0;
+    for (uint32_t e = e0 + lane; e < e1; e += 32) {
+        const double yi = __ldg(y + __ldcs(A.perm + e));
+        double v[kNAtt];
+#pragma unroll
+        for (int k = 0; k < kNAtt; k++)
+            v[k] = __ldcs(A.tval + tidx<kNAtt>(k, e));
+#pragma unroll
+        for (int k = 0; k < NN; k++)
+            acc[k] = fma(v[k], yi, acc[k]);
+        float y1, y2, y3;
+        rng = max(rng, split3z(yi, y1, y2, y3));
+#pragma unroll
+        for (int k = 0; k < NAS; k++) {
+            float a1, a2, a3;
+            rng = max(rng, split3z(v[NN + k], a1, a2, a3));
+            acc3_fma(c[k], a1, a2, a3, y1, y2, y3);
+        }
+    }
+    bool ok = rng < kSplitRangeSpan;
+#pragma unroll
+    for (int k = 0; k < NN; k++)
+        ok &= split_sum_ok(acc[k]);
+    if (!__all_sync(0xffffffffu, ok))
+        return false;
+    // xor 16: the lower half keeps sum k, the upper half sum k + 8 (zero
+    // beyond the 12th), for k = 0..7
+    Acc3 r8[8];
+    const bool up16 = (lane & 16) != 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const Acc3 a = att_part<NN, NAS>(acc, c, k);
+        const Acc3 b = (k + 8 < kNAtt) ? att_part<NN, NAS>(acc, c, k + 8) : Acc3{0.f, 0.f, 0.f};
+        Acc3 keep = up16 ? b : a;
+        const Acc3 send = up16 ? a : b;
+        acc3_add_shfl(keep, send, 16);
+        r8[k] = keep;
+    }
+#pragma unroll
+    for (int half = 4; half >= 1; half >>= 1) {
+        const bool upper = (lane & (2 * half)) != 0;
+#pragma unroll
+        for (int k = 0; k < half; k++) {
+            const Acc3 send = upper ? r8[k] : r8[k + half];
+            Acc3 keep = upper ? r8[k + half] : r8[k];
+            acc3_add_shfl(keep, send, 2 * half);
+            r8[k] = keep;
+        }
+    }
+    const Acc3 send = r8[0];
+    acc3_add_shfl(r8[0], send, 1);
+    const double tot = acc3_to_double(r8[0]);
+    const int k_of_lane = lane >> 1;
+    if ((lane & 1) == 0 && k_of_lane < kNAtt)
+        S[o * kNAtt + k_of_lane] = tot;
+    return true;
+}
+
 template <bool SQ>
 __global__ void __launch_bounds__(kThreads)
 k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
@@ -1070,11 +1205,14 @@ k_att_segments(SysView A, const double *__restrict__ y, double *__restrict__ S)
 // resets the counter.  Which warp computes a unit does not change its sums:
 // the global column gets one partial per star unit, gpart[unit].
 // SPL: which units form their products on the binary32 pipes from exact
-// splits (kSplitStars: star units, kSplitInstr: instrument units); the
+// splits (kSplitStars: star units, kSplitInstr: instrument units,
+// kSplitAtt / kSplitAtt2: 4 or 8 of the 12 taps of the attitude units); the
 // others, and every unit of the preconditioner's squares, use native FP64.
 // ---------------------------------------------------------------------------
 constexpr int kSplitStars = 1;
 constexpr int kSplitInstr = 2;
+constexpr int kSplitAtt = 4;   // attitude units: axis 2 (4 of 12 taps)
+constexpr int kSplitAtt2 = 8;  // attitude units: axes 1 and 2 (8 of 12 taps)
 
 template <int G, int MODE, int SPL>
 __global__ void __launch_bounds__(kThreads, 4)  // 64 registers: no spills in any form
@@ -1114,14 +1252,22 @@ k_aprod2_fused(SysView A, const double *__restrict__ y, double *__restrict__ out
                                                                 grp, q.nstar_groups);
                     }
                 }
-                g = warp_sum(g);
+                const double gv[1] = {g};
+                g = warp_sum_split<1>(gv);
                 if (lane == 0)
                     gpart[i] = g;
             }
         } else if (slot < q.ns + q.na) {
             const int64_t i = c * q.na + (slot - q.ns);
-            if (i < A.nseg)
-                att_body<SQ>(A, y, S, i, A.nseg);
+            if (i < A.nseg) {
+                bool done = false;
+                if constexpr ((SPL & kSplitAtt2) != 0)
+                    done = att_unit_split<8>(A, y, S, i);
+                else if constexpr ((SPL & kSplitAtt) != 0)
+                    done = att_unit_split<4>(A, y, S, i);
+                if (!done)  // native FP64 products (an operand outside the split range)
+                    att_body<SQ>(A, y, S, i, A.nseg);
+            }
         } else {
             const int64_t i = c * q.ni + (slot - q.ns - q.na);
             if (i < q.ninstr_units) {
@@ -1226,8 +1372,8 @@ int split_request(const gsr_config &cfg)
         return 0;
     if (p == GSR_PRODUCTS_SPLIT)
         return GSR_SPLIT_APROD1 | GSR_SPLIT_APROD2_STARS | GSR_SPLIT_APROD2_INSTR;
-    if ((p & ~7) == GSR_PRODUCTS_MASK)
-        return p & 7;
+    if ((p & ~31) == GSR_PRODUCTS_MASK)
+        return p & 31;
     // library choice, measured on the medium workload: aprod 1's instrumental
     // and global products only (see aprod2_split for aprod 2's forms)
     return GSR_SPLIT_APROD1;
@@ -1446,7 +1592,8 @@ int aprod2_split(const gsr_handle_t *h)
 {
     const int r = split_request(h->cfg);
     return ((r & GSR_SPLIT_APROD2_STARS) ? kSplitStars : 0) |
-           ((r & GSR_SPLIT_APROD2_INSTR) ? kSplitInstr : 0);
+           ((r & GSR_SPLIT_APROD2_INSTR) ? kSplitInstr : 0) |
+           ((r & GSR_SPLIT_APROD2_ATT2) ? kSplitAtt2 : ((r & GSR_SPLIT_APROD2_ATT) ? kSplitAtt : 0));
 }
 
 int aprod2_split_active(const gsr_handle_t *h)
@@ -1467,6 +1614,9 @@ static void fused_launch(const gsr_handle_t *h, const double *y, double *out, cu
         case kSplitStars: GSR_FUSED(kSplitStars); return;
         case kSplitInstr: GSR_FUSED(kSplitInstr); return;
         case kSplitStars | kSplitInstr: GSR_FUSED(kSplitStars | kSplitInstr); return;
+        case kSplitAtt: GSR_FUSED(kSplitAtt); return;
+        case kSplitAtt2: GSR_FUSED(kSplitAtt2); return;
+        case kSplitAtt | kSplitInstr: GSR_FUSED(kSplitAtt | kSplitInstr); return;
         default: break;
         }
     }
@@ -1814,6 +1964,15 @@ static cudaError_t fused_occupancy(const gsr_handle_t *h, int *occ)
     case kSplitStars | kSplitInstr:
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             occ, k_aprod2_fused<G, kA2Overwrite, kSplitStars | kSplitInstr>, kThreads, 0);
+    case kSplitAtt:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, k_aprod2_fused<G, kA2Overwrite, kSplitAtt>, kThreads, 0);
+    case kSplitAtt2:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, k_aprod2_fused<G, kA2Overwrite, kSplitAtt2>, kThreads, 0);
+    case kSplitAtt | kSplitInstr:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            occ, k_aprod2_fused<G, kA2Overwrite, kSplitAtt | kSplitInstr>, kThreads, 0);
     default:
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             occ, k_aprod2_fused<G, kA2Overwrite, 0>, kThreads, 0);

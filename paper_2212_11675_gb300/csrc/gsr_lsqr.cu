@@ -36,6 +36,7 @@
 
 #include "gsr_internal.cuh"
 #include "gsr_reduce.cuh"
+#include "gsr_split.cuh"
 
 namespace gsr {
 
@@ -99,7 +100,7 @@ __device__ void init_scalars(SolveState *st, const SolveArgs *args, double vnorm
     st->t = beta * args->isdof;
     st->cy = -alpha * alpha * st->ib;  // -alpha_1^2 / (alpha_0 beta_1)
     st->ia = (alpha > 0.0) ? 1.0 / alpha : 1.0;
-    st->t2 = 0.0;
+    st->theta = 0.0;  // W_0 = 0: the first W update takes no old W
     if (!isfinite(alpha) || st->nonfinite) {
         st->nonfinite = 1;
         st->istop = kIstopNonfinite;
@@ -160,7 +161,6 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
     s.anorm = sq[2];
     s.acond = s.anorm * sq[3];
     s.ia = (alpha > 0.0) ? 1.0 / alpha : 1.0;
-    s.t2 = -s.theta * irho;
     s.rnorm = s.phibar;
     s.arnorm = alpha * fabs(tau);
     s.itn += 1;
@@ -195,11 +195,28 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
     *st = s;
 }
 
+// v += x^2 into an exact three-level accumulator (binary32 pipes) when x is
+// in the split window, else into the binary64 fallback fb
+__device__ __forceinline__ void acc_sqr(Acc3 &c, double &fb, double x)
+{
+    float a1, a2, a3;
+    if (split3z(x, a1, a2, a3) < kSplitRangeSpan)
+        acc3_sqr(c, a1, a2, a3);
+    else
+        fb = fma(x, x, fb);
+}
+
 // The vector pass of iteration i (first: the start, V_1 = p o A^T b / beta_1
-// with w, z, var cleared): w_i = V_i/alpha_i - (theta_i/rho_{i-1}) w_{i-1},
-// var += (w_i/rho_i)^2, z_i = z_{i-1} + (phi_i/rho_i) w_i, V_{i+1} (in place),
-// vp = p o V_{i+1}, and the reductions ||V_{i+1}||^2, sum (w_i/rho_i)^2,
-// ||z_i||^2.  When beta_{i+1} = 0 V is kept (alpha unchanged).
+// with w, z, var cleared).  The stored w is W_i = w_i / rho_i of the paper's
+// recurrence, which takes the division by rho out of three updates:
+//   W_i = V_i / (alpha_i rho_i) - (theta_i / rho_i) W_{i-1},
+//   var += W_i^2,  z_i = z_{i-1} + phi_i W_i,
+// then V_{i+1} (in place), vp = p o V_{i+1}, and the reductions
+// ||V_{i+1}||^2, sum W_i^2, ||z_i||^2.  When beta_{i+1} = 0 V is kept (alpha
+// unchanged).  The three sums of squares accumulate on the binary32 pipes
+// from exact splits (acc3_sqr: within about 2^-60 of the exact sum; values
+// outside the split window in binary64), so an element costs 8 FP64
+// operations, the ones that produce stored values.
 // INL: q holds only the astrometric part of A^T U (single-launch aprod 2);
 // the other columns come from its partial sums, and the global column from
 // one fixed slice of the per-unit partials per block, added by the last
@@ -216,12 +233,15 @@ k_vec(const SysView A, const double *__restrict__ p, double *__restrict__ q, dou
     const double ia = st->ia;           // 1/alpha_i
     const double ib = st->ib;           // 1/beta_{i+1}
     const double bn = st->bnext;        // beta_{i+1}
-    const double t1 = first ? 0.0 : st->t1;
-    const double t2 = first ? 0.0 : st->t2;
-    const double irho = first ? 0.0 : st->irho;
+    const double irho = first ? 0.0 : st->irho;  // 1/rho_i
+    const double c1 = ia * irho;                 // 1/(alpha_i rho_i)
+    const double c2 = first ? 0.0 : -st->theta * irho;
+    const double phi = first ? 0.0 : st->t1;     // phi_i
     const bool upd = bn > 0.0;
     const double k1 = ia * ib, k2 = -bn * ia;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    Acc3 c[3] = {Acc3{0.f, 0.f, 0.f}, Acc3{0.f, 0.f, 0.f}, Acc3{0.f, 0.f, 0.f}};
+    double fb[3] = {0.0, 0.0, 0.0};
+    double gacc = 0.0;
 #pragma unroll 2
     for (int64_t j = gtid(); j < n; j += gstride()) {
         const double pj = p[j];
@@ -236,12 +256,11 @@ k_vec(const SysView A, const double *__restrict__ p, double *__restrict__ q, dou
         const double vo = first ? 0.0 : v[j];
         double wj = 0.0, zj = 0.0, vr = 0.0;
         if (!first) {
-            wj = fma(t2, w[j], vo * ia);
-            const double d = wj * irho;
-            acc[1] = fma(d, d, acc[1]);
-            vr = fma(d, d, var[j]);
-            zj = fma(t1, wj, z[j]);
-            acc[2] = fma(zj, zj, acc[2]);
+            wj = fma(c2, w[j], vo * c1);
+            vr = fma(wj, wj, var[j]);
+            zj = fma(phi, wj, z[j]);
+            acc_sqr(c[1], fb[1], wj);
+            acc_sqr(c[2], fb[2], zj);
         }
         w[j] = wj;
         z[j] = zj;
@@ -251,15 +270,20 @@ k_vec(const SysView A, const double *__restrict__ p, double *__restrict__ q, dou
         const double vn = upd ? fma(pj * qj, k1, k2 * vo) : vo;
         v[j] = vn;
         vp[j] = pj * vn;
-        acc[0] = fma(vn, vn, acc[0]);
+        acc_sqr(c[0], fb[0], vn);
     }
     if (INL) {  // this block's fixed slice of the global-column partials
         const uint32_t per = ((uint32_t)P.ngpart + gridDim.x - 1) / gridDim.x;
         const uint32_t b0 = blockIdx.x * per;
         const uint32_t b1 = min((uint32_t)P.ngpart, b0 + per);
         for (uint32_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
-            acc[3] += P.gpart[b];
+            gacc += P.gpart[b];
     }
+    double acc[4];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        acc[k] = acc3_to_double(c[k]) + fb[k];
+    acc[3] = gacc;
     if (grid_reduce<4>(acc, partial, counter)) {
         __shared__ double vn2;
         if (threadIdx.x == 0) {

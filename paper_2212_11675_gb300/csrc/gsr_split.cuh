@@ -46,6 +46,21 @@ __device__ __forceinline__ uint32_t split3_range(uint32_t hi)
     return (hi & 0x7fffffffu) - ((uint32_t)(1023 + kSplitEMin) << 20);
 }
 
+// Window of the values that are only added, never multiplied (the partial
+// sums of the reductions): split3 is exact and its pieces are normal binary32
+// numbers while the lowest piece, 52 binades below the value, stays at or
+// above 2^-122, and the sum of two values cannot overflow.
+constexpr int kSumEMin = -70;
+constexpr int kSumEMax = 120;
+constexpr uint32_t kSumRangeSpan = (uint32_t)(kSumEMax - kSumEMin + 1) << 20;
+
+// below kSumRangeSpan (unsigned) exactly when kSumEMin <= exponent(d) <=
+// kSumEMax
+__device__ __forceinline__ uint32_t split3_sum_range(uint32_t hi)
+{
+    return (hi & 0x7fffffffu) - ((uint32_t)(1023 + kSumEMin) << 20);
+}
+
 // d = h + m + l exactly for d with its exponent in range (split3_range(hi) <
 // kSplitRangeSpan); hi/lo: the upper/lower words of d.  h takes the leading
 // 24 significand bits (truncated), m the next 23, l the last 6, each with
@@ -117,6 +132,23 @@ __device__ __forceinline__ void acc3_fma(Acc3 &c, float a1, float a2, float a3, 
     c.m = two_sum(c.m, p1, u3);
     c.m = two_sum(c.m, p2, u4);
     c.l = __fadd_rn(c.l, __fadd_rn(__fadd_rn(q, u1), __fadd_rn(__fadd_rn(u2, u3), u4)));
+}
+
+// c += a^2 for a = a1 + a2 + a3 (split3 pieces): acc3_fma with x = a, whose
+// two cross products a1 a2 and a2 a1 are one exact product by 2 a1
+__device__ __forceinline__ void acc3_sqr(Acc3 &c, float a1, float a2, float a3)
+{
+    const float t1 = __fadd_rn(a1, a1);  // exact
+    const float p0 = __fmul_rn(a1, a1), e0 = __fmaf_rn(a1, a1, -p0);
+    const float p1 = __fmul_rn(t1, a2), e1 = __fmaf_rn(t1, a2, -p1);
+    // third level (each term below 2^-45 a^2)
+    const float q = __fmaf_rn(a2, a2, __fmaf_rn(t1, a3, e1));
+    float t, u1, u2, u3;
+    c.h = two_sum(c.h, p0, t);
+    c.m = two_sum(c.m, t, u1);
+    c.m = two_sum(c.m, e0, u2);
+    c.m = two_sum(c.m, p1, u3);
+    c.l = __fadd_rn(c.l, __fadd_rn(__fadd_rn(q, u1), __fadd_rn(u2, u3)));
 }
 
 // c += (h, m, l), another three-level value: both exact levels by TwoSum,

@@ -9,6 +9,7 @@
 //   Z a               -> the same from split3z(a) (zero in range, zero pieces)
 //   R n a0 ... a{n-1} -> the values summed by acc3_add on their split3z
 //                        pieces: "ok sum" (acc3_to_double)
+//   W n a0 ... a{n-1} -> as R, ok from the reduction window (split3_sum_range)
 //   A n a0 x0 ... -> n products accumulated with acc3_fma: "ok h m l d0 d1"
 // numbers in C hex-float notation.
 #include <cmath>
@@ -93,7 +94,7 @@ int main()
             float h, m, l;
             const uint32_t r = split3z(a, h, m, l);
             printf("%a %a %a %d\n", (double)h, (double)m, (double)l, r < kSplitRangeSpan ? 1 : 0);
-        } else if (op == 'R') {
+        } else if (op == 'R' || op == 'W') {
             // n binary64 values summed as the reduce-scatter of the row
             // kernels does: split3z pieces added with acc3_add
             int n;
@@ -106,7 +107,13 @@ int main()
                 if (scanf("%la", &a) != 1)
                     return 2;
                 float h, m, l;
-                ok &= split3z(a, h, m, l) < kSplitRangeSpan;
+                const uint32_t r = split3z(a, h, m, l);
+                uint32_t hi, lo;
+                words(a, hi, lo);
+                if (op == 'R')
+                    ok &= r < kSplitRangeSpan;
+                else
+                    ok &= a == 0.0 || split3_sum_range(hi) < kSumRangeSpan;
                 acc3_add(c, h, m, l);
             }
             printf("%d %a\n", ok, acc3_to_double(c));

@@ -64,6 +64,15 @@ def test_create_checks_the_product_form_before_any_cuda_call():
 
     assert create(60, 7) == _lib.GSR_ERR_ARG
     assert create(60, -1) == _lib.GSR_ERR_ARG
+    # the attitude split forms exclude each other and have no kernel with the
+    # split star units, nor (axes 1 and 2) with the split instrument units
+    M = _lib.GSR_PRODUCTS_MASK
+    assert create(60, M | _lib.GSR_SPLIT_APROD2_ATT | _lib.GSR_SPLIT_APROD2_ATT2) == _lib.GSR_ERR_ARG
+    assert (create(60, M | _lib.GSR_SPLIT_APROD2_ATT | _lib.GSR_SPLIT_APROD2_STARS)
+            == _lib.GSR_ERR_UNSUPPORTED)
+    assert (create(60, M | _lib.GSR_SPLIT_APROD2_ATT2 | _lib.GSR_SPLIT_APROD2_INSTR)
+            == _lib.GSR_ERR_UNSUPPORTED)
+    assert create(60, M | 32) == _lib.GSR_ERR_ARG
     # split products keep x in shared memory: at most 3072 instruments
     assert create(4000, _lib.GSR_PRODUCTS_SPLIT) == _lib.GSR_ERR_UNSUPPORTED
     assert not h.value

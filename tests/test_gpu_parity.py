@@ -219,11 +219,11 @@ def oracle_sensitivity(sys, b, itn, trials=3):
     return sens
 
 
-def compare_solve(sys, itmax, atol, btol, seed=1, lanes=0, x_tol=1e-9, early=20):
+def compare_solve(sys, itmax, atol, btol, seed=1, lanes=0, x_tol=1e-9, early=20, **kw):
     b = _rhs(sys, seed)
     ref = oracle.pc_lsqr(sys, b, itmax, atol, btol)
     ref_early = oracle.pc_lsqr(sys, b, early, 0.0, 0.0)
-    with _solver(sys, lanes_per_star=lanes) as s:
+    with _solver(sys, lanes_per_star=lanes, **kw) as s:
         bd = torch.tensor(b, device=DEV)
         # equal iteration count: stop the GPU where the oracle stopped
         x, se, res = s.lsqr_solve(bd, ref["itn"], 0.0, 0.0)

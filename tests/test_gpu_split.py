@@ -290,6 +290,98 @@ def test_split_instrument_sums_out_of_range_fall_back():
             assert np.all(_err(g, ex) <= 30 * U * mag), (case, products)
 
 
+ATT = _lib.GSR_PRODUCTS_MASK | _lib.GSR_SPLIT_APROD2_ATT
+ATT2 = _lib.GSR_PRODUCTS_MASK | _lib.GSR_SPLIT_APROD2_ATT2
+ATT_INSTR = ATT | _lib.GSR_SPLIT_APROD2_INSTR
+
+
+def _offset_groups(sys):
+    """Rows of every attitude offset, in row order."""
+    out = {}
+    for i in range(sys.m):
+        out.setdefault(int(sys.attoff[i]), []).append(i)
+    return out
+
+
+@pytest.mark.parametrize("products,axes", [(ATT, (2,)), (ATT2, (1, 2)), (ATT_INSTR, (2,))])
+def test_split_attitude_sums_exact_under_cancellation(products, axes):
+    # aprod 2's attitude sums: in every offset the last row's 12 attitude
+    # values cancel the offset's other products of the same axis and tap
+    # (about 2^40 each), so every partial sum S[o][a][j] of an attitude unit
+    # is a rounding residual; an offset holds more than 32 rows (a unit's
+    # loop and its tail).  The column a D + k adds the four residuals of
+    # offsets k-3..k, so the bound is on their magnitudes.
+    sys = small(40, 12, 9, obs=12, seed=31)
+    rng = np.random.default_rng(31)
+    vals = sys.values.copy()
+    vals[:, 5:17] = rng.uniform(1.0, 2.0, size=(sys.m, 12)) * 2.0 ** 20
+    y = rng.uniform(1.0, 2.0, size=sys.m) * 2.0 ** 20 * np.where(np.arange(sys.m) % 2 == 0, 1, -1)
+    groups = _offset_groups(sys)
+    assert min(len(g) for g in groups.values()) > 32
+    resid = {}  # exact partial sum of every (offset, tap)
+    for o, rows in groups.items():
+        last = rows[-1]
+        for t in range(12):
+            part = sum(Fraction(float(vals[i, 5 + t])) * Fraction(float(y[i])) for i in rows[:-1])
+            vals[last, 5 + t] = -float(part / Fraction(float(y[last])))
+            resid[o, t] = part + Fraction(float(vals[last, 5 + t])) * Fraction(float(y[last]))
+    sys = gen.GaiaSystem(sys.n_stars, sys.n_dfa, sys.n_instr, sys.star_ptr, sys.attoff,
+                         sys.instr, vals)
+    x0 = np.zeros(sys.n)
+    ex, mag = _exact_t(sys, y, x0)
+    D, att0 = sys.n_dfa, 5 * sys.n_stars
+    rmag = np.zeros(sys.n)  # sum over the column's offsets of |residual partial|
+    for (o, t), r in resid.items():
+        a, j = divmod(t, 4)
+        rmag[att0 + a * D + o + j] += abs(float(r))
+    cols = np.array([att0 + a * D + k for a in axes for k in range(D)])
+    assert np.median(mag[cols] / np.maximum(rmag[cols], 1e-300)) > 1e6
+    g = _aprod2(sys, y, x0, products)
+    err = _err(g, ex)
+    assert np.all(err[cols] <= 4 * U * rmag[cols] + 2.0 ** -59 * mag[cols])
+    assert np.all(err <= 30 * U * mag)
+    # native FP64 products lose up to 2^-53 of the magnitudes per product
+    gn = _aprod2(sys, y, x0, _lib.GSR_PRODUCTS_NATIVE)
+    errn = _err(gn, ex)
+    assert np.all(errn <= 30 * U * mag)
+    assert np.max(errn[cols] / np.maximum(rmag[cols], 1e-300)) > 1e-12
+
+
+@pytest.mark.parametrize("products", [ATT, ATT2])
+def test_split_attitude_sums_out_of_range_fall_back(products):
+    # an operand outside the split range sends its attitude unit to native
+    # FP64 products; zero values and zero y split exactly
+    sys = small(60, 20, 13, obs=12, seed=32)
+    rng = np.random.default_rng(33)
+    vals = sys.values.copy()
+    vals[5, 16] = 1e-13   # axis-2 value below the split range
+    vals[40, 11] = 5e11   # axis-1 value above it
+    vals[41, 14] = 0.0    # zero value
+    sys = gen.GaiaSystem(sys.n_stars, sys.n_dfa, sys.n_instr, sys.star_ptr, sys.attoff,
+                         sys.instr, vals)
+    x0 = rng.standard_normal(sys.n)
+    for case in range(3):
+        y = rng.standard_normal(sys.m)
+        if case == 1:
+            y[100] = 1e-16  # y below the range: its unit falls back
+        if case == 2:
+            y[::7] = 0.0    # zero y splits exactly
+        ex, mag = _exact_t(sys, y, x0)
+        g = _aprod2(sys, y, x0, products)
+        assert np.all(_err(g, ex) <= 30 * U * mag), case
+
+
+@pytest.mark.parametrize("products", [ATT, ATT2, ATT_INSTR])
+def test_split_attitude_products_and_solve(products):
+    # the attitude split forms against the oracle: both products on the tiny
+    # and a ragged system, and the whole solve at equal iteration count
+    from tests.test_gpu_parity import check_aprods, compare_solve
+    for sys in (gen.make("tiny"), small(300, 30, 20, seed=5)):
+        check_aprods(sys, 8, products=products, instr_mode=_lib.GSR_INSTR_SORTED)
+    compare_solve(gen.make("tiny"), 200, 1e-12, 1e-12, products=products,
+                  instr_mode=_lib.GSR_INSTR_SORTED)
+
+
 @pytest.mark.parametrize("lanes", [4, 8, 16, 32])
 def test_split_star_pass_every_lane_count(lanes):
     # the split star pass of aprod 2 (explicit GSR_PRODUCTS_SPLIT) with 4 lanes
@@ -311,6 +403,12 @@ def test_product_forms_report_what_runs():
         assert s.product_forms() == (False, 2)
     with Solver(tiny, products=_lib.GSR_PRODUCTS_MASK | _lib.GSR_SPLIT_APROD2_STARS) as s:
         assert s.product_forms() == (False, 1)
+    with Solver(tiny, products=ATT) as s:
+        assert s.product_forms() == (False, 4)
+    with Solver(tiny, products=ATT2 | _lib.GSR_SPLIT_APROD1) as s:
+        assert s.product_forms() == (True, 8)
+    with Solver(tiny, products=ATT_INSTR) as s:
+        assert s.product_forms() == (False, 6)
     with Solver(tiny, products=_lib.GSR_PRODUCTS_SPLIT, instr_mode=_lib.GSR_INSTR_SMEM) as s:
         assert s.product_forms() == (True, 0)  # no single-launch aprod 2 on this path
     # more instruments than the split x fits in shared memory: native aprod 1

@@ -154,3 +154,39 @@ def test_reduction_of_split_partials_is_exact(harness):
         mag = sum(abs(v) for v in vals)
         err = abs(Fraction(float.fromhex(got)) - exact)
         assert err <= 2 * 2.0 ** -53 * abs(exact) + 2.0 ** -60 * Fraction(mag), vals
+
+
+def test_reduction_window_is_exact_at_its_ends(harness):
+    """The reductions accept partial sums with exponents in [-70, 120] (they
+    are only added, never multiplied): split exactly, summed with acc3_add,
+    within two binary64 roundings of the exact sum plus 2^-60 of the sum of
+    magnitudes, also under cancellation, at both ends of the window; one
+    binade beyond either end is reported out of the window."""
+    rng = random.Random(8)
+    lines, cases = [], []
+    for trial in range(300):
+        n = rng.choice([2, 5, 8, 12, 16, 32])
+        e = rng.choice([-70, -69, -60, 40, 110, 119]) if trial % 2 else rng.randint(-70, 118)
+        vals = [math.ldexp(rng.uniform(1.0, 2.0) * rng.choice([-1, 1]), e - rng.randint(0, 2)
+                           if e - 2 >= -70 else e) for _ in range(n)]
+        if trial % 3 == 0:
+            s = sum(Fraction(v) for v in vals[:-1])
+            rest = float(s) * 2.0 ** -30 * rng.choice([-1, 1])
+            last = float(-s) + rest
+            if last == 0.0 or _exp(abs(last)) < -70:
+                last = float(-s)
+            vals[-1] = last
+        cases.append(vals)
+        lines.append("W %d %s\n" % (n, " ".join(float(v).hex() for v in vals)))
+    out = harness(lines)
+    for vals, line in zip(cases, out):
+        ok, got = line.split()
+        assert ok == ("1" if all(v == 0.0 or -70 <= _exp(abs(v)) <= 120 for v in vals) else "0")
+        if ok != "1":
+            continue
+        exact = sum(Fraction(v) for v in vals)
+        mag = sum(abs(v) for v in vals)
+        err = abs(Fraction(float.fromhex(got)) - exact)
+        assert err <= 2 * 2.0 ** -53 * abs(exact) + 2.0 ** -60 * Fraction(mag), vals
+    out = harness(["W 1 %s\n" % math.ldexp(1.5, e).hex() for e in (-71, -70, 120, 121)])
+    assert [o.split()[0] for o in out] == ["0", "1", "1", "0"]
