@@ -231,6 +231,7 @@ def _timer(torch, stream, reps):
 
 
 def _rel(torch, x, xr):
+    torch.cuda.synchronize()  # x may come from a solve on another stream
     return float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
 
 
@@ -287,11 +288,13 @@ def batched_vs_sequential(s, xt, noise, torch, stream, ks=(8, 32), target=1e-9, 
     out = {"target_rel_err": target, "ladder": "atol from 1e-6 down"}
     K = max(ks)
     ax = torch.zeros(s.m, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()  # xt and ax come from the current stream, the solves use `stream`
     s.aprod1(xt, ax, stream=stream)
     torch.cuda.synchronize()
     B = torch.empty((K, s.m), dtype=torch.float64, device="cuda")
     for j in range(K):
         torch.add(ax, noise(j), out=B[j])
+    torch.cuda.synchronize()
     del ax
     refs = [s.lsqr_solve(B[j], 20000, ref_tol, ref_tol, stream=stream, want_se=False)[0]
             for j in range(K)]
@@ -373,6 +376,7 @@ def large_comparison(name, torch, stream, ks=(8, 32)):
         with Clocks(torch.cuda.current_device()) as clk:
             if name == "large":
                 b = gen.noise_t(sys_, seed + 1, dev)
+                torch.cuda.synchronize()  # b and xt come from the current stream
                 s.aprod1(xt, b, stream=stream)
                 torch.cuda.synchronize()
                 line["mixed_vs_fp64"] = time_to_solution(s, b, torch, stream, reps=2)
@@ -430,9 +434,11 @@ def profile_main(args):
             X = torch.randn((k, s.n), dtype=torch.float64, device=dev, generator=g)
             Y = torch.randn((k, s.m), dtype=torch.float64, device=dev, generator=g)
             s.set_batch_tiling(args.profile_kt, args.profile_lanes)
+            torch.cuda.synchronize()  # X and Y come from the current stream
             for _ in range(2):
                 s.batched_products(X, Y, stream=stream)
             B = b.repeat(k, 1)
+            torch.cuda.synchronize()
             _, r = s.batched_solve(B, max_outer=1, max_inner=10, inner_tol=0.0, atol=0.0,
                                    stream=stream)
             out["result"] = r[0]
@@ -633,7 +639,7 @@ def main():
     # 6 per row in the star units, 6 in the instrument units, 4 or 8 in the
     # attitude units)
     split1, split2 = solver.product_forms()
-    flops_a1 = 2 * (24 - (7 if split1 else 0)) * m
+    flops_a1 = 2 * (24 - {0: 0, 1: 7, 2: 12}[split1]) * m
     flops_a2 = 2 * (24 - (6 if split2 & 1 else 0) - (6 if split2 & 2 else 0)
                     - (4 if split2 & 4 else 0) - (8 if split2 & 8 else 0)) * m
     gbs_a1, gbs_a2 = bytes_a1 / t_a1 / 1e9, bytes_a2 / t_a2 / 1e9

@@ -98,6 +98,10 @@ extern "C" {
                                      GSR_SPLIT_APROD2_INSTR (no kernel
                                      combines them: GSR_ERR_UNSUPPORTED at
                                      creation; both attitude bits: GSR_ERR_ARG) */
+#define GSR_SPLIT_APROD1_ASTRO 32 /* with GSR_SPLIT_APROD1 (GSR_ERR_ARG
+                                     without it): where aprod 1 runs staged by
+                                     the bulk-copy engine, its 5 astrometric
+                                     products too */
 
 /* Storage and arithmetic of the matrix values. */
 #define GSR_PREC_FP64 0  /* IEEE double values, native FP64 arithmetic */
@@ -280,7 +284,8 @@ int gsr_mixed_solve(void *h, const double *b, int max_outer, int max_inner,
 /*
  * Which FP64 products of the handle run on the binary32 pipes from exact
  * splits: *aprod1_split_on = 1 when aprod 1 forms its instrumental and
- * global products that way (0: native FP64); *aprod2_split_on is a set of
+ * global products that way, 2 when its astrometric products too (0: native
+ * FP64); *aprod2_split_on is a set of
  * bits for aprod 2's single-launch pass: 1 its star units' astrometric and
  * global products, 2 its instrument units' products, 4 the axis-2 products
  * of its attitude units, 8 the axis-1 and axis-2 products of its attitude

@@ -27,7 +27,7 @@ GSR_INSTR_AUTO, GSR_INSTR_SMEM, GSR_INSTR_REPLICAS, GSR_INSTR_SORTED = 0, 1, 2, 
 GSR_PRODUCTS_AUTO, GSR_PRODUCTS_NATIVE, GSR_PRODUCTS_SPLIT = 0, 1, 2
 GSR_PRODUCTS_MASK = 0x100
 GSR_SPLIT_APROD1, GSR_SPLIT_APROD2_STARS, GSR_SPLIT_APROD2_INSTR = 1, 2, 4
-GSR_SPLIT_APROD2_ATT, GSR_SPLIT_APROD2_ATT2 = 8, 16
+GSR_SPLIT_APROD2_ATT, GSR_SPLIT_APROD2_ATT2, GSR_SPLIT_APROD1_ASTRO = 8, 16, 32
 
 EXPORTS = (
     "gsr_config_default", "gsr_create", "gsr_destroy", "gsr_aprod1", "gsr_aprod2",

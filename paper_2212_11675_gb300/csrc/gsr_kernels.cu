@@ -117,15 +117,19 @@ __device__ __forceinline__ uint32_t instr_at(const uint4 &rc, int j)
 // keep the FP64 pipe fed with one merge (four sums were 4% slower: two more
 // FP64 adds per row).  SPLIT: the instrumental and global products on the
 // binary32 pipes (x pieces s_x4 in shared memory, global pieces g1..g3).
-template <bool SMEMX, bool SPLIT>
+// ASTRO (with SPLIT): the five astrometric products too, with the star's x
+// split per row.
+template <bool SMEMX, bool SPLIT, bool ASTRO = false>
 __device__ __forceinline__ double row_sum(const SysView &A, const double *__restrict__ x,
                                           const double (&vk)[kNPar], const uint4 &rc, uint32_t s,
                                           const float4 *s_x4, const double *s_xi, bool split_x,
                                           double xg, float g1, float g2, float g3)
 {
+    static_assert(SPLIT || !ASTRO, "the astrometric split extends the split form");
     double s0, s1;
     if constexpr (SPLIT) {
         bool native = true;
+        const double *xs = x + (int64_t)kNAstro * s;
         if (split_x) {
             // instrumental and global products on the binary32
             // pipes; their sum h + (m + l) starts the FP64 chains
@@ -148,6 +152,15 @@ __device__ __forceinline__ double row_sum(const SysView &A, const double *__rest
                     acc3_fma(c, a1, a2, a3, g1, g2, g3);
                 }
             }
+            if constexpr (ASTRO) {
+#pragma unroll
+                for (int k = 0; k < kNAstro; k++) {
+                    float a1, a2, a3, x1, x2, x3;
+                    rng = max(rng, split3z(vk[k], a1, a2, a3));
+                    rng = max(rng, split3z(__ldg(xs + k), x1, x2, x3));
+                    acc3_fma(c, a1, a2, a3, x1, x2, x3);
+                }
+            }
             if (rng < kSplitRangeSpan && flag == 0.f) {
                 acc3_parts(c, s0, s1);
                 native = false;
@@ -159,11 +172,17 @@ __device__ __forceinline__ double row_sum(const SysView &A, const double *__rest
             for (int j = 0; j < kNInstr; j++)
                 s0 = fma(vk[17 + j], __ldg(x + A.ins0 + instr_at(rc, j)), s0);
             s1 = 0.0;
-        }
-        const double *xs = x + (int64_t)kNAstro * s;
+            if constexpr (ASTRO) {
 #pragma unroll
-        for (int k = 0; k < kNAstro; k++)
-            s0 = fma(vk[k], __ldg(xs + k), s0);
+                for (int k = 0; k < kNAstro; k++)
+                    s0 = fma(vk[k], __ldg(xs + k), s0);
+            }
+        }
+        if constexpr (!ASTRO) {
+#pragma unroll
+            for (int k = 0; k < kNAstro; k++)
+                s0 = fma(vk[k], __ldg(xs + k), s0);
+        }
         const double *xa = x + A.att0 + rc.x;
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -414,7 +433,7 @@ __device__ __forceinline__ void tma_stage_tile(const SysView &A, int64_t t, uint
                  "r"(kTileDeltaBytes), "r"(bar) : "memory");
 }
 
-template <int MODE>
+template <int MODE, bool ASTRO>
 __global__ void __launch_bounds__(kTmaThreads, 1)
 k_aprod1_tma(SysView A, const double *__restrict__ x, double *__restrict__ y, SolveState *st,
              double *partial, unsigned *counter, CgState *cg, int *kerr, int64_t drop)
@@ -511,8 +530,8 @@ k_aprod1_tma(SysView A, const double *__restrict__ x, double *__restrict__ y, So
             if (d == 0xffffu)
                 while ((int64_t)A.star_ptr[st_ + 1] <= r)
                     ++st_;
-            const double sum = row_sum<true, true>(A, x, vk, rc, st_, s_x4, nullptr, split_x, xg,
-                                                   g1, g2, g3);
+            const double sum = row_sum<true, true, ASTRO>(A, x, vk, rc, st_, s_x4, nullptr,
+                                                          split_x, xg, g1, g2, g3);
             double yn;
             if (MODE == 1) {
                 yn = fma(cy, yst ? yo : y[r], sum);
@@ -1372,8 +1391,8 @@ int split_request(const gsr_config &cfg)
         return 0;
     if (p == GSR_PRODUCTS_SPLIT)
         return GSR_SPLIT_APROD1 | GSR_SPLIT_APROD2_STARS | GSR_SPLIT_APROD2_INSTR;
-    if ((p & ~31) == GSR_PRODUCTS_MASK)
-        return p & 31;
+    if ((p & ~63) == GSR_PRODUCTS_MASK)
+        return p & 63;
     // library choice, measured on the medium workload: aprod 1's instrumental
     // and global products only (see aprod2_split for aprod 2's forms)
     return GSR_SPLIT_APROD1;
@@ -1402,14 +1421,11 @@ cudaError_t aprod1_tma_prepare(gsr_handle_t *h)
                                            h->device);
     if (e != cudaSuccess || need == 0 || need > (size_t)optin)
         return e;
-    e = cudaFuncSetAttribute(k_aprod1_tma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)need);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_aprod1_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)need);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_aprod1_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)need);
+    const void *fns[6] = {(const void *)k_aprod1_tma<0, false>, (const void *)k_aprod1_tma<1, false>,
+                          (const void *)k_aprod1_tma<2, false>, (const void *)k_aprod1_tma<0, true>,
+                          (const void *)k_aprod1_tma<1, true>, (const void *)k_aprod1_tma<2, true>};
+    for (int i = 0; i < 6 && e == cudaSuccess; i++)
+        e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     if (e == cudaSuccess)
         h->a1_tma_avail = 1;
     return e;
@@ -1421,8 +1437,11 @@ static cudaError_t a1_launch(const gsr_handle_t *h, const double *x, double *y,
                              cudaStream_t st, CgState *cg = nullptr)
 {
     const bool smem = h->sys.I <= kSmemInstrMax;
-    if (h->a1_tma)
-        k_aprod1_tma<MODE><<<h->grid_rows, kTmaThreads, aprod1_tma_smem(h), st>>>(
+    if (h->a1_tma && (split_request(h->cfg) & GSR_SPLIT_APROD1_ASTRO))
+        k_aprod1_tma<MODE, true><<<h->grid_rows, kTmaThreads, aprod1_tma_smem(h), st>>>(
+            h->sys, x, y, st_slot, partial, counter, cg, h->d_kerr, h->drop_tile);
+    else if (h->a1_tma)
+        k_aprod1_tma<MODE, false><<<h->grid_rows, kTmaThreads, aprod1_tma_smem(h), st>>>(
             h->sys, x, y, st_slot, partial, counter, cg, h->d_kerr, h->drop_tile);
     else if (aprod1_split(h))
         k_aprod1<MODE, true, true><<<h->grid_rows, kThreads, (size_t)h->sys.I * sizeof(float4),
@@ -1914,7 +1933,7 @@ int aprod1_grid(const gsr_handle_t *h)
     int occ = 0;
     cudaError_t e;
     if (h->a1_tma)  // one block per SM
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1_tma<1>, kTmaThreads,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1_tma<1, false>, kTmaThreads,
                                                           aprod1_tma_smem(h));
     else if (aprod1_split(h))
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_aprod1<1, true, true>, kThreads,

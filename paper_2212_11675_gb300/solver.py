@@ -216,13 +216,14 @@ class Solver:
 
     def product_forms(self):
         """(aprod1_split, aprod2_split): which FP64 products run on the binary32
-        pipes from exact splits: aprod1_split a bool, aprod2_split a set of bits
-        (1 star units, 2 instrument units, 4 and 8 the axis-2 and axes-1-2 taps
-        of the attitude units of the single-launch aprod 2)."""
+        pipes from exact splits: aprod1_split 0 (none), 1 (instrumental and
+        global) or 2 (also astrometric), aprod2_split a set of bits (1 star
+        units, 2 instrument units, 4 and 8 the axis-2 and axes-1-2 taps of the
+        attitude units of the single-launch aprod 2)."""
         a1, a2 = ctypes.c_int(), ctypes.c_int()
         check(lib().gsr_product_forms(self._h, ctypes.byref(a1), ctypes.byref(a2)),
               "gsr_product_forms")
-        return bool(a1.value), int(a2.value)
+        return int(a1.value), int(a2.value)
 
     def time_iteration(self, b, iters=20, stream=None):
         """Average durations (ms) of aprod 1, aprod 2 and the vector pass of an

@@ -72,7 +72,9 @@ def test_create_checks_the_product_form_before_any_cuda_call():
             == _lib.GSR_ERR_UNSUPPORTED)
     assert (create(60, M | _lib.GSR_SPLIT_APROD2_ATT2 | _lib.GSR_SPLIT_APROD2_INSTR)
             == _lib.GSR_ERR_UNSUPPORTED)
-    assert create(60, M | 32) == _lib.GSR_ERR_ARG
+    # the astrometric split extends aprod 1's split form
+    assert create(60, M | _lib.GSR_SPLIT_APROD1_ASTRO) == _lib.GSR_ERR_ARG
+    assert create(60, M | 64) == _lib.GSR_ERR_ARG
     # split products keep x in shared memory: at most 3072 instruments
     assert create(4000, _lib.GSR_PRODUCTS_SPLIT) == _lib.GSR_ERR_UNSUPPORTED
     assert not h.value

@@ -133,6 +133,79 @@ def test_split_out_of_range_operands_fall_back():
             np.testing.assert_array_equal(g[~uses5], g0[~uses5])
 
 
+ASTRO = _lib.GSR_PRODUCTS_MASK | _lib.GSR_SPLIT_APROD1 | _lib.GSR_SPLIT_APROD1_ASTRO
+
+
+def test_split_astrometric_products_exact_under_cancellation():
+    # rows whose attitude values are zero and whose 12 astrometric,
+    # instrumental and global products (about 2^48 each) cancel to a rounding
+    # residual: with the astrometric products also split (staged aprod 1),
+    # the row is within the final roundings plus 2^-60 of sum |terms|
+    sys = small(40, 12, 9, obs=8, seed=41)
+    rng = np.random.default_rng(41)
+    x = rng.standard_normal(sys.n)
+    ins0 = 5 * sys.n_stars + 3 * sys.n_dfa
+    x[:5 * sys.n_stars] = rng.uniform(1.0, 2.0, size=5 * sys.n_stars) * 2.0 ** 24
+    x[ins0:] = rng.uniform(1.0, 2.0, size=sys.n - ins0) * 2.0 ** 24
+    vals = sys.values.copy()
+    vals[:, 5:17] = 0.0
+    sign = np.where(np.arange(11) % 2 == 0, 1.0, -1.0)
+    big = rng.uniform(1.0, 2.0, size=(sys.m, 11)) * 2.0 ** 24 * sign[None, :]
+    vals[:, 0:5] = big[:, :5]
+    vals[:, 17:23] = big[:, 5:]
+    cols = columns(sys)
+    xg = Fraction(float(x[-1]))
+    for i in range(sys.m):
+        part = sum(Fraction(float(vals[i, k])) * Fraction(float(x[cols[i, k]]))
+                   for k in list(range(5)) + list(range(17, 23)))
+        vals[i, 23] = -float(part / xg)
+    sys = gen.GaiaSystem(sys.n_stars, sys.n_dfa, sys.n_instr, sys.star_ptr, sys.attoff,
+                         sys.instr, vals)
+    from paper_2212_11675_gb300.solver import Solver
+    with Solver(sys, products=ASTRO) as s:
+        assert s.aprod1_staging() and s.product_forms()[0] == 2
+    y0 = np.zeros(sys.m)
+    ex, mag = _exact(sys, x, y0)
+    exf = np.array([float(e) for e in ex])
+    assert np.median(mag / np.maximum(np.abs(exf), 1e-300)) > 1e6
+    g = _aprod1(sys, x, y0, ASTRO)
+    assert np.all(_err(g, ex) <= 2 * U * np.abs(exf) + 2.0 ** -60 * mag)
+    # the default split form keeps the five astrometric FMAs native
+    gd = _aprod1(sys, x, y0, _lib.GSR_PRODUCTS_SPLIT)
+    assert np.all(_err(gd, ex) <= 30 * U * mag)
+    assert np.max(_err(gd, ex) / np.maximum(np.abs(exf), 1e-300)) > 1e-12
+
+
+def test_split_astrometric_out_of_range_fall_back():
+    sys = small(60, 20, 13, obs=12, seed=42)
+    rng = np.random.default_rng(43)
+    vals = sys.values.copy()
+    vals[0, 2] = 1e-12    # astrometric value below 2^-30
+    vals[1, 4] = 3e12     # above 2^30
+    vals[2, 0] = 0.0      # zero value
+    sys = gen.GaiaSystem(sys.n_stars, sys.n_dfa, sys.n_instr, sys.star_ptr, sys.attoff,
+                         sys.instr, vals)
+    x = rng.standard_normal(sys.n)
+    y0 = rng.standard_normal(sys.m)
+    for case in range(3):
+        xc = x.copy()
+        if case == 1:
+            xc[5 * 3 + 1] = 1e-14  # star 3's parallax out of range: its rows go native
+        if case == 2:
+            xc[5 * 7] = 0.0        # a zero x splits exactly
+        ex, mag = _exact(sys, xc, y0)
+        g = _aprod1(sys, xc, y0, ASTRO)
+        assert np.all(_err(g, ex) <= 27 * U * mag), case
+
+
+def test_split_astrometric_products_and_solve():
+    from tests.test_gpu_parity import check_aprods, compare_solve
+    from tests._systems import ragged
+    for sys in (gen.make("tiny"), ragged()):
+        check_aprods(sys, 8, products=ASTRO)
+    compare_solve(gen.make("tiny"), 200, 1e-12, 1e-12, products=ASTRO)
+
+
 def test_split_matches_native_on_a_generated_system():
     sys = gen.make("tiny")
     rng = np.random.default_rng(9)
@@ -395,6 +468,10 @@ def test_product_forms_report_what_runs():
     tiny = gen.make("tiny")
     with Solver(tiny) as s:  # default: split aprod 1, native aprod 2
         assert s.product_forms() == (True, 0)
+    with Solver(tiny, products=ASTRO) as s:  # staged aprod 1: astrometric products too
+        assert s.product_forms() == (2, 0)
+        s.set_aprod1_staging(False)  # the register form has no astrometric split
+        assert s.product_forms() == (1, 0)
     with Solver(tiny, products=_lib.GSR_PRODUCTS_NATIVE) as s:
         assert s.product_forms() == (False, 0)
     with Solver(tiny, products=_lib.GSR_PRODUCTS_SPLIT) as s:
@@ -413,4 +490,4 @@ def test_product_forms_report_what_runs():
         assert s.product_forms() == (True, 0)  # no single-launch aprod 2 on this path
     # more instruments than the split x fits in shared memory: native aprod 1
     with Solver(small(300, 50, 7000, seed=9)) as s:
-        assert s.product_forms()[0] is False
+        assert s.product_forms()[0] == 0
