@@ -147,7 +147,7 @@ static void release(gsr_handle_t *h)
                    h->d_xp64, h->d_q64, h->d_iseg, h->d_cseg, h->d_cseg32, h->d_irow, h->d_ival32, h->d_ival, h->d_ipart, h->d_gpart, h->d_a2ctr, h->d_bX32, h->d_bQ32,
                    h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT, h->d_bS, h->d_bXcm,
                    h->d_bCcm, h->d_bB, h->d_bnorms, h->d_bpartial, h->d_bcounter, h->d_bs,
-                   h->d_bipart, h->d_iperm, h->d_q32att, h->d_bQ32att,
+                   h->d_bipart,
                    h->d_bargs};
     for (void *p : dev)
         if (p)
@@ -278,9 +278,6 @@ static int create_mixed(gsr_handle_t *h, cudaStream_t st)
     TRY(dalloc(h, &h->d_xatt4, 3 * A.D * 4));
     CK(cudaMemset(h->d_xatt4, 0, 3 * A.D * 4 * sizeof(float)));
     TRY(dalloc(h, &h->d_q32, m));
-    TRY(dalloc(h, &h->d_iperm, m));
-    TRY(dalloc(h, &h->d_q32att, m));
-    CK(launch_invert_perm(h, st));
     CK(launch_to_f32(h, h->d_val, h->d_val32, kNPar * mp, st));
     CK(launch_to_f32(h, h->d_tval, h->d_tval32, kNAtt * mp, st));
     A.val32 = h->d_val32;
@@ -1066,16 +1063,14 @@ static int ensure_batched(gsr_handle_t *h, int k)
     const SysView &A = h->sys;
     const int ldk = (k + 7) / 8 * 8;
     if (ldk > h->bk) {
-        void *old[] = {h->d_bX32, h->d_bQ32, h->d_bQ32att, h->d_bC, h->d_bS_, h->d_bD, h->d_bZ,
-                       h->d_bT};
+        void *old[] = {h->d_bX32, h->d_bQ32, h->d_bC, h->d_bS_, h->d_bD, h->d_bZ, h->d_bT};
         for (void *p : old)
             if (p)
                 cudaFree(p);
-        h->d_bX32 = nullptr; h->d_bQ32 = nullptr; h->d_bQ32att = nullptr; h->d_bC = nullptr;
-        h->d_bS_ = nullptr; h->d_bD = nullptr; h->d_bZ = nullptr; h->d_bT = nullptr;
+        h->d_bX32 = nullptr; h->d_bQ32 = nullptr; h->d_bC = nullptr; h->d_bS_ = nullptr;
+        h->d_bD = nullptr; h->d_bZ = nullptr; h->d_bT = nullptr;
         TRY(dalloc(h, &h->d_bX32, A.n * ldk));
         TRY(dalloc(h, &h->d_bQ32, A.m * ldk));
-        TRY(dalloc(h, &h->d_bQ32att, A.m * ldk));
         TRY(dalloc(h, &h->d_bC, A.n * ldk));
         TRY(dalloc(h, &h->d_bS_, A.n * ldk));
         TRY(dalloc(h, &h->d_bD, A.n * ldk));

@@ -68,8 +68,7 @@ __device__ __forceinline__ bool grid_reduce_cols(double (&v)[KT], double *partia
 template <int KT>
 __global__ void __launch_bounds__(kThreads, 3)
 k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ldk, int c0,
-           BatchState *bs, double *partial, unsigned *counter, const uint32_t *__restrict__ iperm,
-           float *__restrict__ Qatt)
+           BatchState *bs, double *partial, unsigned *counter)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -110,14 +109,10 @@ k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ld
                 df_acc(h[c], l[c], __fmul_rn(a, xv[c]));
         }
         float *q = Q + r * ldk + c0;
-        // Qatt: the same row again at its place in the attitude order
-        float *qa = Qatt ? Qatt + (int64_t)__ldcs(iperm + r) * ldk + c0 : nullptr;
 #pragma unroll
         for (int c = 0; c < KT; c++) {
             const float qv = __fadd_rn(h[c], l[c]);
             q[c] = qv;
-            if (qa)
-                qa[c] = qv;
             const float pq = __fmul_rn(qv, qv);  // q^2 = pq + fma(q, q, -pq) exactly
             df_acc(nh[c], nl[c], pq);
             nl[c] = __fadd_rn(nl[c], __fmaf_rn(qv, qv, -pq));
@@ -226,8 +221,7 @@ k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ld
 // ---------------------------------------------------------------------------
 template <int KT>
 __global__ void __launch_bounds__(kThreads)
-k_b_att(SysView A, const float *__restrict__ Y, const float *__restrict__ Yatt,
-        double *__restrict__ S, int ldk, int c0)
+k_b_att(SysView A, const float *__restrict__ Y, double *__restrict__ S, int ldk, int c0)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -247,11 +241,7 @@ k_b_att(SysView A, const float *__restrict__ Y, const float *__restrict__ Yatt,
         // the same order as one at a time
         uint32_t e = e0 + lane;
         for (; e + 32 < e1; e += 64) {
-            // Yatt: Y in the order of the copy (row e of Yatt is row perm[e]
-            // of Y), read in sequence
-            const float *pa = Yatt ? Yatt + (int64_t)e * ldk : Y + (int64_t)__ldcs(A.perm + e) * ldk;
-            const float *pb = Yatt ? Yatt + (int64_t)(e + 32) * ldk
-                                   : Y + (int64_t)__ldcs(A.perm + e + 32) * ldk;
+            const uint32_t ra = __ldcs(A.perm + e), rb = __ldcs(A.perm + e + 32);
             float va[4], vb[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -259,8 +249,8 @@ k_b_att(SysView A, const float *__restrict__ Y, const float *__restrict__ Yatt,
                 vb[j] = __ldcs(A.tval32 + tidx<kNAtt>(4 * a + j, e + 32));
             }
             float ya[KT], yb[KT];
-            load_cols<KT>(pa + c0, ya);
-            load_cols<KT>(pb + c0, yb);
+            load_cols<KT>(Y + (int64_t)ra * ldk + c0, ya);
+            load_cols<KT>(Y + (int64_t)rb * ldk + c0, yb);
 #pragma unroll
             for (int j = 0; j < 4; j++)
 #pragma unroll
@@ -274,8 +264,7 @@ k_b_att(SysView A, const float *__restrict__ Y, const float *__restrict__ Yatt,
         }
         if (e < e1) {
             float yv[KT];
-            load_cols<KT>((Yatt ? Yatt + (int64_t)e * ldk : Y + (int64_t)__ldcs(A.perm + e) * ldk) + c0,
-                          yv);
+            load_cols<KT>(Y + (int64_t)__ldcs(A.perm + e) * ldk + c0, yv);
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const float v = __ldcs(A.tval32 + tidx<kNAtt>(4 * a + j, e));
@@ -587,13 +576,12 @@ __global__ void k_b_update_x(const double *__restrict__ p, const double *__restr
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-// Qatt: also write Q in the attitude order (the inner solve), or null
 template <int KT>
 static cudaError_t b_aprod1(const gsr_handle_t *h, const float *X, float *Q, int ldk, int c0,
-                            cudaStream_t st, float *Qatt = nullptr)
+                            cudaStream_t st)
 {
     k_b_aprod1<KT><<<h->grid_b1, kThreads, 0, st>>>(h->sys, X, Q, ldk, c0, h->d_bs,
-                                                    h->d_bpartial, h->d_bcounter, h->d_iperm, Qatt);
+                                                    h->d_bpartial, h->d_bcounter);
     return cudaGetLastError();
 }
 
@@ -609,10 +597,9 @@ static int stars_grid(const gsr_handle_t *h)
     return h->nsm * occ;
 }
 
-// Yatt: Y in the attitude order for the attitude pass, or null
 template <int KT>
 static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, int ldk, int c0,
-                            cudaStream_t st, const float *Yatt = nullptr)
+                            cudaStream_t st)
 {
     // the star and attitude passes keep at most 4 columns per lane (register
     // pressure); wider tiles are split
@@ -623,7 +610,7 @@ static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, in
         case 32: k_b_stars<KS, 32><<<stars_grid<KS, 32>(h), kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
         default: k_b_stars<KS, 16><<<stars_grid<KS, 16>(h), kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
         }
-        k_b_att<KS><<<h->grid_att, kThreads, 0, st>>>(h->sys, Y, Yatt, h->d_bS, ldk, cs);
+        k_b_att<KS><<<h->grid_att, kThreads, 0, st>>>(h->sys, Y, h->d_bS, ldk, cs);
         k_b_att_combine<KS><<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_bS, T, ldk, cs);
     }
     k_b_instr<KT><<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_iseg, h->d_irow, h->d_ival32, Y,
@@ -645,9 +632,9 @@ static cudaError_t b_prologue_tile(const gsr_handle_t *h, int ldk, int c0, cudaS
 template <int KT>
 static cudaError_t b_iteration_tile_a(const gsr_handle_t *h, int ldk, int c0, cudaStream_t s)
 {
-    cudaError_t e = b_aprod1<KT>(h, h->d_bX32, h->d_bQ32, ldk, c0, s, h->d_bQ32att);
+    cudaError_t e = b_aprod1<KT>(h, h->d_bX32, h->d_bQ32, ldk, c0, s);
     if (e == cudaSuccess)
-        e = b_aprod2<KT>(h, h->d_bQ32, h->d_bT, ldk, c0, s, h->d_bQ32att);
+        e = b_aprod2<KT>(h, h->d_bQ32, h->d_bT, ldk, c0, s);
     if (e != cudaSuccess)
         return e;
     k_b_vec1<KT><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_bT, h->d_bS_, h->d_bD, h->d_bZ,

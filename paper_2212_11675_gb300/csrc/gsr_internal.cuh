@@ -225,11 +225,6 @@ struct gsr_handle_t {
     // mixed precision
     float *d_val32 = nullptr, *d_tval32 = nullptr;
     float *d_x32 = nullptr, *d_q32 = nullptr;
-    // mixed inner solve: the CG's q32 also in the order of the offset-sorted
-    // attitude copy (q32att[e] = q32[perm[e]]), written by aprod 1 through
-    // iperm (the inverse of perm), so aprod 2's attitude units stream it
-    uint32_t *d_iperm = nullptr;
-    float *d_q32att = nullptr;
     float *d_xatt4 = nullptr;           // [3D][4] attitude part of x32 as one float4 per offset
     double *d_c = nullptr, *d_s = nullptr, *d_d = nullptr, *d_t = nullptr, *d_zc = nullptr;
     double *d_xm = nullptr, *d_r = nullptr, *d_xneg = nullptr, *d_onorm = nullptr;
@@ -243,7 +238,6 @@ struct gsr_handle_t {
     int bkcm = 0;                                     // columns of the column-major buffers
     int bkB = 0;                                      // columns of the staged right-hand sides
     float *d_bX32 = nullptr, *d_bQ32 = nullptr;
-    float *d_bQ32att = nullptr;  // d_bQ32 in the attitude order (rows e = perm order)
     double *d_bC = nullptr, *d_bS_ = nullptr, *d_bD = nullptr, *d_bZ = nullptr, *d_bT = nullptr;
     double *d_bS = nullptr;                           // attitude sums of one column tile
     double *d_bipart = nullptr;                       // [I][4][8] instrumental partials
@@ -347,7 +341,6 @@ cudaError_t launch_norms2(const gsr_handle_t *h, const double *c, const double *
 cudaError_t launch_neg(const gsr_handle_t *h, const double *a, double *b, int64_t n, cudaStream_t st);
 cudaError_t launch_count_pos(const gsr_handle_t *h, const double *a, double *out, cudaStream_t st);
 cudaError_t launch_to_f32(const gsr_handle_t *h, const double *a, float *b, int64_t n, cudaStream_t st);
-cudaError_t launch_invert_perm(const gsr_handle_t *h, cudaStream_t st);
 int aprod1_f32_grid(const gsr_handle_t *h);
 int aprod2_f32_grid(const gsr_handle_t *h);
 int aprod2_f32_fused_grid(const gsr_handle_t *h);

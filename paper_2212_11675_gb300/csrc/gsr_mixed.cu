@@ -42,7 +42,7 @@ template <int MODE, bool SMEMX, int U>
 __global__ void __launch_bounds__(kThreads, U == 1 ? 4 : 2)
 k_aprod1_f32(SysView A, const float *__restrict__ x32, const float4 *__restrict__ xatt4,
              double *__restrict__ y, float *__restrict__ q32, CgState *cg, double *partial,
-             unsigned *counter, const uint32_t *__restrict__ iperm, float *__restrict__ q32att)
+             unsigned *counter)
 {
     extern __shared__ float s_x32[];
     if (SMEMX) {
@@ -110,8 +110,6 @@ k_aprod1_f32(SysView A, const float *__restrict__ x32, const float4 *__restrict_
             } else {
                 const float qv = __fadd_rn(h0, l0);
                 q32[r] = qv;
-                if (q32att)  // the same value at the row's place in the attitude order
-                    q32att[__ldcs(iperm + r)] = qv;
                 // q^2 = pq + eq exactly (product error by FMA), accumulated
                 // in double-float on the FP32 pipe
                 const float pq = __fmul_rn(qv, qv);
@@ -249,9 +247,7 @@ k_aprod2_f32_stars(SysView A, const float *__restrict__ y32, double *__restrict_
 }
 
 // inner aprod 2, attitude part over the offset-sorted binary32 copy
-// yatt: y32 in the order of the copy (yatt[e] = y32[perm[e]]), or null
 __device__ __forceinline__ void att_body_f32(const SysView &A, const float *__restrict__ y32,
-                                             const float *__restrict__ yatt,
                                              double *__restrict__ S, int64_t warp, int64_t nwarps)
 {
     const int lane = threadIdx.x & 31;
@@ -264,21 +260,14 @@ __device__ __forceinline__ void att_body_f32(const SysView &A, const float *__re
             h[k] = l[k] = 0.f;
         uint32_t e = e0 + lane;
         for (; e + 32 < e1; e += 64) {  // two entries per lane in flight
-            float ya, yb;
-            if (yatt) {
-                ya = __ldcs(yatt + e);
-                yb = __ldcs(yatt + e + 32);
-            } else {
-                const uint32_t ra = __ldcs(A.perm + e), rb = __ldcs(A.perm + e + 32);
-                ya = __ldg(y32 + ra);
-                yb = __ldg(y32 + rb);
-            }
+            const uint32_t ra = __ldcs(A.perm + e), rb = __ldcs(A.perm + e + 32);
             float va[kNAtt], vb[kNAtt];
 #pragma unroll
             for (int k = 0; k < kNAtt; k++) {
                 va[k] = __ldcs(A.tval32 + tidx<kNAtt>(k, e));
                 vb[k] = __ldcs(A.tval32 + tidx<kNAtt>(k, e + 32));
             }
+            const float ya = __ldg(y32 + ra), yb = __ldg(y32 + rb);
 #pragma unroll
             for (int k = 0; k < kNAtt; k++) {
                 df_acc(h[k], l[k], __fmul_rn(va[k], ya));
@@ -286,7 +275,7 @@ __device__ __forceinline__ void att_body_f32(const SysView &A, const float *__re
             }
         }
         if (e < e1) {
-            const float yi = yatt ? __ldcs(yatt + e) : __ldg(y32 + __ldcs(A.perm + e));
+            const float yi = __ldg(y32 + __ldcs(A.perm + e));
 #pragma unroll
             for (int k = 0; k < kNAtt; k++)
                 df_acc(h[k], l[k], __fmul_rn(__ldcs(A.tval32 + tidx<kNAtt>(k, e)), yi));
@@ -327,7 +316,7 @@ k_att_segments_f32(SysView A, const float *__restrict__ y32, double *__restrict_
 {
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    att_body_f32(A, y32, nullptr, S, warp, nwarps);
+    att_body_f32(A, y32, S, warp, nwarps);
 }
 
 // inner aprod 2, instrumental part over the instrument-sorted binary32 copy,
@@ -434,8 +423,7 @@ __global__ void __launch_bounds__(kThreads)
 k_aprod2_f32_fused(SysView A, const float *__restrict__ y32, double *__restrict__ out,
                    double *__restrict__ S, const uint32_t *__restrict__ cseg,
                    const uint32_t *__restrict__ irow, const float *__restrict__ ival32,
-                   double *__restrict__ part, int nwin, int ks, double *__restrict__ gpart, A2Queue q,
-                   const float *__restrict__ yatt)
+                   double *__restrict__ part, int nwin, int ks, double *__restrict__ gpart, A2Queue q)
 {
     const int lane = threadIdx.x & 31;
     const int L = q.ns + q.na + q.ni;
@@ -474,7 +462,7 @@ k_aprod2_f32_fused(SysView A, const float *__restrict__ y32, double *__restrict_
         } else if (slot < q.ns + q.na) {
             const int64_t i = c * q.na + (slot - q.ns);
             if (i < A.nseg)
-                att_body_f32(A, y32, yatt, S, i, A.nseg);
+                att_body_f32(A, y32, S, i, A.nseg);
         } else {
             const int64_t i = c * q.ni + (slot - q.ns - q.na);
             if (i < q.ninstr_units)
@@ -697,9 +685,8 @@ bool x32_in_smem(const gsr_handle_t *h) { return h->sys.I <= kSmemInstrMax32; }
 constexpr int kA1f32Tiles = 1;
 
 template <int MODE>
-// q32att: also write q32 in the attitude order (the CG), or null
 static cudaError_t a1f_launch(const gsr_handle_t *h, const float *x32, double *y, float *q32,
-                              cudaStream_t st, float *q32att = nullptr)
+                              cudaStream_t st)
 {
     double *part = h->d_partial + kRedU * kPartialsPerKind;
     unsigned *cnt = h->d_counter + kRedU;
@@ -707,10 +694,10 @@ static cudaError_t a1f_launch(const gsr_handle_t *h, const float *x32, double *y
     if (x32_in_smem(h))
         k_aprod1_f32<MODE, true, U><<<h->grid_rows32, kThreads, (size_t)h->sys.I * sizeof(float),
                                       st>>>(h->sys, x32, (const float4 *)h->d_xatt4, y, q32,
-                                            h->d_cg, part, cnt, h->d_iperm, q32att);
+                                            h->d_cg, part, cnt);
     else
         k_aprod1_f32<MODE, false, U><<<h->grid_rows32, kThreads, 0, st>>>(
-            h->sys, x32, (const float4 *)h->d_xatt4, y, q32, h->d_cg, part, cnt, h->d_iperm, q32att);
+            h->sys, x32, (const float4 *)h->d_xatt4, y, q32, h->d_cg, part, cnt);
     return cudaGetLastError();
 }
 
@@ -723,11 +710,11 @@ static cudaError_t a2f_launch(const gsr_handle_t *h, const float *y32, double *o
         if (h->nq32 > 1)
             k_aprod2_f32_fused<G, MODE, true><<<h->grid_fused32, kThreads, 0, st>>>(
                 h->sys, y32, out, h->d_attS, h->d_cseg32, h->d_irow, h->d_ival32, h->d_ipart,
-                h->nq32, h->ks32, h->d_gpart, q, nullptr);
+                h->nq32, h->ks32, h->d_gpart, q);
         else
             k_aprod2_f32_fused<G, MODE, false><<<h->grid_fused32, kThreads, 0, st>>>(
                 h->sys, y32, out, h->d_attS, h->d_iseg, h->d_irow, h->d_ival32, h->d_ipart, 1,
-                h->ks32, h->d_gpart, q, nullptr);
+                h->ks32, h->d_gpart, q);
         const int nb_att = (int)((3 * h->sys.D + kThreads - 1) / kThreads < 4 * h->nsm
                                      ? (3 * h->sys.D + kThreads - 1) / kThreads
                                      : 4 * h->nsm);
@@ -784,26 +771,23 @@ static cudaError_t cg_iteration(const gsr_handle_t *h, cudaStream_t s, cudaGraph
                                 int in_graph)
 {
     const SysView &A = h->sys;
-    const bool fused = h->ipath == kIpSorted && h->a2_fused;
-    // with the single-launch aprod 2, aprod 1 also writes q32 in the
-    // attitude order for its attitude units
-    cudaError_t e = a1f_launch<1>(h, h->d_x32, nullptr, h->d_q32, s, fused ? h->d_q32att : nullptr);
+    cudaError_t e = a1f_launch<1>(h, h->d_x32, nullptr, h->d_q32, s);
     if (e != cudaSuccess)
         return e;
     A2Parts P = {};
     double *part = h->d_partial + kRedV * kPartialsPerKind;
     unsigned *cnt = h->d_counter + kRedV;
-    if (fused) {
+    if (h->ipath == kIpSorted && h->a2_fused) {
         // single-launch aprod 2 without the combine; the CG pass combines
         const A2Queue q = a2_queue(h, 8, (int64_t)A.I * h->nq32 * h->ks32);
         if (h->nq32 > 1)
             k_aprod2_f32_fused<8, kA2Overwrite, true><<<h->grid_fused32, kThreads, 0, s>>>(
                 h->sys, h->d_q32, h->d_t, h->d_attS, h->d_cseg32, h->d_irow, h->d_ival32,
-                h->d_ipart, h->nq32, h->ks32, h->d_gpart, q, h->d_q32att);
+                h->d_ipart, h->nq32, h->ks32, h->d_gpart, q);
         else
             k_aprod2_f32_fused<8, kA2Overwrite, false><<<h->grid_fused32, kThreads, 0, s>>>(
                 h->sys, h->d_q32, h->d_t, h->d_attS, h->d_iseg, h->d_irow, h->d_ival32, h->d_ipart,
-                1, h->ks32, h->d_gpart, q, h->d_q32att);
+                1, h->ks32, h->d_gpart, q);
         P = {h->d_attS, h->d_ipart, h->nq32 * h->ks32, h->d_gpart, (int)q.nstar_units, h->d_a2ctr};
         k_cg_vec1<true><<<h->grid_vec, kThreads, 0, s>>>(A, h->d_p, h->d_t, h->d_s, h->d_d, h->d_zc,
                                                          h->d_cg, h->d_cgargs, part, cnt, loop,
@@ -927,20 +911,6 @@ cudaError_t launch_count_pos(const gsr_handle_t *h, const double *a, double *out
 {
     k_count_pos<<<h->grid_vec, kThreads, 0, st>>>(a, h->sys.n, h->d_partial + kRedU * kPartialsPerKind,
                                                    h->d_counter + kRedU, out);
-    return cudaGetLastError();
-}
-
-// iperm[perm[e]] = e: the place of every row in the offset-sorted attitude copy
-__global__ void k_invert_perm(const uint32_t *__restrict__ perm, uint32_t *__restrict__ iperm,
-                              int64_t m)
-{
-    for (int64_t e = gtid32(); e < m; e += gstride32())
-        iperm[perm[e]] = (uint32_t)e;
-}
-
-cudaError_t launch_invert_perm(const gsr_handle_t *h, cudaStream_t st)
-{
-    k_invert_perm<<<h->nsm * 8, kThreads, 0, st>>>(h->d_perm, h->d_iperm, h->sys.m);
     return cudaGetLastError();
 }
 
