@@ -363,7 +363,8 @@ constexpr uint64_t kWaitNs = 1000000000ull;                         // 1 s
 // aprod 1, ms): 18 warps with one stage each and y staged 0.305; 20 warps
 // 0.308; 16 warps 0.321; 22 warps (80 registers, spills) 0.339; 12 warps
 // with two stages and no y 0.373; 24 warps with one stage and no y 0.399;
-// the register form 0.328.  More stages per warp cost warps (shared memory),
+// the register form 0.328; with ||U||^2 accumulated on the binary32 pipes
+// 0.309 against 0.305.  More stages per warp cost warps (shared memory),
 // and one tile ahead already covers the copy latency: a warp spends about
 // 5 us on a tile.
 constexpr int kTmaWarps = 18;

@@ -195,17 +195,6 @@ __device__ void lsqr_scalars(SolveState *st, const SolveArgs *args, double vnorm
     *st = s;
 }
 
-// v += x^2 into an exact three-level accumulator (binary32 pipes) when x is
-// in the split window, else into the binary64 fallback fb
-__device__ __forceinline__ void acc_sqr(Acc3 &c, double &fb, double x)
-{
-    float a1, a2, a3;
-    if (split3z(x, a1, a2, a3) < kSplitRangeSpan)
-        acc3_sqr(c, a1, a2, a3);
-    else
-        fb = fma(x, x, fb);
-}
-
 // The vector pass of iteration i (first: the start, V_1 = p o A^T b / beta_1
 // with w, z, var cleared).  The stored w is W_i = w_i / rho_i of the paper's
 // recurrence, which takes the division by rho out of three updates:
@@ -259,8 +248,8 @@ k_vec(const SysView A, const double *__restrict__ p, double *__restrict__ q, dou
             wj = fma(c2, w[j], vo * c1);
             vr = fma(wj, wj, var[j]);
             zj = fma(phi, wj, z[j]);
-            acc_sqr(c[1], fb[1], wj);
-            acc_sqr(c[2], fb[2], zj);
+            acc3_sqr_or(c[1], fb[1], wj);
+            acc3_sqr_or(c[2], fb[2], zj);
         }
         w[j] = wj;
         z[j] = zj;
@@ -270,7 +259,7 @@ k_vec(const SysView A, const double *__restrict__ p, double *__restrict__ q, dou
         const double vn = upd ? fma(pj * qj, k1, k2 * vo) : vo;
         v[j] = vn;
         vp[j] = pj * vn;
-        acc_sqr(c[0], fb[0], vn);
+        acc3_sqr_or(c[0], fb[0], vn);
     }
     if (INL) {  // this block's fixed slice of the global-column partials
         const uint32_t per = ((uint32_t)P.ngpart + gridDim.x - 1) / gridDim.x;

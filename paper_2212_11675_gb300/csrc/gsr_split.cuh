@@ -151,6 +151,17 @@ __device__ __forceinline__ void acc3_sqr(Acc3 &c, float a1, float a2, float a3)
     c.l = __fadd_rn(c.l, __fadd_rn(__fadd_rn(q, u1), __fadd_rn(u2, u3)));
 }
 
+// c += x^2 on the binary32 pipes when x splits exactly, else fb += x^2 in
+// binary64 (operands outside the split window)
+__device__ __forceinline__ void acc3_sqr_or(Acc3 &c, double &fb, double x)
+{
+    float a1, a2, a3;
+    if (split3z(x, a1, a2, a3) < kSplitRangeSpan)
+        acc3_sqr(c, a1, a2, a3);
+    else
+        fb = fma(x, x, fb);
+}
+
 // c += (h, m, l), another three-level value: both exact levels by TwoSum,
 // the third rounded
 __device__ __forceinline__ void acc3_add(Acc3 &c, float h, float m, float l)
