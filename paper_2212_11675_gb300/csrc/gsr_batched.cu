@@ -332,6 +332,25 @@ k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restri
         for (int c = 0; c < KT; c++)
             h[c] = l[c] = 0.f;
         uint32_t e = e0 + lane;
+        // four entries per lane in flight, then pairs, then one (the sums
+        // take the entries in order either way)
+        for (; e + 96 < e1; e += 128) {
+            uint32_t r4[4];
+            float v4[4], y4[4][KT];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                r4[u] = __ldcs(irow + e + 32 * u);
+                v4[u] = __ldcs(ival + e + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                load_cols<KT>(Y + (int64_t)r4[u] * ldk + c0, y4[u]);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int c = 0; c < KT; c++)
+                    df_acc(h[c], l[c], __fmul_rn(v4[u], y4[u][c]));
+        }
         for (; e + 32 < e1; e += 64) {
             const uint32_t ra = __ldcs(irow + e), rb = __ldcs(irow + e + 32);
             const float va = __ldcs(ival + e), vb = __ldcs(ival + e + 32);
