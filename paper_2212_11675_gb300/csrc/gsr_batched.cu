@@ -4,9 +4,14 @@
 // once per column tile and applied to KT columns (KT = 1, 2, 4 or 8), so the
 // matrix traffic of k solves is paid ceil(k/KT) times instead of k times.
 //
-// Dense vectors of the inner solve are row-major with leading dimension k:
-// entry (j, c) of an n x k block is at j*k + c, so the gather of unknown j
-// fetches KT consecutive values (one 32-byte sector for KT = 8 binary32).
+// Dense blocks of the inner solve are stored in panels of 8 columns: entry
+// (j, c) of a block with `rows` rows is at ((c / 8) rows + j) 8 + c % 8
+// (pidx).  A column tile of KT <= 8 columns lies in one panel, so the gather
+// of unknown j fetches KT consecutive values (one 32-byte sector for KT = 8
+// binary32) and a tile's gathers touch only its own rows x 8 panel, whatever
+// the number of columns (with one row-major block of leading dimension k, 32
+// columns spread a tile's sectors over four times the address range and its
+// products ran 1.7x slower than at 8 columns).
 //
 // Column sections:
 //   aprod 1: row-parallel, one row per lane (as the single form)
@@ -27,6 +32,14 @@
 namespace gsr {
 
 constexpr int kInstrSplit = 4;  // warps per instrument in the batched instrumental pass
+
+constexpr int kPanel = 8;  // columns per panel of the dense blocks
+
+// offset of entry (r, c) in a panelled block of `rows` rows
+__host__ __device__ __forceinline__ int64_t pidx(int64_t r, int64_t rows, int c)
+{
+    return ((int64_t)(c / kPanel) * rows + r) * kPanel + (c % kPanel);
+}
 
 __device__ __forceinline__ uint32_t instr_b(const uint4 &rc, int j)
 {
@@ -67,14 +80,13 @@ __device__ __forceinline__ bool grid_reduce_cols(double (&v)[KT], double *partia
 // three blocks per SM: at four the 8-column tile spills (measured 3% slower)
 template <int KT>
 __global__ void __launch_bounds__(kThreads, 3)
-k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ldk, int c0,
+k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int c0,
            BatchState *bs, double *partial, unsigned *counter)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t ntiles = (A.m + 31) >> 5;
-    const int64_t mp = A.mp;
     float nh[KT], nl[KT];  // |Q[:, c]|^2 of this thread (double-float)
 #pragma unroll
     for (int c = 0; c < KT; c++)
@@ -103,12 +115,12 @@ k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ld
                 col = A.glb0;
             const float a = __ldcs(v + 32 * k);
             float xv[KT];
-            load_cols<KT>(X + col * ldk + c0, xv);
+            load_cols<KT>(X + pidx(col, A.n, c0), xv);
 #pragma unroll
             for (int c = 0; c < KT; c++)
                 df_acc(h[c], l[c], __fmul_rn(a, xv[c]));
         }
-        float *q = Q + r * ldk + c0;
+        float *q = Q + pidx(r, A.m, c0);
 #pragma unroll
         for (int c = 0; c < KT; c++) {
             const float qv = __fadd_rn(h[c], l[c]);
@@ -138,7 +150,7 @@ k_b_aprod1(SysView A, const float *__restrict__ X, float *__restrict__ Q, int ld
 // ---------------------------------------------------------------------------
 template <int KT, int G>
 __global__ void __launch_bounds__(kThreads)
-k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ldk, int c0)
+k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int c0)
 {
     __shared__ double s_g[kThreads / 32][KT];
     constexpr int GPW = 32 / G;
@@ -146,7 +158,6 @@ k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ld
     const int gw = (threadIdx.x & 31) / G;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t mp = A.mp;
     float gh[KT], gl[KT];
 #pragma unroll
     for (int c = 0; c < KT; c++)
@@ -167,7 +178,7 @@ k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ld
         for (uint32_t r = r0 + lane; r < r1; r += G) {
             const float *v = A.val32 + tidx<kNPar>(0, r);
             float yv[KT];
-            load_cols<KT>(Y + (int64_t)r * ldk + c0, yv);
+            load_cols<KT>(Y + pidx(r, A.m, c0), yv);
 #pragma unroll
             for (int k = 0; k < kNAstro; k++) {
                 const float a = __ldcs(v + 32 * k);
@@ -197,7 +208,7 @@ k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ld
             const int v = P >= G ? lane * PER + k : lane / (G / P);
             const bool owner = P >= G || (lane % (G / P)) == 0;
             if (owner && v < NV && s < A.S)
-                T[((int64_t)kNAstro * s + v / KT) * ldk + c0 + v % KT] = df_to_d(rh[k], rl[k]);
+                T[pidx((int64_t)kNAstro * s + v / KT, A.n, c0) + v % KT] = df_to_d(rh[k], rl[k]);
         }
     }
 #pragma unroll
@@ -211,7 +222,7 @@ k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ld
         double t = 0.0;
         for (int w = 0; w < kThreads / 32; w++)
             t += s_g[w][threadIdx.x];
-        atomicAdd(T + A.glb0 * ldk + c0 + threadIdx.x, t);
+        atomicAdd(T + pidx(A.glb0, A.n, c0) + threadIdx.x, t);
     }
 }
 
@@ -221,12 +232,11 @@ k_b_stars(SysView A, const float *__restrict__ Y, double *__restrict__ T, int ld
 // ---------------------------------------------------------------------------
 template <int KT>
 __global__ void __launch_bounds__(kThreads)
-k_b_att(SysView A, const float *__restrict__ Y, double *__restrict__ S, int ldk, int c0)
+k_b_att(SysView A, const float *__restrict__ Y, double *__restrict__ S, int c0)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t mp = A.mp;
     constexpr int NV = 4 * KT;  // sums per (offset, axis)
     for (int64_t oa = warp; oa < A.nseg * 3; oa += nwarps) {
         const int64_t o = oa / 3;
@@ -249,8 +259,8 @@ k_b_att(SysView A, const float *__restrict__ Y, double *__restrict__ S, int ldk,
                 vb[j] = __ldcs(A.tval32 + tidx<kNAtt>(4 * a + j, e + 32));
             }
             float ya[KT], yb[KT];
-            load_cols<KT>(Y + (int64_t)ra * ldk + c0, ya);
-            load_cols<KT>(Y + (int64_t)rb * ldk + c0, yb);
+            load_cols<KT>(Y + pidx(ra, A.m, c0), ya);
+            load_cols<KT>(Y + pidx(rb, A.m, c0), yb);
 #pragma unroll
             for (int j = 0; j < 4; j++)
 #pragma unroll
@@ -264,7 +274,7 @@ k_b_att(SysView A, const float *__restrict__ Y, double *__restrict__ S, int ldk,
         }
         if (e < e1) {
             float yv[KT];
-            load_cols<KT>(Y + (int64_t)__ldcs(A.perm + e) * ldk + c0, yv);
+            load_cols<KT>(Y + pidx(__ldcs(A.perm + e), A.m, c0), yv);
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const float v = __ldcs(A.tval32 + tidx<kNAtt>(4 * a + j, e));
@@ -282,10 +292,10 @@ k_b_att(SysView A, const float *__restrict__ Y, double *__restrict__ S, int ldk,
     }
 }
 
-// attitude columns of T from S; ldk-strided, column tile c0
+// attitude columns of T from S, column tile c0
 template <int KT>
 __global__ void k_b_att_combine(SysView A, const double *__restrict__ S, double *__restrict__ T,
-                                int ldk, int c0)
+                                int c0)
 {
     const int64_t total = 3 * A.D * KT;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -300,7 +310,7 @@ __global__ void k_b_att_combine(SysView A, const double *__restrict__ S, double 
             if (o >= 0 && o < A.nseg)
                 t += S[((o * 3 + a) * 4 + j) * KT + c];
         }
-        T[(A.att0 + colrow) * ldk + c0 + c] = t;
+        T[pidx(A.att0 + colrow, A.n, c0) + c] = t;
     }
 }
 
@@ -313,7 +323,7 @@ template <int KT>
 __global__ void __launch_bounds__(kThreads)
 k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restrict__ irow,
           const float *__restrict__ ival, const float *__restrict__ Y, double *__restrict__ part,
-          int ldk, int c0)
+          int c0)
 {
     // warp w takes chunk (w % kInstrSplit) of instrument w / kInstrSplit; two
     // entries per lane are in flight to hide the dependent row -> Y gathers
@@ -344,7 +354,7 @@ k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restri
             }
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                load_cols<KT>(Y + (int64_t)r4[u] * ldk + c0, y4[u]);
+                load_cols<KT>(Y + pidx(r4[u], A.m, c0), y4[u]);
 #pragma unroll
             for (int u = 0; u < 4; u++)
 #pragma unroll
@@ -355,8 +365,8 @@ k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restri
             const uint32_t ra = __ldcs(irow + e), rb = __ldcs(irow + e + 32);
             const float va = __ldcs(ival + e), vb = __ldcs(ival + e + 32);
             float ya[KT], yb[KT];
-            load_cols<KT>(Y + (int64_t)ra * ldk + c0, ya);
-            load_cols<KT>(Y + (int64_t)rb * ldk + c0, yb);
+            load_cols<KT>(Y + pidx(ra, A.m, c0), ya);
+            load_cols<KT>(Y + pidx(rb, A.m, c0), yb);
 #pragma unroll
             for (int c = 0; c < KT; c++) {
                 df_acc(h[c], l[c], __fmul_rn(va, ya[c]));
@@ -365,7 +375,7 @@ k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restri
         }
         if (e < e1) {
             float yv[KT];
-            load_cols<KT>(Y + (int64_t)__ldcs(irow + e) * ldk + c0, yv);
+            load_cols<KT>(Y + pidx(__ldcs(irow + e), A.m, c0), yv);
             const float v = __ldcs(ival + e);
 #pragma unroll
             for (int c = 0; c < KT; c++)
@@ -383,7 +393,7 @@ k_b_instr(SysView A, const uint32_t *__restrict__ iseg, const uint32_t *__restri
 // instrumental rows of T from the per-chunk partials (fixed order)
 template <int KT>
 __global__ void k_b_instr_combine(SysView A, const double *__restrict__ part, double *__restrict__ T,
-                                  int ldk, int c0)
+                                  int c0)
 {
     const int64_t total = A.I * KT;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -394,12 +404,12 @@ __global__ void k_b_instr_combine(SysView A, const double *__restrict__ part, do
 #pragma unroll
         for (int q = 0; q < kInstrSplit; q++)
             t += part[(f * kInstrSplit + q) * KT + c];
-        T[(A.ins0 + f) * ldk + c0 + c] = t;
+        T[pidx(A.ins0 + f, A.n, c0) + c] = t;
     }
 }
 
 // ---------------------------------------------------------------------------
-// batched CG vector kernels: n x k row-major FP64 blocks, per-column scalars
+// batched CG vector kernels: n x k panelled FP64 blocks, per-column scalars
 // ---------------------------------------------------------------------------
 // S = p o C, Dd = S, Z = 0, X32 = fl32(p o Dd), gamma_c = |S_c|^2; zeroes the
 // global row of T.  One launch per column tile (c0, KT).
@@ -407,7 +417,7 @@ template <int KT>
 __global__ void __launch_bounds__(kThreads)
 k_b_init(const double *__restrict__ p, const double *__restrict__ C, double *__restrict__ Sv,
          double *__restrict__ Dd, double *__restrict__ Z, float *__restrict__ X32,
-         double *__restrict__ T, int64_t n, int64_t glb0, int ldk, int c0, BatchState *bs,
+         double *__restrict__ T, int64_t n, int64_t glb0, int c0, BatchState *bs,
          const BatchArgs *args, double *partial, unsigned *counter)
 {
     double acc[KT];
@@ -419,7 +429,7 @@ k_b_init(const double *__restrict__ p, const double *__restrict__ C, double *__r
         const double pj = p[j];
 #pragma unroll
         for (int c = 0; c < KT; c++) {
-            const int64_t i = j * ldk + c0 + c;
+            const int64_t i = pidx(j, n, c0) + c;
             const double sj = pj * C[i];
             Sv[i] = sj;
             Dd[i] = sj;
@@ -429,7 +439,7 @@ k_b_init(const double *__restrict__ p, const double *__restrict__ C, double *__r
         }
     }
     if (blockIdx.x == 0 && threadIdx.x < KT)
-        T[glb0 * ldk + c0 + threadIdx.x] = 0.0;
+        T[pidx(glb0, n, c0) + threadIdx.x] = 0.0;
     if (grid_reduce<KT>(acc, partial, counter) && threadIdx.x == 0) {
         if (c0 == 0) {
             bs->nonfinite = 0;
@@ -451,7 +461,7 @@ k_b_init(const double *__restrict__ p, const double *__restrict__ C, double *__r
 template <int KT>
 __global__ void __launch_bounds__(kThreads)
 k_b_vec1(const double *__restrict__ p, const double *__restrict__ T, double *__restrict__ Sv,
-         const double *__restrict__ Dd, double *__restrict__ Z, int64_t n, int ldk, int c0,
+         const double *__restrict__ Dd, double *__restrict__ Z, int64_t n, int c0,
          BatchState *bs, const BatchArgs *args, double *partial, unsigned *counter)
 {
     double al[KT], acc[KT];
@@ -465,7 +475,7 @@ k_b_vec1(const double *__restrict__ p, const double *__restrict__ T, double *__r
         const double pj = p[j];
 #pragma unroll
         for (int c = 0; c < KT; c++) {
-            const int64_t i = j * ldk + c0 + c;
+            const int64_t i = pidx(j, n, c0) + c;
             const double sj = fma(-al[c], pj * T[i], Sv[i]);
             Sv[i] = sj;
             Z[i] = fma(al[c], Dd[i], Z[i]);
@@ -497,7 +507,7 @@ k_b_vec1(const double *__restrict__ p, const double *__restrict__ T, double *__r
 template <int KT>
 __global__ void k_b_vec2(const double *__restrict__ p, const double *__restrict__ Sv,
                          double *__restrict__ Dd, float *__restrict__ X32, double *__restrict__ T,
-                         int64_t n, int64_t glb0, int ldk, int c0, const BatchState *bs)
+                         int64_t n, int64_t glb0, int c0, const BatchState *bs)
 {
     double be[KT];
 #pragma unroll
@@ -508,14 +518,14 @@ __global__ void k_b_vec2(const double *__restrict__ p, const double *__restrict_
         const double pj = p[j];
 #pragma unroll
         for (int c = 0; c < KT; c++) {
-            const int64_t i = j * ldk + c0 + c;
+            const int64_t i = pidx(j, n, c0) + c;
             const double dj = fma(be[c], Dd[i], Sv[i]);
             Dd[i] = dj;
             X32[i] = (float)(pj * dj);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x < KT)
-        T[glb0 * ldk + c0 + threadIdx.x] = 0.0;
+        T[pidx(glb0, n, c0) + threadIdx.x] = 0.0;
 }
 
 // loop flag: clear when every column is done
@@ -532,16 +542,16 @@ __global__ void k_b_flag(BatchState *bs, int k, cudaGraphConditionalHandle loop,
 }
 
 // generic layout change with optional binary32 output: to_rm = 1 maps a
-// column-major (rows x k) block to row-major, 0 the reverse
+// column-major (rows x k) block to the panelled layout, 0 the reverse
 __global__ void k_b_layout(int to_rm, const double *__restrict__ src, double *__restrict__ dst64,
-                           float *__restrict__ dst32, int64_t rows, int k, int ldk)
+                           float *__restrict__ dst32, int64_t rows, int k)
 {
     const int64_t total = rows * k;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = i / rows;
         const int64_t r = i - c * rows;
-        const int64_t rm = r * ldk + c, cm = i;
+        const int64_t rm = pidx(r, rows, (int)c), cm = i;
         const double v = to_rm ? src[cm] : src[rm];
         const int64_t to = to_rm ? rm : cm;
         if (dst32)
@@ -551,44 +561,42 @@ __global__ void k_b_layout(int to_rm, const double *__restrict__ src, double *__
     }
 }
 
-// row-major binary32 (rows x ldk) -> column-major FP64 (rows x k)
+// panelled binary32 (rows x k) -> column-major FP64 (rows x k)
 __global__ void k_b_rm32_to_cm(const float *__restrict__ src, double *__restrict__ dst, int64_t rows,
-                               int k, int ldk)
+                               int k)
 {
     const int64_t total = rows * k;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = i / rows;
         const int64_t r = i - c * rows;
-        dst[i] = (double)src[r * ldk + c];
+        dst[i] = (double)src[pidx(r, rows, (int)c)];
     }
 }
 
-// dst_f32: 0 FP64 out, 1 binary32 out, 2 binary32 row-major source -> FP64
-// column-major out.  The row-major side has leading dimension h->bk.
+// dst_f32: 0 FP64 out, 1 binary32 out, 2 binary32 panelled source -> FP64
+// column-major out (to_rm = 1: column-major in, panelled out).
 cudaError_t launch_b_layout(const gsr_handle_t *h, int to_rm, const double *src, void *dst,
                             int dst_f32, int64_t rows, int k, cudaStream_t st)
 {
     if (dst_f32 == 2)
-        k_b_rm32_to_cm<<<h->nsm * 8, kThreads, 0, st>>>((const float *)src, (double *)dst, rows, k,
-                                                         h->bk);
+        k_b_rm32_to_cm<<<h->nsm * 8, kThreads, 0, st>>>((const float *)src, (double *)dst, rows, k);
     else
         k_b_layout<<<h->nsm * 8, kThreads, 0, st>>>(to_rm, src, dst_f32 ? nullptr : (double *)dst,
-                                                     dst_f32 ? (float *)dst : nullptr, rows, k, h->bk);
+                                                     dst_f32 ? (float *)dst : nullptr, rows, k);
     return cudaGetLastError();
 }
 
-// X[:, c] += p o Z[:, c] (X column-major n x k, Z row-major with leading
-// dimension ldk)
+// X[:, c] += p o Z[:, c] (X column-major n x k, Z panelled)
 __global__ void k_b_update_x(const double *__restrict__ p, const double *__restrict__ Z,
-                             double *__restrict__ X, int64_t n, int k, int ldk)
+                             double *__restrict__ X, int64_t n, int k)
 {
     const int64_t total = n * k;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(i / n);
         const int64_t j = i - c * n;
-        X[i] = fma(p[j], Z[j * ldk + c], X[i]);
+        X[i] = fma(p[j], Z[pidx(j, n, c)], X[i]);
     }
 }
 
@@ -596,10 +604,10 @@ __global__ void k_b_update_x(const double *__restrict__ p, const double *__restr
 // launchers
 // ---------------------------------------------------------------------------
 template <int KT>
-static cudaError_t b_aprod1(const gsr_handle_t *h, const float *X, float *Q, int ldk, int c0,
+static cudaError_t b_aprod1(const gsr_handle_t *h, const float *X, float *Q, int c0,
                             cudaStream_t st)
 {
-    k_b_aprod1<KT><<<h->grid_b1, kThreads, 0, st>>>(h->sys, X, Q, ldk, c0, h->d_bs,
+    k_b_aprod1<KT><<<h->grid_b1, kThreads, 0, st>>>(h->sys, X, Q, c0, h->d_bs,
                                                     h->d_bpartial, h->d_bcounter);
     return cudaGetLastError();
 }
@@ -617,7 +625,7 @@ static int stars_grid(const gsr_handle_t *h)
 }
 
 template <int KT>
-static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, int ldk, int c0,
+static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, int c0,
                             cudaStream_t st)
 {
     // the star and attitude passes keep at most 4 columns per lane (register
@@ -625,53 +633,53 @@ static cudaError_t b_aprod2(const gsr_handle_t *h, const float *Y, double *T, in
     constexpr int KS = (KT > 4) ? 4 : KT;
     for (int cs = c0; cs < c0 + KT; cs += KS) {
         switch (h->b_lanes) {
-        case 8: k_b_stars<KS, 8><<<stars_grid<KS, 8>(h), kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
-        case 32: k_b_stars<KS, 32><<<stars_grid<KS, 32>(h), kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
-        default: k_b_stars<KS, 16><<<stars_grid<KS, 16>(h), kThreads, 0, st>>>(h->sys, Y, T, ldk, cs); break;
+        case 8: k_b_stars<KS, 8><<<stars_grid<KS, 8>(h), kThreads, 0, st>>>(h->sys, Y, T, cs); break;
+        case 32: k_b_stars<KS, 32><<<stars_grid<KS, 32>(h), kThreads, 0, st>>>(h->sys, Y, T, cs); break;
+        default: k_b_stars<KS, 16><<<stars_grid<KS, 16>(h), kThreads, 0, st>>>(h->sys, Y, T, cs); break;
         }
-        k_b_att<KS><<<h->grid_att, kThreads, 0, st>>>(h->sys, Y, h->d_bS, ldk, cs);
-        k_b_att_combine<KS><<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_bS, T, ldk, cs);
+        k_b_att<KS><<<h->grid_att, kThreads, 0, st>>>(h->sys, Y, h->d_bS, cs);
+        k_b_att_combine<KS><<<h->nsm * 4, kThreads, 0, st>>>(h->sys, h->d_bS, T, cs);
     }
     k_b_instr<KT><<<h->nsm * 8, kThreads, 0, st>>>(h->sys, h->d_iseg, h->d_irow, h->d_ival32, Y,
-                                                  h->d_bipart, ldk, c0);
-    k_b_instr_combine<KT><<<h->nsm * 2, kThreads, 0, st>>>(h->sys, h->d_bipart, T, ldk, c0);
+                                                  h->d_bipart, c0);
+    k_b_instr_combine<KT><<<h->nsm * 2, kThreads, 0, st>>>(h->sys, h->d_bipart, T, c0);
     return cudaGetLastError();
 }
 
 template <int KT>
-static cudaError_t b_prologue_tile(const gsr_handle_t *h, int ldk, int c0, cudaStream_t s)
+static cudaError_t b_prologue_tile(const gsr_handle_t *h, int c0, cudaStream_t s)
 {
     k_b_init<KT><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_bC, h->d_bS_, h->d_bD, h->d_bZ,
-                                                   h->d_bX32, h->d_bT, h->sys.n, h->sys.glb0, ldk,
+                                                   h->d_bX32, h->d_bT, h->sys.n, h->sys.glb0,
                                                    c0, h->d_bs, h->d_bargs, h->d_bpartial,
                                                    h->d_bcounter);
     return cudaGetLastError();
 }
 
 template <int KT>
-static cudaError_t b_iteration_tile_a(const gsr_handle_t *h, int ldk, int c0, cudaStream_t s)
+static cudaError_t b_iteration_tile_a(const gsr_handle_t *h, int c0, cudaStream_t s)
 {
-    cudaError_t e = b_aprod1<KT>(h, h->d_bX32, h->d_bQ32, ldk, c0, s);
+    cudaError_t e = b_aprod1<KT>(h, h->d_bX32, h->d_bQ32, c0, s);
     if (e == cudaSuccess)
-        e = b_aprod2<KT>(h, h->d_bQ32, h->d_bT, ldk, c0, s);
+        e = b_aprod2<KT>(h, h->d_bQ32, h->d_bT, c0, s);
     if (e != cudaSuccess)
         return e;
     k_b_vec1<KT><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_bT, h->d_bS_, h->d_bD, h->d_bZ,
-                                                   h->sys.n, ldk, c0, h->d_bs, h->d_bargs,
+                                                   h->sys.n, c0, h->d_bs, h->d_bargs,
                                                    h->d_bpartial, h->d_bcounter);
     k_b_vec2<KT><<<h->grid_vec, kThreads, 0, s>>>(h->d_p, h->d_bS_, h->d_bD, h->d_bX32, h->d_bT,
-                                                   h->sys.n, h->sys.glb0, ldk, c0, h->d_bs);
+                                                   h->sys.n, h->sys.glb0, c0, h->d_bs);
     return cudaGetLastError();
 }
 
-static cudaError_t b_dispatch(const gsr_handle_t *h, int kt, int which, int ldk, int c0,
+static cudaError_t b_dispatch(const gsr_handle_t *h, int kt, int which, int c0,
                               cudaStream_t s)
 {
     switch (kt) {
-    case 1: return which ? b_iteration_tile_a<1>(h, ldk, c0, s) : b_prologue_tile<1>(h, ldk, c0, s);
-    case 2: return which ? b_iteration_tile_a<2>(h, ldk, c0, s) : b_prologue_tile<2>(h, ldk, c0, s);
-    case 4: return which ? b_iteration_tile_a<4>(h, ldk, c0, s) : b_prologue_tile<4>(h, ldk, c0, s);
-    default: return which ? b_iteration_tile_a<8>(h, ldk, c0, s) : b_prologue_tile<8>(h, ldk, c0, s);
+    case 1: return which ? b_iteration_tile_a<1>(h, c0, s) : b_prologue_tile<1>(h, c0, s);
+    case 2: return which ? b_iteration_tile_a<2>(h, c0, s) : b_prologue_tile<2>(h, c0, s);
+    case 4: return which ? b_iteration_tile_a<4>(h, c0, s) : b_prologue_tile<4>(h, c0, s);
+    default: return which ? b_iteration_tile_a<8>(h, c0, s) : b_prologue_tile<8>(h, c0, s);
     }
 }
 
@@ -681,7 +689,7 @@ static cudaError_t b_prologue(const gsr_handle_t *h, int k, cudaStream_t s,
                               cudaGraphConditionalHandle loop, int in_graph)
 {
     for (int c0 = 0; c0 < k; c0 += h->b_kt) {
-        cudaError_t e = b_dispatch(h, h->b_kt, 0, k, c0, s);
+        cudaError_t e = b_dispatch(h, h->b_kt, 0, c0, s);
         if (e != cudaSuccess)
             return e;
     }
@@ -693,7 +701,7 @@ static cudaError_t b_iteration(const gsr_handle_t *h, int k, cudaStream_t s,
                                cudaGraphConditionalHandle loop, int in_graph)
 {
     for (int c0 = 0; c0 < k; c0 += h->b_kt) {
-        cudaError_t e = b_dispatch(h, h->b_kt, 1, k, c0, s);
+        cudaError_t e = b_dispatch(h, h->b_kt, 1, c0, s);
         if (e != cudaSuccess)
             return e;
     }
@@ -780,11 +788,11 @@ cudaError_t run_batched_inner(gsr_handle_t *h, int k, int max_inner, cudaStream_
 
 cudaError_t launch_b_update_x(const gsr_handle_t *h, double *X, int k, cudaStream_t st)
 {
-    k_b_update_x<<<h->nsm * 8, kThreads, 0, st>>>(h->d_p, h->d_bZ, X, h->sys.n, k, h->bk);
+    k_b_update_x<<<h->nsm * 8, kThreads, 0, st>>>(h->d_p, h->d_bZ, X, h->sys.n, k);
     return cudaGetLastError();
 }
 
-// single products on the binary32 copy for k columns (row-major blocks),
+// single products on the binary32 copy for k columns (panelled blocks),
 // for the parity tests and the tuner: Q = A32 X and T = A32^T Y
 cudaError_t launch_b_products(const gsr_handle_t *h, int k, const float *X, float *Q, const float *Y,
                               double *T, cudaStream_t st)
@@ -792,10 +800,10 @@ cudaError_t launch_b_products(const gsr_handle_t *h, int k, const float *X, floa
     for (int c0 = 0; c0 < k; c0 += h->b_kt) {
         cudaError_t e;
         switch (h->b_kt) {
-        case 1: e = b_aprod1<1>(h, X, Q, k, c0, st); if (e == cudaSuccess) e = b_aprod2<1>(h, Y, T, k, c0, st); break;
-        case 2: e = b_aprod1<2>(h, X, Q, k, c0, st); if (e == cudaSuccess) e = b_aprod2<2>(h, Y, T, k, c0, st); break;
-        case 4: e = b_aprod1<4>(h, X, Q, k, c0, st); if (e == cudaSuccess) e = b_aprod2<4>(h, Y, T, k, c0, st); break;
-        default: e = b_aprod1<8>(h, X, Q, k, c0, st); if (e == cudaSuccess) e = b_aprod2<8>(h, Y, T, k, c0, st); break;
+        case 1: e = b_aprod1<1>(h, X, Q, c0, st); if (e == cudaSuccess) e = b_aprod2<1>(h, Y, T, c0, st); break;
+        case 2: e = b_aprod1<2>(h, X, Q, c0, st); if (e == cudaSuccess) e = b_aprod2<2>(h, Y, T, c0, st); break;
+        case 4: e = b_aprod1<4>(h, X, Q, c0, st); if (e == cudaSuccess) e = b_aprod2<4>(h, Y, T, c0, st); break;
+        default: e = b_aprod1<8>(h, X, Q, c0, st); if (e == cudaSuccess) e = b_aprod2<8>(h, Y, T, c0, st); break;
         }
         if (e != cudaSuccess)
             return e;
