@@ -70,14 +70,17 @@ extern "C" {
  * sums, within 2^-60 of the sum of the magnitudes of the products it
  * accumulates (below the rounding of one FP64 FMA).  Operands whose exponent
  * is outside [-30, 30] (zero entries excepted) send the rows that use them
- * (aprod 1), or their star group or instrument unit (aprod 2), to native
- * FP64 products.  gsr_product_forms() tells which forms a handle runs. */
+ * (aprod 1), or their star group, attitude unit or instrument unit (aprod 2),
+ * to native FP64 products.  gsr_product_forms() tells which forms a handle
+ * runs. */
 #define GSR_PRODUCTS_AUTO 0   /* library choice: aprod 1's split form where it
                                  applies (I <= 3072); native products
                                  otherwise and in aprod 2 */
 #define GSR_PRODUCTS_NATIVE 1 /* every product on the FP64 pipe */
-#define GSR_PRODUCTS_SPLIT 2  /* every split form: GSR_SPLIT_APROD1 |
-                                 GSR_SPLIT_APROD2_STARS | GSR_SPLIT_APROD2_INSTR */
+#define GSR_PRODUCTS_SPLIT 2  /* the first three split forms: GSR_SPLIT_APROD1 |
+                                 GSR_SPLIT_APROD2_STARS | GSR_SPLIT_APROD2_INSTR
+                                 (the attitude and astrometric forms only
+                                 through GSR_PRODUCTS_MASK) */
 #define GSR_PRODUCTS_MASK 0x100 /* GSR_PRODUCTS_MASK | a set of the bits below:
                                    exactly the split forms named */
 #define GSR_SPLIT_APROD1 1        /* aprod 1: the 6 instrumental and the global
